@@ -1,0 +1,187 @@
+/*
+ * lqt.h - C ABI of the GB300 (sm_103a) temporally parallel continuous-time LQT
+ * solver.
+ *
+ * Method: Sarkka & Garcia-Fernandez, "Temporal Parallelisation of the HJB
+ * Equation and Continuous-Time Linear Quadratic Control" (arXiv 2212.11744).
+ * The problem (Sec. II-B, eq. LQT_Control_problem) is
+ *
+ *     dx/dt = F(t) x + L(t) u + c(t)
+ *     cost  = 1/2 (Hf x(tf) - rf)' Xf (Hf x(tf) - rf)
+ *           + int 1/2 (r - H x)' X (r - H x) + 1/2 u' U u dt
+ *
+ * on [t_0, t_T] split into T sub-intervals t_0 < t_1 < ... < t_T.  The solver
+ *   (a) integrates every sub-interval's conditional value function
+ *       (A, b, C, eta, J, zeta) with K classical RK4 steps of the backward
+ *       conditional HJB ODEs (Sec. IV-B, Theorem Backward_HJB_LQT, boundary
+ *       eq. abcej_boundary), element T being the terminal cost (Sec. IV-D,
+ *       eq. LQT_final_initialisation);
+ *   (b) scans the elements from the right with the combination rule of
+ *       Sec. IV-A (eq. lqt_comb), giving the value function
+ *       V(x, t_k) = zeta_k + 1/2 x' S_k x - v_k' x at every t_k (eq. eJ_vS);
+ *   (c) scans the one-sub-interval affine maps x_{k+1} = Psi_k x_k + alpha_k
+ *       (Sec. IV-E, Method 1 combination eqs. Psi_comb/alpha_comb, with the
+ *       maps from the one-sub-interval form of Method 2) for the optimal
+ *       states, and evaluates u_k = U^-1 L' (v_k - S_k x_k) (eq.
+ *       LQT_optimal_control).
+ *
+ * Conventions for every entry point
+ *  - All array pointers are DEVICE pointers unless stated otherwise; the caller
+ *    owns every buffer.  The library allocates no device memory: scratch space
+ *    is caller-provided and sized by lqt_workspace_size().
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and never synchronise, except lqt_get_status()
+ *    and lqt_solve_host().
+ *  - Matrices are row-major and dense; symmetric outputs are written in full.
+ *    Arrays indexed by boundary run over k = 0..T (T+1 entries).
+ *  - FP64 throughout.
+ *  - Errors: invalid arguments are rejected on the host before any launch and
+ *    returned directly.  Numerical trouble found on the device (a non-finite
+ *    value in an output, a zero pivot) is recorded in a per-device status word
+ *    read and cleared by lqt_get_status().
+ *  - Supported state dimensions n: 1, 2, 3, 4, 8.  Other n return
+ *    LQT_EUNSUPPORTED.
+ */
+#ifndef LQT_H
+#define LQT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LQT_OK = 0,
+  LQT_EINVAL = 1,       /* bad dimension, NULL pointer, bad sampling mode       */
+  LQT_EWORKSPACE = 2,   /* workspace NULL or smaller than lqt_workspace_size()   */
+  LQT_ENONFINITE = 3,   /* device found a NaN/Inf in an output                   */
+  LQT_ESINGULAR = 4,    /* device found a zero pivot (U or I + C J singular)     */
+  LQT_ETIMEOUT = 5,     /* lqt_get_status() deadline passed before the stream     */
+  LQT_ECUDA = 6,        /* a CUDA runtime call failed                             */
+  LQT_EUNSUPPORTED = 7  /* dimension not compiled in                              */
+} lqt_status;
+
+/* How a time-varying coefficient is sampled.  For sub-interval j with
+ * h_j = (t_{j+1} - t_j)/K the RK4 stages of the element ODE need the
+ * coefficients at the half-step times t_j + p h_j / 2, p = 0..2K. */
+typedef enum {
+  LQT_CONST = 0,        /* 1 sample                                              */
+  LQT_PER_INTERVAL = 1, /* T samples; sample j holds on all of sub-interval j     */
+  LQT_PER_STAGE = 2     /* 2KT+1 samples; sample 2Kj+p is at t_j + p h_j / 2      */
+} lqt_sampling;
+
+/* One coefficient: `ptr` points at its samples, each sample a row-major matrix
+ * or vector of the coefficient's shape, samples back to back. */
+typedef struct {
+  const double *ptr;
+  int32_t mode; /* lqt_sampling */
+} lqt_coef;
+
+/* The problem of Sec. II-B.  Shapes per sample:
+ *   F n x n, L n x m, c n (ptr NULL = zero), H nr x n (ptr NULL = identity,
+ *   then nr must equal n), X nr x nr symmetric PSD, U m x m symmetric PD,
+ *   r nr (ptr NULL = zero); Hf nr x n (NULL = identity), Xf nr x nr, rf nr
+ *   (NULL = zero).  t: T+1 strictly increasing block boundaries. */
+typedef struct {
+  int32_t n, m, nr;
+  int64_t T;
+  int32_t K; /* RK4 steps per sub-interval, >= 1 */
+  const double *t;
+  lqt_coef F, L, c, H, X, U, r;
+  const double *Hf, *Xf, *rf;
+} lqt_problem;
+
+/* Conditional value function elements of Sec. IV-A (eq. LQT_V_form2), T+1 of
+ * them (index T = terminal element): A[T+1][n][n], b[T+1][n], C[T+1][n][n],
+ * eta[T+1][n], J[T+1][n][n], zeta[T+1].  Device pointers. */
+typedef struct {
+  double *A, *b, *C, *eta, *J, *zeta;
+} lqt_elements;
+
+/* Which call a workspace is for. */
+enum {
+  LQT_WS_BUILD = 0,
+  LQT_WS_VALUE = 1,
+  LQT_WS_TRAJ = 2,
+  LQT_WS_SOLVE = 3,
+  LQT_WS_SEQUENTIAL = 4
+};
+
+/* Bytes of device workspace the call `which` needs for problem p (host call,
+ * reads only the scalar fields and sampling modes of p).  0 if p is invalid. */
+size_t lqt_workspace_size(const lqt_problem *p, int32_t which);
+
+/* Stage (a): every element a_j, j = 0..T-1, by K RK4 steps of the backward
+ * conditional HJB ODEs of Sec. IV-B (Theorem Backward_HJB_LQT) from the
+ * boundary A=I, b=C=eta=J=0, zeta=0 at s = t_{j+1} down to s = t_j, and the
+ * terminal element a_T of Sec. IV-D (A=b=C=0, J=Hf'XfHf, eta=Hf'Xf rf,
+ * zeta = 1/2 rf'Xf rf).  zeta obeys d zeta/ds = -1/2 r'Xr + 1/2 eta'B eta +
+ * eta'c (B = L U^-1 L'), the state-free part of the same HJB.
+ * out: caller-owned device arrays (see lqt_elements). */
+lqt_status lqt_build_elements(const lqt_problem *p, const lqt_elements *out, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/* Stage (b): the reverse all-prefix-sums sbar_k = a_k (x) ... (x) a_T of the
+ * T+1 elements (Sec. III-D, Theorem parallel_HJB, eq. parallel_V_HJB) with the
+ * combination of Sec. IV-A, as a chunked reduce / scan / value-form
+ * down-sweep.  Writes S_k = J(sbar_k) [T+1][n][n], v_k = eta(sbar_k) [T+1][n]
+ * and zeta_k [T+1] (eq. eJ_vS).  zeta may be NULL. */
+lqt_status lqt_scan_value(const lqt_problem *p, const lqt_elements *el, double *S, double *v, double *zeta,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* Stage (c): optimal states and controls at the boundaries.  For each k the
+ * one-sub-interval map of Method 2 (Sec. IV-E, eq. Opt_trajectory_method2 with
+ * t_0 replaced by t_k): Psi_k = (I + C_k S_{k+1})^-1 A_k,
+ * alpha_k = (I + C_k S_{k+1})^-1 (b_k + C_k v_{k+1}); the maps are composed
+ * with the associative rule of Method 1 (eqs. Psi_comb, alpha_comb) in a
+ * prefix scan applied to x0, giving x[T+1][n]; then u_k = U^-1 L' (v_k - S_k
+ * x_k) (eq. LQT_optimal_control) with the coefficients at t_k, u[T+1][m].
+ * x0: device [n].  u may be NULL. */
+lqt_status lqt_scan_trajectory(const lqt_problem *p, const lqt_elements *el, const double *S, const double *v,
+                               const double *x0, double *x, double *u, void *ws, size_t ws_bytes, void *stream);
+
+/* Stages (a)+(b)+(c) in one call, with the elements and the maps kept in the
+ * workspace.  cost (device, 1 double, may be NULL) receives the optimal cost
+ * V(x0, t_0) = zeta_0 + 1/2 x0'S_0 x0 - v_0'x0 (eq. V_quadratic_LQT).  zeta, u
+ * may be NULL.  Graph-capturable (no allocation, no synchronisation). */
+lqt_status lqt_solve(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
+                     double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* The sequential method of Sec. VI-A as ONE GPU thread (the comparison
+ * baseline): K RK4 steps per sub-interval of the Riccati ODEs for S, v, zeta
+ * (Sec. II-B, eq. LQT_differential_S_v) backward from t_T, then K RK4 steps
+ * per sub-interval of the closed-loop ODE (eq. optimal_trajectory_ODE_LQT)
+ * forward from x0, with S, v at the step midpoints from the cubic Hermite
+ * interpolant of the backward solution.  Same outputs as lqt_solve. */
+lqt_status lqt_solve_sequential(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta,
+                                double *x, double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* End-to-end convenience call on HOST buffers: the problem's pointers (t, the
+ * coefficients, Hf, Xf, rf) and x0 point at host memory, and so do the
+ * outputs.  Copies the inputs to the caller's device workspace (its size from
+ * lqt_workspace_size(p, LQT_WS_SOLVE) + lqt_host_staging_size(p)), runs
+ * lqt_solve on `stream`, copies the outputs back and synchronises the stream.
+ * Host buffers should be pinned for full copy speed. */
+size_t lqt_host_staging_size(const lqt_problem *p);
+lqt_status lqt_solve_host(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
+                          double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* Waits for `stream` (polling, at most timeout_ms; < 0 waits forever), then
+ * reads and clears the current device's status word.  Returns LQT_OK,
+ * LQT_ENONFINITE, LQT_ESINGULAR, LQT_ETIMEOUT or LQT_ECUDA. */
+lqt_status lqt_get_status(void *stream, int32_t timeout_ms);
+
+/* Human-readable name of a status code (static string). */
+const char *lqt_strerror(lqt_status s);
+
+/* Number of kernel launches the last call on this host thread made (for
+ * launch accounting). */
+int32_t lqt_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQT_H */

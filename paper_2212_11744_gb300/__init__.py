@@ -1,0 +1,222 @@
+"""GB300-native temporally parallel continuous-time LQT solver.
+
+Python binding of the C ABI in include/lqt.h, with the same entry-point names.
+Every step of the solve runs in the CUDA library (csrc/); this module only
+moves arrays to the device (PyTorch is used for device memory and streams) and
+fills the C structs.
+
+    import paper_2212_11744_gb300 as lqt
+    dp = lqt.DeviceProblem(problem)        # problem: n, m, nr, T, K, t, F, L, ...
+    out = lqt.lqt_solve(dp)                # dict of device tensors S, v, zeta, x, u, cost
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BUILD, LQT_WS_SEQUENTIAL, LQT_WS_SOLVE,
+                   LQT_WS_TRAJ, LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
+
+__all__ = [
+    "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
+    "lqt_scan_trajectory", "lqt_solve", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
+    "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path",
+]
+
+_COEFS = ("F", "L", "c", "H", "X", "U", "r")
+
+
+def library_path() -> str:
+    return _abi.LIB_PATH
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class _Marshal:
+    """Copies a problem's arrays into tensors (device or pinned host) and fills lqt_problem."""
+
+    def __init__(self, p, device, pinned: bool):
+        self.keep = []
+        self.n, self.m, self.nr, self.T, self.K = int(p.n), int(p.m), int(p.nr), int(p.T), int(p.K)
+
+        def put(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            t = torch.from_numpy(a)
+            if device is not None:
+                t = t.to(device)
+            elif pinned:
+                t = t.pin_memory()
+            self.keep.append(t)
+            return t
+
+        s = lqt_problem()
+        s.n, s.m, s.nr, s.T, s.K = self.n, self.m, self.nr, self.T, self.K
+        s.t = _ptr(put(p.t))
+        for name in _COEFS:
+            co = getattr(p, name)
+            if co is None:
+                setattr(s, name, lqt_coef(None, 0))
+            else:
+                setattr(s, name, lqt_coef(_ptr(put(co.values)), int(co.mode)))
+        s.Hf = _ptr(put(p.Hf))
+        s.Xf = _ptr(put(p.Xf))
+        s.rf = _ptr(put(p.rf))
+        self.x0 = put(p.x0) if getattr(p, "x0", None) is not None else None
+        self.struct = s
+
+    def ref(self):
+        return ct.byref(self.struct)
+
+
+class DeviceProblem(_Marshal):
+    """A problem with every array resident on the GPU."""
+
+    def __init__(self, problem, device: str = "cuda"):
+        super().__init__(problem, torch.device(device), False)
+        self.device = torch.device(device)
+
+
+class HostProblem(_Marshal):
+    """A problem whose arrays stay in (pinned) host memory, for lqt_solve_host."""
+
+    def __init__(self, problem, pinned: bool = True):
+        super().__init__(problem, None, pinned)
+
+
+def lqt_strerror(code: int) -> str:
+    return _abi.strerror(code)
+
+
+def lqt_last_launch_count() -> int:
+    return int(_abi.lib().lqt_last_launch_count())
+
+
+def lqt_workspace_size(dp: _Marshal, which: int) -> int:
+    return int(_abi.lib().lqt_workspace_size(dp.ref(), which))
+
+
+def _workspace(dp: DeviceProblem, which: int, ws: Optional[torch.Tensor]):
+    need = lqt_workspace_size(dp, which)
+    if need == 0:
+        raise LQTError(_abi.LQT_EINVAL, "lqt_workspace_size")
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=dp.device)
+    return ws
+
+
+def _empty(dp, *shape):
+    return torch.empty(*shape, dtype=torch.float64, device=dp.device)
+
+
+def _elements_struct(el: dict) -> lqt_elements:
+    return lqt_elements(_ptr(el["A"]), _ptr(el["b"]), _ptr(el["C"]), _ptr(el["eta"]), _ptr(el["J"]),
+                        _ptr(el.get("zeta")))
+
+
+def new_elements(dp: DeviceProblem) -> dict:
+    n, T1 = dp.n, dp.T + 1
+    return {"A": _empty(dp, T1, n, n), "b": _empty(dp, T1, n), "C": _empty(dp, T1, n, n), "eta": _empty(dp, T1, n),
+            "J": _empty(dp, T1, n, n), "zeta": _empty(dp, T1)}
+
+
+def lqt_build_elements(dp: DeviceProblem, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    out = new_elements(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_BUILD, ws)
+    es = _elements_struct(out)
+    _abi.check(_abi.lib().lqt_build_elements(dp.ref(), ct.byref(es), ws.data_ptr(), ws.numel(),
+                                             _stream_handle(stream)), "lqt_build_elements")
+    return out
+
+
+def lqt_scan_value(dp: DeviceProblem, elements: dict, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    n, T1 = dp.n, dp.T + 1
+    out = out or {"S": _empty(dp, T1, n, n), "v": _empty(dp, T1, n), "zeta": _empty(dp, T1)}
+    ws = _workspace(dp, LQT_WS_VALUE, ws)
+    es = _elements_struct(elements)
+    _abi.check(_abi.lib().lqt_scan_value(dp.ref(), ct.byref(es), _ptr(out["S"]), _ptr(out["v"]),
+                                         _ptr(out.get("zeta")), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+               "lqt_scan_value")
+    return out
+
+
+def lqt_scan_trajectory(dp: DeviceProblem, elements: dict, S, v, x0=None, out: Optional[dict] = None, ws=None,
+                        stream=None) -> dict:
+    n, m, T1 = dp.n, dp.m, dp.T + 1
+    x0 = dp.x0 if x0 is None else x0
+    out = out or {"x": _empty(dp, T1, n), "u": _empty(dp, T1, m)}
+    ws = _workspace(dp, LQT_WS_TRAJ, ws)
+    es = _elements_struct(elements)
+    _abi.check(_abi.lib().lqt_scan_trajectory(dp.ref(), ct.byref(es), _ptr(S), _ptr(v), _ptr(x0), _ptr(out["x"]),
+                                              _ptr(out.get("u")), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+               "lqt_scan_trajectory")
+    return out
+
+
+def new_solution(dp: DeviceProblem) -> dict:
+    n, m, T1 = dp.n, dp.m, dp.T + 1
+    return {"S": _empty(dp, T1, n, n), "v": _empty(dp, T1, n), "zeta": _empty(dp, T1), "x": _empty(dp, T1, n),
+            "u": _empty(dp, T1, m), "cost": _empty(dp, 1)}
+
+
+def lqt_solve(dp: DeviceProblem, x0=None, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    x0 = dp.x0 if x0 is None else x0
+    out = new_solution(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_SOLVE, ws)
+    _abi.check(_abi.lib().lqt_solve(dp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]), _ptr(out.get("zeta")),
+                                    _ptr(out["x"]), _ptr(out.get("u")), _ptr(out.get("cost")), ws.data_ptr(),
+                                    ws.numel(), _stream_handle(stream)), "lqt_solve")
+    return out
+
+
+def lqt_solve_sequential(dp: DeviceProblem, x0=None, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    x0 = dp.x0 if x0 is None else x0
+    out = new_solution(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_SEQUENTIAL, ws)
+    _abi.check(_abi.lib().lqt_solve_sequential(dp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]),
+                                               _ptr(out.get("zeta")), _ptr(out["x"]), _ptr(out.get("u")),
+                                               _ptr(out.get("cost")), ws.data_ptr(), ws.numel(),
+                                               _stream_handle(stream)), "lqt_solve_sequential")
+    return out
+
+
+def lqt_host_staging_size(hp: HostProblem) -> int:
+    return int(_abi.lib().lqt_host_staging_size(hp.ref()))
+
+
+def host_solution(hp: HostProblem, pinned: bool = True) -> dict:
+    n, m, T1 = hp.n, hp.m, hp.T + 1
+
+    def e(*shape):
+        t = torch.empty(*shape, dtype=torch.float64)
+        return t.pin_memory() if pinned else t
+
+    return {"S": e(T1, n, n), "v": e(T1, n), "zeta": e(T1), "x": e(T1, n), "u": e(T1, m), "cost": e(1)}
+
+
+def lqt_solve_host(hp: HostProblem, ws: torch.Tensor, out: Optional[dict] = None, x0=None, stream=None) -> dict:
+    """Host buffers in and out; `ws` is a device uint8 tensor of at least
+    lqt_workspace_size(hp, LQT_WS_SOLVE) + lqt_host_staging_size(hp) bytes."""
+    x0 = hp.x0 if x0 is None else x0
+    out = host_solution(hp) if out is None else out
+    _abi.check(_abi.lib().lqt_solve_host(hp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]), _ptr(out.get("zeta")),
+                                         _ptr(out["x"]), _ptr(out.get("u")), _ptr(out.get("cost")), ws.data_ptr(),
+                                         ws.numel(), _stream_handle(stream)), "lqt_solve_host")
+    return out
+
+
+def lqt_get_status(stream=None, timeout_ms: int = 10000) -> int:
+    return int(_abi.lib().lqt_get_status(_stream_handle(stream), timeout_ms))

@@ -1,0 +1,323 @@
+// C ABI entry points of the LQT library (declared in include/lqt.h): host-side
+// argument validation, workspace layout, dispatch to the kernels, the device
+// status word and the host-buffer convenience call.
+#include <chrono>
+#include <cstring>
+#include <thread>
+
+#include <cuda_runtime.h>
+
+#include "lqt_internal.h"
+
+namespace lqt {
+
+__device__ unsigned g_status_word = 0;
+
+static thread_local int32_t t_launches = 0;
+void count_launch(int k) { t_launches += k; }
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool supported_n(int n) { return n == 1 || n == 2 || n == 3 || n == 4 || n == 8; }
+
+// Largest padded factor width compiled for each n.
+static int max_M(int n) { return n == 1 ? 1 : n == 2 ? 2 : n <= 4 ? 4 : 8; }
+
+static bool valid_mode(int32_t m) { return m == LQT_CONST || m == LQT_PER_INTERVAL || m == LQT_PER_STAGE; }
+
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+// Structural validation shared by every call.  Returns LQT_OK or an error.
+static lqt_status validate(const lqt_problem* p) {
+  if (!p) return LQT_EINVAL;
+  if (p->n < 1 || p->m < 1 || p->nr < 1 || p->T < 1 || p->K < 1) return LQT_EINVAL;
+  if (!supported_n(p->n)) return LQT_EUNSUPPORTED;
+  if (p->m > 16 || p->nr > 16) return LQT_EUNSUPPORTED;
+  if (padded_M(p->m) > max_M(p->n)) return LQT_EUNSUPPORTED;
+  if (!p->t || !p->F.ptr || !p->L.ptr || !p->X.ptr || !p->U.ptr || !p->Xf) return LQT_EINVAL;
+  if (!p->H.ptr && p->nr != p->n) return LQT_EINVAL;
+  if (!p->Hf && p->nr != p->n) return LQT_EINVAL;
+  const lqt_coef* cs[7] = {&p->F, &p->L, &p->c, &p->H, &p->X, &p->U, &p->r};
+  for (const lqt_coef* c : cs) {
+    if (c->ptr && !valid_mode(c->mode)) return LQT_EINVAL;
+    if (c->ptr && !aligned8(c->ptr)) return LQT_EINVAL;
+  }
+  if (!aligned8(p->t) || !aligned8(p->Xf) || (p->Hf && !aligned8(p->Hf)) || (p->rf && !aligned8(p->rf)))
+    return LQT_EINVAL;
+  return LQT_OK;
+}
+
+static Layout make_layout(const lqt_problem& p) {
+  Layout L{};
+  L.n = p.n; L.m = p.m; L.nr = p.nr; L.K = p.K; L.T = p.T;
+  L.M = padded_M(p.m);
+  const int32_t mH = p.H.ptr ? p.H.mode : kConst;
+  const int32_t mr = p.r.ptr ? p.r.mode : kConst;
+  L.mode_Lt = combine_modes(p.L.mode, p.U.mode);
+  L.mode_Q = combine_modes(mH, p.X.mode);
+  L.mode_qr = combine_modes(L.mode_Q, mr);
+  size_t off = 0;
+  L.off_Lt = off;
+  off = align_up(off + sample_count(L.mode_Lt, p.T, p.K) * (size_t)p.n * L.M * sizeof(double));
+  L.off_Q = off;
+  off = align_up(off + sample_count(L.mode_Q, p.T, p.K) * (size_t)(p.n * (p.n + 1) / 2) * sizeof(double));
+  L.off_qr = off;
+  off = align_up(off + sample_count(L.mode_qr, p.T, p.K) * (size_t)(p.n + 1) * sizeof(double));
+  L.off_Ku = off;
+  const bool ku_const = p.L.mode == LQT_CONST && p.U.mode == LQT_CONST;
+  off = align_up(off + (ku_const ? 1 : (size_t)p.T + 1) * (size_t)p.m * p.n * sizeof(double));
+  L.coef_bytes = off;
+  return L;
+}
+
+static size_t element_bytes(const lqt_problem& p) {
+  const size_t n = p.n, T1 = (size_t)p.T + 1;
+  return align_up(T1 * n * n * 8) * 3 + align_up(T1 * n * 8) * 2 + align_up(T1 * 8);
+}
+
+static ElemPtrs carve_elements(const lqt_problem& p, char* base) {
+  const size_t n = p.n, T1 = (size_t)p.T + 1;
+  ElemPtrs e;
+  char* c = base;
+  e.A = (double*)c; c += align_up(T1 * n * n * 8);
+  e.C = (double*)c; c += align_up(T1 * n * n * 8);
+  e.J = (double*)c; c += align_up(T1 * n * n * 8);
+  e.b = (double*)c; c += align_up(T1 * n * 8);
+  e.eta = (double*)c; c += align_up(T1 * n * 8);
+  e.zeta = (double*)c;
+  return e;
+}
+
+static lqt_status from_cuda(cudaError_t e) { return e == cudaSuccess ? LQT_OK : LQT_ECUDA; }
+
+}  // namespace lqt
+
+using namespace lqt;
+
+extern "C" {
+
+size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
+  if (validate(p) != LQT_OK) return 0;
+  const Layout L = make_layout(*p);
+  const size_t T1 = (size_t)p->T + 1;
+  switch (which) {
+    case LQT_WS_BUILD: return L.coef_bytes;
+    case LQT_WS_VALUE: return scan_workspace_bytes(p->n, p->T, false);
+    case LQT_WS_TRAJ: return L.coef_bytes + scan_workspace_bytes(p->n, p->T, true);
+    case LQT_WS_SOLVE:
+      return L.coef_bytes + element_bytes(*p) + align_up(T1 * 8) + scan_workspace_bytes(p->n, p->T, true);
+    case LQT_WS_SEQUENTIAL: return L.coef_bytes + align_up(sequential_workspace_bytes(p->n, p->T, p->K));
+    default: return 0;
+  }
+}
+
+lqt_status lqt_build_elements(const lqt_problem* p, const lqt_elements* out, void* ws, size_t ws_bytes,
+                              void* stream) {
+  t_launches = 0;
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (!out || !out->A || !out->b || !out->C || !out->eta || !out->J) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_BUILD);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  Coefs cf;
+  cudaError_t e = launch_prepare_coefs(*p, L, (char*)ws, cf, st);
+  if (e != cudaSuccess) return LQT_ECUDA;
+  ElemPtrs el{out->A, out->b, out->C, out->eta, out->J, out->zeta};
+  return from_cuda(launch_build(*p, L, cf, el, st));
+}
+
+lqt_status lqt_scan_value(const lqt_problem* p, const lqt_elements* el, double* S, double* v, double* zeta,
+                          void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (!el || !el->A || !el->b || !el->C || !el->eta || !el->J || !S || !v) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_VALUE);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  const Layout L = make_layout(*p);
+  Coefs cf{};
+  ElemPtrs e{el->A, el->b, el->C, el->eta, el->J, el->zeta};
+  return from_cuda(run_value_and_traj(*p, L, cf, e, S, v, zeta, nullptr, nullptr, nullptr, nullptr, true, false,
+                                      nullptr, nullptr, (char*)ws, ws_bytes, (cudaStream_t)stream));
+}
+
+lqt_status lqt_scan_trajectory(const lqt_problem* p, const lqt_elements* el, const double* S, const double* v,
+                               const double* x0, double* x, double* u, void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (!el || !el->A || !el->b || !el->C || !el->eta || !el->J || !S || !v || !x0 || !x) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_TRAJ);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  Coefs cf;
+  if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
+  ElemPtrs e{el->A, el->b, el->C, el->eta, el->J, el->zeta};
+  return from_cuda(run_value_and_traj(*p, L, cf, e, nullptr, nullptr, nullptr, x0, x, u, nullptr, false, true, S, v,
+                                      (char*)ws + L.coef_bytes, ws_bytes - L.coef_bytes, st));
+}
+
+lqt_status lqt_solve(const lqt_problem* p, const double* x0, double* S, double* v, double* zeta, double* x,
+                     double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (!x0 || !S || !v || !x) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_SOLVE);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  char* base = (char*)ws;
+  Coefs cf;
+  if (launch_prepare_coefs(*p, L, base, cf, st) != cudaSuccess) return LQT_ECUDA;
+  ElemPtrs el = carve_elements(*p, base + L.coef_bytes);
+  double* zbuf = (double*)(base + L.coef_bytes + element_bytes(*p));
+  double* zout = zeta ? zeta : zbuf;
+  if (launch_build(*p, L, cf, el, st) != cudaSuccess) return LQT_ECUDA;
+  char* scan = base + L.coef_bytes + element_bytes(*p) + align_up(((size_t)p->T + 1) * 8);
+  return from_cuda(run_value_and_traj(*p, L, cf, el, S, v, zout, x0, x, u, cost, true, true, nullptr, nullptr, scan,
+                                      ws_bytes - (scan - base), st));
+}
+
+lqt_status lqt_solve_sequential(const lqt_problem* p, const double* x0, double* S, double* v, double* zeta,
+                                double* x, double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (!x0 || !S || !v || !x) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_SEQUENTIAL);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  Coefs cf;
+  if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
+  return from_cuda(launch_sequential(*p, L, cf, x0, S, v, zeta, x, u, cost, (char*)ws + L.coef_bytes, st));
+}
+
+// ---------------------------------------------------------------------------
+// host-buffer call
+// ---------------------------------------------------------------------------
+
+static size_t coef_bytes_of(const lqt_coef& c, const lqt_problem& p, size_t per_sample) {
+  if (!c.ptr) return 0;
+  return (size_t)sample_count(c.mode, p.T, p.K) * per_sample * sizeof(double);
+}
+
+size_t lqt_host_staging_size(const lqt_problem* p) {
+  if (validate(p) != LQT_OK) return 0;
+  const size_t n = p->n, m = p->m, nr = p->nr, T1 = (size_t)p->T + 1;
+  size_t b = align_up(T1 * 8);
+  b += align_up(coef_bytes_of(p->F, *p, n * n)) + align_up(coef_bytes_of(p->L, *p, n * m)) +
+       align_up(coef_bytes_of(p->c, *p, n)) + align_up(coef_bytes_of(p->H, *p, nr * n)) +
+       align_up(coef_bytes_of(p->X, *p, nr * nr)) + align_up(coef_bytes_of(p->U, *p, m * m)) +
+       align_up(coef_bytes_of(p->r, *p, nr));
+  b += align_up(nr * n * 8) + align_up(nr * nr * 8) + align_up(nr * 8) + align_up(n * 8);
+  // outputs: S, v, zeta, x, u, cost
+  b += align_up(T1 * n * n * 8) + align_up(T1 * n * 8) + align_up(T1 * 8) + align_up(T1 * n * 8) +
+       align_up(T1 * m * 8) + 256;
+  return b;
+}
+
+lqt_status lqt_solve_host(const lqt_problem* hp, const double* x0, double* S, double* v, double* zeta, double* x,
+                          double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
+  lqt_status s = validate(hp);
+  if (s != LQT_OK) return s;
+  if (!x0 || !S || !v || !x) return LQT_EINVAL;
+  const size_t solve_ws = lqt_workspace_size(hp, LQT_WS_SOLVE);
+  const size_t staging = lqt_host_staging_size(hp);
+  if (!ws || ws_bytes < solve_ws + staging) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = hp->n, m = hp->m, nr = hp->nr, T1 = (size_t)hp->T + 1;
+  char* cur = (char*)ws + align_up(solve_ws);
+  cudaError_t e = cudaSuccess;
+  auto stage = [&](const void* src, size_t bytes) -> const double* {
+    if (!src || bytes == 0) return nullptr;
+    char* dst = cur;
+    cur += align_up(bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    return (const double*)dst;
+  };
+  lqt_problem d = *hp;
+  d.t = stage(hp->t, T1 * 8);
+  d.F.ptr = stage(hp->F.ptr, coef_bytes_of(hp->F, *hp, n * n));
+  d.L.ptr = stage(hp->L.ptr, coef_bytes_of(hp->L, *hp, n * m));
+  d.c.ptr = stage(hp->c.ptr, coef_bytes_of(hp->c, *hp, n));
+  d.H.ptr = stage(hp->H.ptr, coef_bytes_of(hp->H, *hp, nr * n));
+  d.X.ptr = stage(hp->X.ptr, coef_bytes_of(hp->X, *hp, nr * nr));
+  d.U.ptr = stage(hp->U.ptr, coef_bytes_of(hp->U, *hp, m * m));
+  d.r.ptr = stage(hp->r.ptr, coef_bytes_of(hp->r, *hp, nr));
+  d.Hf = stage(hp->Hf, nr * n * 8);
+  d.Xf = stage(hp->Xf, nr * nr * 8);
+  d.rf = stage(hp->rf, nr * 8);
+  const double* dx0 = stage(x0, n * 8);
+  auto carve = [&](size_t bytes) {
+    double* p = (double*)cur;
+    cur += align_up(bytes);
+    return p;
+  };
+  double* dS = carve(T1 * n * n * 8);
+  double* dv = carve(T1 * n * 8);
+  double* dz = carve(T1 * 8);
+  double* dxo = carve(T1 * n * 8);
+  double* du = carve(T1 * m * 8);
+  double* dc = carve(8);
+  if (e != cudaSuccess) return LQT_ECUDA;
+  s = lqt_solve(&d, dx0, dS, dv, dz, dxo, u ? du : nullptr, dc, ws, solve_ws, stream);
+  if (s != LQT_OK) return s;
+  e = cudaMemcpyAsync(S, dS, T1 * n * n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, T1 * n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && zeta) e = cudaMemcpyAsync(zeta, dz, T1 * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x, dxo, T1 * n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, T1 * m * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && cost) e = cudaMemcpyAsync(cost, dc, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return from_cuda(e);
+}
+
+// ---------------------------------------------------------------------------
+// status
+// ---------------------------------------------------------------------------
+
+lqt_status lqt_get_status(void* stream, int32_t timeout_ms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(st);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return LQT_ECUDA;
+    if (timeout_ms >= 0) {
+      const auto ms =
+          std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (ms > timeout_ms) return LQT_ETIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  unsigned word = 0;
+  if (cudaMemcpyFromSymbol(&word, g_status_word, sizeof(word)) != cudaSuccess) return LQT_ECUDA;
+  const unsigned zero = 0;
+  if (cudaMemcpyToSymbol(g_status_word, &zero, sizeof(zero)) != cudaSuccess) return LQT_ECUDA;
+  if (word & kStatusNonFinite) return LQT_ENONFINITE;
+  if (word & kStatusSingular) return LQT_ESINGULAR;
+  return LQT_OK;
+}
+
+const char* lqt_strerror(lqt_status s) {
+  switch (s) {
+    case LQT_OK: return "ok";
+    case LQT_EINVAL: return "invalid argument";
+    case LQT_EWORKSPACE: return "workspace missing or too small";
+    case LQT_ENONFINITE: return "non-finite value produced on the device";
+    case LQT_ESINGULAR: return "singular matrix met on the device";
+    case LQT_ETIMEOUT: return "timed out waiting for the stream";
+    case LQT_ECUDA: return "CUDA runtime error";
+    case LQT_EUNSUPPORTED: return "dimension not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int32_t lqt_last_launch_count(void) { return t_launches; }
+
+}  // extern "C"

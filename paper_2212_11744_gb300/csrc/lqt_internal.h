@@ -1,0 +1,110 @@
+// Internal declarations shared by the CUDA translation units of the LQT
+// library (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lqt.h"
+
+namespace lqt {
+
+// Device status word bits (read and cleared by lqt_get_status).
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusSingular = 2u;
+
+extern __device__ unsigned g_status_word;
+
+// Internal sampling modes of derived coefficients.  The public ones keep their
+// values; STAGE_BLOCK holds (2K+1) samples per sub-interval without sharing
+// the end points (needed when a per-stage input is combined with a
+// per-interval one).
+enum : int32_t { kConst = 0, kPerInterval = 1, kPerStage = 2, kStageBlock = 3 };
+
+__host__ __device__ __forceinline__ int64_t sample_index(int32_t mode, int64_t j, int32_t p, int32_t K) {
+  switch (mode) {
+    case kConst: return 0;
+    case kPerInterval: return j;
+    case kPerStage: return 2 * (int64_t)K * j + p;
+    default: return (2 * (int64_t)K + 1) * j + p;
+  }
+}
+
+// Number of samples a mode holds.
+__host__ __device__ __forceinline__ int64_t sample_count(int32_t mode, int64_t T, int32_t K) {
+  switch (mode) {
+    case kConst: return 1;
+    case kPerInterval: return T;
+    case kPerStage: return 2 * (int64_t)K * T + 1;
+    default: return (2 * (int64_t)K + 1) * T;
+  }
+}
+
+struct Coef {
+  const double* ptr;
+  int32_t mode;
+};
+
+// Coefficients in the form the kernels consume (all device pointers):
+//   F   n x n                       (input)
+//   c   n, NULL = 0                 (input)
+//   Lt  n x M: B = L U^-1 L^T = Lt Lt^T (Lt = L R^-T, U = R R^T), zero-padded
+//       to M columns                (derived)
+//   Q   packed upper triangle of H^T X H (derived)
+//   qr  [H^T X r (n), r^T X r]      (derived, n+1 per sample)
+//   Ku  U^-1 L^T (m x n) at the T+1 boundaries (derived; CONST or T+1)
+struct Coefs {
+  Coef F, c, Lt, Q, qr;
+  const double* Ku;
+  int32_t Ku_per_boundary;
+  int32_t M;  // padded column count of Lt
+};
+
+struct ElemPtrs {
+  double *A, *b, *C, *eta, *J, *zeta;
+};
+
+// Sizes of the internal arrays of one problem.
+struct Layout {
+  int32_t n, m, nr, K, M;
+  int64_t T;
+  int32_t mode_Lt, mode_Q, mode_qr;
+  // byte offsets inside the workspace
+  size_t off_Lt, off_Q, off_qr, off_Ku, off_status;
+  size_t coef_bytes;  // end of the coefficient region
+};
+
+// Padded factor width for m.
+inline int32_t padded_M(int32_t m) { return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 64; }
+
+// Combined sampling mode of a derived coefficient from its inputs' modes.
+inline int32_t combine_modes(int32_t a, int32_t b) {
+  if (a == kConst) return b;
+  if (b == kConst) return a;
+  if (a == b) return a;
+  return kStageBlock;  // one per-interval, one per-stage (or already block)
+}
+
+// Launch-count accounting (per host thread).
+void count_launch(int k = 1);
+
+// -------------------------------------------------------------------------
+// launchers (defined in the .cu files, dispatched on n)
+// -------------------------------------------------------------------------
+cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* ws, Coefs& out, cudaStream_t s);
+cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                         cudaStream_t s);
+cudaError_t launch_terminal_values(const lqt_problem& p, double* J, double* eta, double* zeta, cudaStream_t s);
+
+size_t scan_workspace_bytes(int32_t n, int64_t T, bool with_traj);
+cudaError_t run_value_and_traj(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& el,
+                               double* S, double* v, double* zeta, const double* x0, double* x, double* u,
+                               double* cost, bool do_value, bool do_traj, const double* S_in, const double* v_in,
+                               char* ws, size_t ws_bytes, cudaStream_t s);
+size_t sequential_workspace_bytes(int32_t n, int64_t T, int32_t K);
+cudaError_t launch_sequential(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* x0,
+                              double* S, double* v, double* zeta, double* x, double* u, double* cost, char* ws,
+                              cudaStream_t s);
+
+}  // namespace lqt

@@ -1,0 +1,583 @@
+// Stages (b) and (c): the reverse scan of the elements with the LQT
+// combination (Sec. III-D Theorem parallel_HJB, Sec. IV-A eq. lqt_comb) and the
+// forward scan of the one-sub-interval affine maps of the optimal state
+// (Sec. IV-E, Method 1 combination eqs. Psi_comb/alpha_comb).
+//
+// Both scans are chunked and hierarchical instead of a Blelloch up/down sweep
+// over single elements:
+//   level 0: each thread owns a chunk of G0 consecutive elements;
+//   reduce : each thread folds its group (right to left) into one aggregate,
+//            giving the next level's elements;
+//   top    : one group left -> fold it sequentially from the zero value;
+//   down   : each thread re-folds its group in VALUE form, starting from the
+//            suffix value of everything to its right (read from the level
+//            above).  A value-form combination costs about 40% of a full one
+//            and yields the optimal-state map of that sub-interval for free.
+// Level 0 uses long chunks (the wide level, throughput-bound); upper levels
+// use pairs (they are latency-bound: on this GPU one FP64 warp instruction
+// occupies a sub-partition for ~62 cycles whatever the lane count, so the
+// critical path is what counts there).
+#include <cuda_runtime.h>
+
+#include "lqt_device.cuh"
+#include "lqt_internal.h"
+
+namespace lqt {
+
+constexpr int kUpperGroup = 2;
+
+// Level-0 chunk length from T: longest power of two <= 32 that still leaves
+// >= 16384 chunks (so every sub-partition has a warp), at least 2.
+static int level0_group(int64_t T) {
+  int g = 2;
+  while (g < 32 && (T + 1) / (2 * g) >= 16384) g *= 2;
+  return g;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+// element source abstraction: public SoA (level 0) or packed records
+// ---------------------------------------------------------------------------
+
+template <int N>
+struct SrcPublic {
+  ElemPtrs el;
+  __device__ __forceinline__ void load(int64_t k, Elem<N>& e) const { load_public<N>(el, k, e); }
+};
+template <int N>
+struct SrcPacked {
+  const double* p;
+  __device__ __forceinline__ void load(int64_t k, Elem<N>& e) const {
+    load_packed<N>(p + k * packed_elem_doubles<N>(), e);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// value scan kernels
+// ---------------------------------------------------------------------------
+
+// agg[g] = e[gG] (x) e[gG+1] (x) ... (x) e[min(gG+G, cnt)-1]
+template <int N, class Src>
+__global__ void __launch_bounds__(128) reduce_elems_kernel(Src src, int64_t cnt, int G, double* __restrict__ agg) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first >= cnt) return;
+  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+  Elem<N> acc, e;
+  src.load(last, acc);
+  for (int64_t k = last - 1; k >= first; --k) {
+    src.load(k, e);
+    combine<N>(e, acc, acc);
+  }
+  store_packed<N>(agg + g * packed_elem_doubles<N>(), acc);
+}
+
+struct DownOut {
+  // packed value output (levels >= 1)
+  double* vals;
+  // level-0 outputs (public layout); zeta may be null
+  double *S, *v, *zeta;
+  // level-0 optimal-state maps and chunk composites (may be null)
+  double* maps;       // [T][N*N + N]
+  double* composite;  // [chunks-1][N*N + N]
+  int64_t T;
+};
+
+template <int N>
+__device__ __forceinline__ void store_val_public(const DownOut& o, int64_t k, const Val<N>& V) {
+  double* S = o.S + k * N * N;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) S[i * N + j] = V.S[sidx<N>(i, j)];
+#pragma unroll
+  for (int i = 0; i < N; ++i) o.v[k * N + i] = V.v[i];
+  if (o.zeta) o.zeta[k] = V.zeta;
+  bool ok = isfinite(V.zeta);
+#pragma unroll
+  for (int i = 0; i < Dim<N>::NS; ++i) ok = ok && isfinite(V.S[i]);
+  if (!ok) flag(kStatusNonFinite);
+}
+
+// Suffix values of one group, right to left, from the carry `above` (the
+// value of everything after the group; zero value at the right end).
+template <int N, class Src, bool Level0>
+__global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, int G, const double* __restrict__ above,
+                                                          int64_t cnt_above, DownOut o) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first >= cnt) return;
+  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+  Val<N> carry;
+  if (above != nullptr && g + 1 < cnt_above)
+    load_val<N>(above + (g + 1) * packed_val_doubles<N>(), carry);
+  else
+    zero_val<N>(carry);
+  // composite of the maps of this chunk (x_{first} -> x_{last+1})
+  double P[N * N], pv[N];
+  constexpr int PM = N * N + N;
+  if (Level0) {
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) P[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) pv[i] = 0.0;
+  }
+  Elem<N> e;
+  Val<N> nv;
+  double Psi[N * N], alpha[N];
+  for (int64_t k = last; k >= first; --k) {
+    src.load(k, e);
+    combine_value<N>(e, carry, nv, Psi, alpha);
+    if (Level0) {
+      store_val_public<N>(o, k, nv);
+      if (o.maps != nullptr && k < o.T) {
+        double* mp = o.maps + k * PM;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) mp[i] = Psi[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) mp[N * N + i] = alpha[i];
+        // (P, pv) <- (P Psi, P alpha + pv)
+        double P2[N * N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          double s = pv[i];
+#pragma unroll
+          for (int l = 0; l < N; ++l) s = fma(P[i * N + l], alpha[l], s);
+          pv[i] = s;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            double t = 0.0;
+#pragma unroll
+            for (int l = 0; l < N; ++l) t = fma(P[i * N + l], Psi[l * N + j], t);
+            P2[i * N + j] = t;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) P[i] = P2[i];
+      }
+    } else {
+      store_val<N>(o.vals + k * packed_val_doubles<N>(), nv);
+    }
+    carry = nv;
+  }
+  if (Level0 && o.composite != nullptr && last + 1 <= o.T) {
+    // chunk g maps x_{first} to x_{last+1}; only chunks that end at or before T
+    double* cp = o.composite + g * PM;
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) cp[i] = P[i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) cp[N * N + i] = pv[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// affine-map (trajectory) scan kernels
+// ---------------------------------------------------------------------------
+
+// comp[g] = map[last] o ... o map[first]  (apply first map first)
+template <int N>
+__global__ void __launch_bounds__(128) reduce_maps_kernel(const double* __restrict__ maps, int64_t cnt, int G,
+                                                          double* __restrict__ comp) {
+  constexpr int PM = N * N + N;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first >= cnt) return;
+  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+  double P[N * N], p[N];
+  const double* m0 = maps + first * PM;
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) P[i] = m0[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) p[i] = m0[N * N + i];
+  for (int64_t k = first + 1; k <= last; ++k) {
+    const double* mk = maps + k * PM;
+    double Ps[N * N], ps[N];
+    // x -> Psi_k (P x + p) + alpha_k
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = mk[N * N + i];
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(mk[i * N + l], p[l], s);
+      ps[i] = s;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        double t = 0.0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) t = fma(mk[i * N + l], P[l * N + j], t);
+        Ps[i * N + j] = t;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) P[i] = Ps[i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = ps[i];
+  }
+  double* out = comp + g * PM;
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) out[i] = P[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[N * N + i] = p[i];
+}
+
+// starts[i] for i in group g: starts[first] = above[g] (or x_in at the top),
+// starts[i+1] = map_i(starts[i]); the group holding the last map also writes
+// starts[cnt].
+template <int N>
+__global__ void __launch_bounds__(128) down_maps_kernel(const double* __restrict__ maps, int64_t cnt, int G,
+                                                        const double* __restrict__ above,
+                                                        const double* __restrict__ x_in,
+                                                        double* __restrict__ starts) {
+  constexpr int PM = N * N + N;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first >= cnt) return;
+  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+  double x[N];
+  const double* xs = above ? above + g * N : x_in;
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = xs[i];
+  for (int64_t k = first; k <= last; ++k) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) starts[k * N + i] = x[i];
+    const double* mk = maps + k * PM;
+    double y[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = mk[N * N + i];
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(mk[i * N + l], x[l], s);
+      y[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = y[i];
+  }
+  if (last == cnt - 1) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) starts[cnt * N + i] = x[i];
+  }
+}
+
+// Optimal-state maps of the sub-intervals of one chunk from given S, v
+// (standalone trajectory call), with the chunk composite.
+template <int N>
+__global__ void __launch_bounds__(128) maps_from_values_kernel(SrcPublic<N> src, int64_t T, int G,
+                                                               const double* __restrict__ S,
+                                                               const double* __restrict__ v, double* maps,
+                                                               double* composite) {
+  constexpr int PM = N * N + N;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first > T) return;
+  const int64_t last = (first + G < T + 1 ? first + G : T + 1) - 1;
+  double P[N * N], pv[N];
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) P[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) pv[i] = 0.0;
+  Elem<N> e;
+  Val<N> V, nv;
+  double Psi[N * N], alpha[N];
+  for (int64_t k = (last < T ? last : T - 1); k >= first; --k) {
+    src.load(k, e);
+    const double* Sk = S + (k + 1) * N * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = i; j < N; ++j) V.S[sidx<N>(i, j)] = 0.5 * (Sk[i * N + j] + Sk[j * N + i]);
+#pragma unroll
+    for (int i = 0; i < N; ++i) V.v[i] = v[(k + 1) * N + i];
+    V.zeta = 0.0;
+    combine_value<N>(e, V, nv, Psi, alpha);
+    double* mp = maps + k * PM;
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) mp[i] = Psi[i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) mp[N * N + i] = alpha[i];
+    double P2[N * N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = pv[i];
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(P[i * N + l], alpha[l], s);
+      pv[i] = s;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        double t = 0.0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) t = fma(P[i * N + l], Psi[l * N + j], t);
+        P2[i * N + j] = t;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) P[i] = P2[i];
+  }
+  if (last + 1 <= T) {
+    double* cp = composite + g * PM;
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) cp[i] = P[i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) cp[N * N + i] = pv[i];
+  }
+}
+
+// Level-0 apply: states of every boundary in chunk g from its start state,
+// controls u_k = Ku (v_k - S_k x_k), and (thread 0) the optimal cost.
+template <int N>
+__global__ void __launch_bounds__(128) final_traj_kernel(const double* __restrict__ maps, int64_t T, int G,
+                                                         const double* __restrict__ starts1,
+                                                         const double* __restrict__ x0,
+                                                         const double* __restrict__ S,
+                                                         const double* __restrict__ v,
+                                                         const double* __restrict__ zeta, const double* __restrict__ Ku,
+                                                         int32_t Ku_per_boundary, int32_t m, double* __restrict__ x,
+                                                         double* __restrict__ u, double* __restrict__ cost) {
+  constexpr int PM = N * N + N;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first > T) return;
+  const int64_t last = (first + G < T + 1 ? first + G : T + 1) - 1;
+  double xc[N];
+  const double* xs = starts1 ? starts1 + g * N : x0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) xc[i] = xs[i];
+  bool ok = true;
+  for (int64_t k = first; k <= last; ++k) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      x[k * N + i] = xc[i];
+      ok = ok && isfinite(xc[i]);
+    }
+    if (u != nullptr) {
+      double e[N];
+      const double* Sk = S + k * N * N;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        double s = v[k * N + i];
+#pragma unroll
+        for (int l = 0; l < N; ++l) s = fma(-Sk[i * N + l], xc[l], s);
+        e[i] = s;
+      }
+      const double* Kk = Ku + (Ku_per_boundary ? k * m * N : 0);
+      for (int a = 0; a < m; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) s = fma(Kk[a * N + l], e[l], s);
+        u[k * m + a] = s;
+      }
+    }
+    if (k < T) {
+      const double* mk = maps + k * PM;
+      double y[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        double s = mk[N * N + i];
+#pragma unroll
+        for (int l = 0; l < N; ++l) s = fma(mk[i * N + l], xc[l], s);
+        y[i] = s;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) xc[i] = y[i];
+    }
+  }
+  if (!ok) flag(kStatusNonFinite);
+  if (g == 0 && cost != nullptr) {
+    // V(x0, t0) = zeta_0 + 1/2 x0'S_0 x0 - v_0'x0
+    double c = zeta ? zeta[0] : 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(S[i * N + l], x0[l], s);
+      c = fma(x0[i], fma(0.5, s, -v[i]), c);
+    }
+    *cost = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+
+static unsigned blocks_for(int64_t threads) { return (unsigned)ceil_div(threads, 128); }
+
+// Workspace plan of the scans (byte offsets from the scan region start).
+struct ScanPlan {
+  int G0;
+  int64_t T;
+  // value levels >= 1
+  int nlev;
+  int64_t cnt[64];
+  size_t off_agg[64], off_val[64];
+  // trajectory
+  size_t off_maps;  // level-0 maps [T]
+  int tlev;
+  int64_t tcnt[64];                 // number of maps at trajectory level l (l >= 1)
+  size_t off_tmap[64], off_tstart[64];
+  size_t bytes;
+};
+
+template <int N>
+static ScanPlan make_plan(int64_t T, bool with_traj) {
+  ScanPlan pl;
+  pl.G0 = level0_group(T);
+  pl.T = T;
+  size_t off = 0;
+  const size_t PE = sizeof(double) * packed_elem_doubles<N>();
+  const size_t PV = sizeof(double) * packed_val_doubles<N>();
+  const size_t PM = sizeof(double) * (N * N + N);
+  int64_t c = T + 1;
+  int G = pl.G0;
+  pl.nlev = 0;
+  while (c > G) {
+    const int64_t nc = ceil_div(c, G);
+    pl.cnt[pl.nlev] = nc;
+    pl.off_agg[pl.nlev] = off;
+    off = align_up(off + nc * PE);
+    pl.off_val[pl.nlev] = off;
+    off = align_up(off + nc * PV);
+    ++pl.nlev;
+    c = nc;
+    G = kUpperGroup;
+  }
+  pl.off_maps = off;
+  pl.tlev = 0;
+  if (with_traj) {
+    off = align_up(off + (size_t)T * PM);
+    // level-1 maps: chunk composites, one per level-0 chunk that ends <= T
+    int64_t mc = ceil_div(T + 1, pl.G0) - 1;
+    while (mc > 0) {
+      pl.tcnt[pl.tlev] = mc;
+      pl.off_tmap[pl.tlev] = off;
+      off = align_up(off + mc * PM);
+      pl.off_tstart[pl.tlev] = off;
+      off = align_up(off + (mc + 1) * sizeof(double) * N);
+      ++pl.tlev;
+      if (mc <= kUpperGroup) break;
+      mc = ceil_div(mc, kUpperGroup);
+    }
+  }
+  pl.bytes = align_up(off);
+  return pl;
+}
+
+template <int N>
+static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& out0, char* ws, cudaStream_t st) {
+  const int64_t T = pl.T;
+  SrcPublic<N> s0{el};
+  // reduce up the levels
+  int64_t c = T + 1;
+  int G = pl.G0;
+  for (int l = 0; l < pl.nlev; ++l) {
+    double* agg = (double*)(ws + pl.off_agg[l]);
+    if (l == 0) {
+      reduce_elems_kernel<N, SrcPublic<N>><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, G, agg);
+    } else {
+      SrcPacked<N> sp{(const double*)(ws + pl.off_agg[l - 1])};
+      reduce_elems_kernel<N, SrcPacked<N>><<<blocks_for(pl.cnt[l]), 128, 0, st>>>(sp, c, G, agg);
+    }
+    count_launch();
+    c = pl.cnt[l];
+    G = kUpperGroup;
+  }
+  // down the levels: top level first (one group, zero carry)
+  for (int l = pl.nlev; l >= 0; --l) {
+    const int Gl = (l == 0) ? pl.G0 : kUpperGroup;
+    const int64_t cl = (l == 0) ? T + 1 : pl.cnt[l - 1];
+    const double* above = (l < pl.nlev) ? (const double*)(ws + pl.off_val[l]) : nullptr;
+    const int64_t cabove = (l < pl.nlev) ? pl.cnt[l] : 0;
+    const int64_t groups = ceil_div(cl, Gl);
+    if (l == 0) {
+      down_values_kernel<N, SrcPublic<N>, true><<<blocks_for(groups), 128, 0, st>>>(s0, cl, Gl, above, cabove, out0);
+    } else {
+      SrcPacked<N> sp{(const double*)(ws + pl.off_agg[l - 1])};
+      DownOut o{};
+      o.vals = (double*)(ws + pl.off_val[l - 1]);
+      o.T = T;
+      down_values_kernel<N, SrcPacked<N>, false><<<blocks_for(groups), 128, 0, st>>>(sp, cl, Gl, above, cabove, o);
+    }
+    count_launch();
+  }
+}
+
+template <int N>
+static void traj_scan(const ScanPlan& pl, const double* x0, const double* S, const double* v, const double* zeta,
+                      const Coefs& cf, int32_t m, double* x, double* u, double* cost, char* ws, cudaStream_t st) {
+  const int64_t T = pl.T;
+  const double* maps0 = (const double*)(ws + pl.off_maps);
+  // reduce the chunk composites up the trajectory levels
+  for (int l = 1; l < pl.tlev; ++l) {
+    reduce_maps_kernel<N><<<blocks_for(pl.tcnt[l]), 128, 0, st>>>((const double*)(ws + pl.off_tmap[l - 1]),
+                                                                    pl.tcnt[l - 1], kUpperGroup,
+                                                                    (double*)(ws + pl.off_tmap[l]));
+    count_launch();
+  }
+  // starts down the levels
+  for (int l = pl.tlev - 1; l >= 0; --l) {
+    const double* above = (l + 1 < pl.tlev) ? (const double*)(ws + pl.off_tstart[l + 1]) : nullptr;
+    const int G = (l + 1 < pl.tlev) ? kUpperGroup : (int)pl.tcnt[l];
+    down_maps_kernel<N><<<blocks_for(ceil_div(pl.tcnt[l], G)), 128, 0, st>>>(
+        (const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G, above, x0, (double*)(ws + pl.off_tstart[l]));
+    count_launch();
+  }
+  const double* starts1 = pl.tlev > 0 ? (const double*)(ws + pl.off_tstart[0]) : nullptr;
+  final_traj_kernel<N><<<blocks_for(ceil_div(T + 1, pl.G0)), 128, 0, st>>>(
+      maps0, T, pl.G0, starts1, x0, S, v, zeta, cf.Ku, cf.Ku_per_boundary, m, x, u, cost);
+  count_launch();
+}
+
+template <int N>
+static cudaError_t run_n(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
+                         double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
+                         bool do_traj, char* ws, cudaStream_t st) {
+  const ScanPlan pl = make_plan<N>(p.T, do_traj);
+  double* maps0 = (double*)(ws + pl.off_maps);
+  double* comp1 = pl.tlev > 0 ? (double*)(ws + pl.off_tmap[0]) : nullptr;
+  if (do_value) {
+    DownOut o{};
+    o.S = S; o.v = v; o.zeta = zeta; o.T = p.T;
+    o.maps = do_traj ? maps0 : nullptr;
+    o.composite = do_traj ? comp1 : nullptr;
+    value_scan<N>(pl, el, o, ws, st);
+  } else if (do_traj) {
+    SrcPublic<N> s0{el};
+    maps_from_values_kernel<N><<<blocks_for(ceil_div(p.T + 1, pl.G0)), 128, 0, st>>>(s0, p.T, pl.G0, S, v, maps0,
+                                                                                     comp1);
+    count_launch();
+  }
+  if (do_traj) traj_scan<N>(pl, x0, S, v, zeta, cf, p.m, x, u, cost, ws, st);
+  return cudaGetLastError();
+}
+
+size_t scan_workspace_bytes(int32_t n, int64_t T, bool with_traj) {
+  switch (n) {
+    case 1: return make_plan<1>(T, with_traj).bytes;
+    case 2: return make_plan<2>(T, with_traj).bytes;
+    case 3: return make_plan<3>(T, with_traj).bytes;
+    case 4: return make_plan<4>(T, with_traj).bytes;
+    case 8: return make_plan<8>(T, with_traj).bytes;
+    default: return 0;
+  }
+}
+
+cudaError_t run_value_and_traj(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& el,
+                               double* S, double* v, double* zeta, const double* x0, double* x, double* u,
+                               double* cost, bool do_value, bool do_traj, const double* S_in, const double* v_in,
+                               char* ws, size_t ws_bytes, cudaStream_t st) {
+  (void)lay;
+  (void)ws_bytes;
+  double* Sx = do_value ? S : const_cast<double*>(S_in);
+  double* vx = do_value ? v : const_cast<double*>(v_in);
+  switch (p.n) {
+    case 1: return run_n<1>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    case 2: return run_n<2>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    case 3: return run_n<3>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    case 4: return run_n<4>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    case 8: return run_n<8>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lqt

@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads and exports every symbol include/lqt.h
+declares; host-side validation rejects bad arguments before any launch.  CPU
+only (no compute calls)."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lqt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqt_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2212_11744_gb300 import build as B
+    path = B.build()
+    import paper_2212_11744_gb300 as m
+    assert os.path.samefile(path, m.library_path())
+    return ct.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    funcs = header_functions()
+    assert len(funcs) >= 10
+    for f in funcs:
+        assert hasattr(lib, f), f
+    from paper_2212_11744_gb300 import _abi
+    assert set(_abi.EXPORTED) == set(funcs)
+
+
+def _problem(**over):
+    import paper_2212_11744_gb300 as m
+    p = W.point_mass_2d(T=16, K=2)
+    for k, v in over.items():
+        setattr(p, k, v)
+    return m.HostProblem(p, pinned=False)
+
+
+def test_workspace_sizes_positive_and_ordered(lib):
+    import paper_2212_11744_gb300 as m
+    hp = _problem()
+    sizes = {w: m.lqt_workspace_size(hp, w) for w in range(5)}
+    assert all(s > 0 for s in sizes.values())
+    assert sizes[m.LQT_WS_SOLVE] > sizes[m.LQT_WS_VALUE]
+    assert m.lqt_workspace_size(hp, 99) == 0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    import paper_2212_11744_gb300 as m
+    from paper_2212_11744_gb300 import _abi
+    L = _abi.lib()
+    hp = _problem()
+    dummy = ct.c_void_p(256)
+    # unsupported state dimension
+    hp.struct.n = 5
+    assert m.lqt_workspace_size(hp, m.LQT_WS_SOLVE) == 0
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, dummy, 1 << 30, None) == \
+        _abi.LQT_EUNSUPPORTED
+    hp.struct.n = 4
+    # bad sampling mode
+    hp.struct.r.mode = 7
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, dummy, 1 << 30, None) == \
+        _abi.LQT_EINVAL
+    hp.struct.r.mode = m.LQT_PER_STAGE
+    # T = 0
+    hp.struct.T = 0
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, dummy, 1 << 30, None) == \
+        _abi.LQT_EINVAL
+    hp.struct.T = 16
+    # missing output
+    assert L.lqt_solve(hp.ref(), dummy, None, dummy, None, dummy, None, None, dummy, 1 << 30, None) == \
+        _abi.LQT_EINVAL
+    # workspace too small
+    need = m.lqt_workspace_size(hp, m.LQT_WS_SOLVE)
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, dummy, need - 1, None) == \
+        _abi.LQT_EWORKSPACE
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, None, need, None) == \
+        _abi.LQT_EWORKSPACE
+    # misaligned coefficient pointer
+    good = hp.struct.F.ptr
+    hp.struct.F.ptr = good + 3
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, dummy, need, None) == _abi.LQT_EINVAL
+    hp.struct.F.ptr = good
+    # H absent but nr != n
+    hp.struct.nr = 3
+    assert L.lqt_solve(hp.ref(), dummy, dummy, dummy, None, dummy, None, None, dummy, need, None) == _abi.LQT_EINVAL
+
+
+def test_strerror_names_every_status(lib):
+    import paper_2212_11744_gb300 as m
+    names = {m.lqt_strerror(c) for c in range(8)}
+    assert len(names) == 8 and "unknown status" not in names

@@ -1,0 +1,218 @@
+"""GPU path (through the C ABI) against the oracle, element by element.
+
+Tolerance: relative 1e-9 per output tensor, measured as
+max |gpu - oracle| / max(max |oracle|, floor), the floor (1e-8 of the
+tensor's scale, at least 1e-12) keeping outputs that are identically ~0 from
+dividing by rounding noise.  Both sides use the same discretisation (K RK4
+steps of the element ODEs per sub-interval and the combination rule), so only
+rounding order differs: the GPU's chunked tree and factor form B = Lt Lt^T
+against the oracle's sequential fold and explicit B.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def lqt():
+    import paper_2212_11744_gb300 as m
+    return m
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = np.abs(b).max() if b.size else 0.0
+    den = max(scale, 1e-12)
+    return float(np.abs(a - b).max() / den) if b.size else 0.0
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def check_solution(got, ref, keys=("S", "v", "zeta", "x", "u"), tol=TOL, label=""):
+    errs = {k: relerr(to_np(got[k]), ref[k]) for k in keys}
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, f"{label} relative errors above {tol}: {errs}"
+    return errs
+
+
+CASES = [
+    ("double_integrator_T1024_K10", lambda: W.double_integrator(T=1024, K=10)),
+    ("point_mass_T1000_K4", lambda: W.point_mass_2d(T=1000, K=4)),
+    ("general_n3_m2_nr2_T37", lambda: W.general_time_varying(3, 2, 2, T=37, K=3, seed=21)),
+    ("general_mixed_modes_T45", lambda: W.general_time_varying(
+        4, 2, 3, T=45, K=2, seed=22, modes={"r": W.PER_INTERVAL, "X": W.CONST, "F": W.PER_INTERVAL,
+                                             "L": W.CONST, "U": W.PER_INTERVAL})),
+    ("general_nonuniform_T29", lambda: W.general_time_varying(2, 1, 2, T=29, K=4, seed=23, nonuniform=True)),
+    ("scalar_n1_T50", lambda: W.general_time_varying(1, 1, 1, T=50, K=5, seed=24)),
+    ("n8_m4_T300", lambda: W.batched_member(5, T=300, n=8)),
+    ("n8_m8_T33", lambda: W.general_time_varying(8, 8, 8, T=33, K=2, seed=25, tf=1.0)),
+    ("T1", lambda: W.general_time_varying(3, 1, 3, T=1, K=4, seed=26, tf=0.5)),
+    ("T2", lambda: W.general_time_varying(2, 2, 2, T=2, K=1, seed=27)),
+    ("T3", lambda: W.general_time_varying(4, 2, 4, T=3, K=2, seed=28)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_solve_matches_oracle(name, make):
+    p = make()
+    ref = oracle.solve(p)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    out = m.lqt_solve(dp)
+    torch.cuda.synchronize()
+    assert m.lqt_get_status() == 0
+    check_solution(out, ref, label=name)
+    assert abs(float(out["cost"][0]) - ref["cost"]) <= TOL * max(1.0, abs(ref["cost"]))
+
+
+@pytest.mark.parametrize("name,make", CASES[:8], ids=[c[0] for c in CASES[:8]])
+def test_build_elements_matches_oracle(name, make):
+    p = make()
+    ref = oracle.build_elements(p)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    el = m.lqt_build_elements(dp)
+    torch.cuda.synchronize()
+    for k in ("A", "b", "C", "eta", "J", "zeta"):
+        e = relerr(to_np(el[k]), ref[k])
+        assert e <= 1e-11, (name, k, e)
+
+
+def test_scan_value_on_oracle_elements():
+    """Stage (b) alone, fed the oracle's elements, against the oracle's fold."""
+    p = W.general_time_varying(4, 2, 4, T=211, K=2, seed=31)
+    ref_el = oracle.build_elements(p)
+    S, v, z = oracle.suffix_values(p.n, ref_el)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    el = {k: torch.from_numpy(np.ascontiguousarray(ref_el[k])).cuda() for k in ref_el}
+    out = m.lqt_scan_value(dp, el)
+    torch.cuda.synchronize()
+    assert relerr(to_np(out["S"]), S) <= TOL
+    assert relerr(to_np(out["v"]), v) <= TOL
+    assert relerr(to_np(out["zeta"]), z) <= TOL
+
+
+def test_scan_trajectory_standalone():
+    """Stage (c) alone, fed the oracle's elements and values."""
+    p = W.point_mass_2d(T=517, K=4)
+    ref = oracle.solve(p, keep_elements=True)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    el = {k: torch.from_numpy(np.ascontiguousarray(ref["elements"][k])).cuda() for k in ref["elements"]}
+    S = torch.from_numpy(ref["S"]).cuda()
+    v = torch.from_numpy(ref["v"]).cuda()
+    out = m.lqt_scan_trajectory(dp, el, S, v)
+    torch.cuda.synchronize()
+    assert relerr(to_np(out["x"]), ref["x"]) <= TOL
+    assert relerr(to_np(out["u"]), ref["u"]) <= TOL
+
+
+def test_scan_worked_example_on_gpu():
+    """The paper's all-prefix-sums example (Sec. II-C) through the GPU scans:
+    with n = 1, A = 1, C = J = 0 the combination adds eta (reverse sums) and the
+    affine maps add b (prefix sums).  Exact in FP64."""
+    import os
+    rows = [list(map(float, ln.split())) for ln in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                                     "scan_worked_example.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    a, pre, suf = map(np.array, rows)
+    T = len(a)  # 8 boundaries 0..7 -> treat as T = 7 sub-intervals + terminal
+    p = W.general_time_varying(1, 1, 1, T=T - 1, K=1, seed=1)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    dev = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    el = {"A": dev(np.ones((T, 1, 1))), "b": dev(np.zeros((T, 1))), "C": dev(np.zeros((T, 1, 1))),
+          "eta": dev(a[:, None]), "J": dev(np.zeros((T, 1, 1))), "zeta": dev(np.zeros(T))}
+    out = m.lqt_scan_value(dp, el)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(out["v"])[:, 0], suf)
+    el["b"] = dev(a[:, None])
+    traj = m.lqt_scan_trajectory(dp, el, dev(np.zeros((T, 1, 1))), dev(np.zeros((T, 1))), x0=dev([0.0]))
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(traj["x"])[1:, 0], pre[:-1])
+
+
+SEQ_CASES = [
+    CASES[0], CASES[2],
+    ("mixed_K8", lambda: W.resample(CASES[3][1](), 8)),
+    ("point_mass_T256", lambda: W.point_mass_2d(T=256)),
+]
+
+
+@pytest.mark.parametrize("name,make", SEQ_CASES, ids=[c[0] for c in SEQ_CASES])
+def test_sequential_sweep_matches_oracle(name, make):
+    """The one-thread sequential sweep against the oracle's sequential method
+    (cases where RK4 of the Riccati equation is stable at the given step; at
+    coarser steps both blow up identically, while the per-sub-interval element
+    ODEs of the parallel method, started from the zero-length boundary, stay
+    finite)."""
+    p = make()
+    ref = oracle.sequential(p)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    out = m.lqt_solve_sequential(dp)
+    torch.cuda.synchronize()
+    check_solution(out, ref, label=name)
+
+
+def test_solve_host_matches_device():
+    p = W.point_mass_2d(T=777, K=4)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    dev = m.lqt_solve(dp)
+    hp = m.HostProblem(p)
+    need = m.lqt_workspace_size(hp, m.LQT_WS_SOLVE) + m.lqt_host_staging_size(hp)
+    ws = torch.empty(need + 4096, dtype=torch.uint8, device="cuda")
+    host = m.lqt_solve_host(hp, ws)
+    torch.cuda.synchronize()
+    for k in ("S", "v", "zeta", "x", "u", "cost"):
+        assert np.array_equal(to_np(dev[k]), host[k].numpy()), k
+
+
+def test_nonfinite_input_sets_status():
+    p = W.point_mass_2d(T=64, K=4)
+    p.r.values[100, 0] = np.nan
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    m.lqt_solve(dp)
+    assert m.lqt_get_status() == 3  # LQT_ENONFINITE
+    # the word is cleared by the read
+    p2 = W.point_mass_2d(T=64, K=4)
+    m.lqt_solve(m.DeviceProblem(p2))
+    assert m.lqt_get_status() == 0
+
+
+def test_repeat_calls_are_deterministic():
+    p = W.general_time_varying(4, 2, 4, T=300, K=2, seed=41)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    a = m.lqt_solve(dp)
+    b = m.lqt_solve(dp)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.slow
+def test_point_mass_full_size_against_oracle():
+    """The 2-D point-mass workload at its largest size, T = 2^20 sub-intervals,
+    K = 4, in the launch configuration the benchmark times: every output at
+    every boundary against the full oracle."""
+    p = W.point_mass_2d(T=1 << 20, K=4)
+    m = lqt()
+    dp = m.DeviceProblem(p)
+    out = m.lqt_solve(dp)
+    torch.cuda.synchronize()
+    assert m.lqt_get_status() == 0
+    ref = oracle.solve(p)
+    check_solution(out, ref, label="point_mass_2^20")
