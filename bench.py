@@ -1,0 +1,376 @@
+"""Benchmark of the temporally parallel LQT solver on one GB300 (or N replicas).
+
+Workload: the 2-D point-mass tracking problem (n=4 states, m=2 inputs, the
+paper's F and L of Sec. VI-A), t in [0, 100], T = 2^20 sub-intervals with
+K = 4 RK4 steps each, X(t) and r(t) sampled on the half-step grid (1.35 GB of
+inputs, larger than L2).  One step = one lqt_solve: element build + value scan
++ trajectory scan + controls + optimal cost.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is sub-intervals per second over all ranks with
+inputs resident on the device; `e2e` is the same metric through the host-buffer
+entry point lqt_solve_host with the host<->device copies inside the timed
+region.  Under torchrun every rank solves its own copy of the workload
+(replicas: the method has no cross-GPU exchange at this size).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LQT sub-intervals/s (build+scan+trajectory) vs sequential GPU sweep, same tol"
+UNIT = "sub-intervals/s"
+T_DEFAULT = 1 << 20
+K_STEPS = 4
+FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12  # SMs x sub-partitions x DFMA/clk x flop x max clock
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "build_kernel_point_mass_n4.md")
+
+
+def build_flops_per_block(n: int, m_pad: int, K: int, has_c: bool) -> float:
+    """FP64 operations of one element build (FMA = 2), as the kernel is written:
+    per right-hand side A Lt and J Lt (2 n^2 M), Lt^T eta (n M), dA (n^2 (M+n)),
+    db (n (M + n[c])), dC (n(n+1)/2 M), deta (n (n + M + n[c])), J F (n^3), dJ
+    (n(n+1)/2 (M + 2 adds)), dzeta (M + n[c]); 4 right-hand sides and 7 axpys of
+    the 3n^2/... state (n^2 + n + 2 n(n+1)/2 + n + 1 entries) per RK4 step."""
+    ns = n * (n + 1) // 2
+    c = n if has_c else 0
+    fma = 2 * n * n * m_pad + n * m_pad + n * n * (m_pad + n) + n * (m_pad + c) + ns * m_pad + \
+        n * (n + m_pad + c) + n ** 3 + ns * m_pad + m_pad + c
+    adds = 2 * ns + 2
+    rhs = 2 * fma + adds
+    state = n * n + n + 2 * ns + n + 1
+    step = 4 * rhs + 7 * 2 * state
+    return float(K * step)
+
+
+def scan_flops_per_block(n: int) -> float:
+    """Approximate FP64 work of stages (b)+(c) per sub-interval: one full
+    combination (reduce), one value-form combination with the map, the chunk
+    composition and the state/control update."""
+    full = 2 * (n ** 3 * (1 + 2 + 1 + 1.5 + 1 + 1.5) + 2 * n ** 3 / 3)
+    value = 2 * (n ** 3 * (1 + 1 + 1 + 0.5) + n ** 3 / 3)
+    comp = 2 * n ** 3
+    return float(full + value + comp + 2 * 2 * n * n)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lqt_build.cu", "lqt_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2212_11744_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per build-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    txt = open(PROFILE_TRAFFIC).read()
+    mh = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    mt = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != source_hash():
+        return None
+    return float(mt.group(1))
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+def barrier(ws):
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.zeros(1, device="cuda")
+        dist.all_reduce(t)
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    import torch
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline_sample(p, seconds_hint=True):
+    """Times the oracle (single thread, as it stands) on the first Ts
+    sub-intervals of the workload."""
+    import oracle
+    import workloads as W
+    Ts = min(1 << 19, p.T)
+    sub = W.truncate(p, Ts)
+    t0 = time.perf_counter()
+    oracle.solve(sub)
+    dt = time.perf_counter() - t0
+    return {"value": Ts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {Ts} of the {p.T} sub-intervals (same grid and samples), one solve, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    oracle.build()
+    p = W.point_mass_2d(T=T_DEFAULT, K=K_STEPS)
+    Ts = 1 << 16
+    sub = W.truncate(p, Ts)
+    for _ in range(args.warmup):
+        oracle.solve(sub)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(sub)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = Ts / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(p),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {Ts} of the {p.T} sub-intervals per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def workload_config(p):
+    return {"workload": f"point_mass_2d n={p.n} m={p.m} T={p.T} K={p.K} t=[0,100] X,r per RK4 half-step",
+            "T": p.T, "n": p.n, "m": p.m, "K": p.K,
+            "l2": f"inputs larger than L2 ({p.nbytes_inputs() / 1e9:.2f} GB of coefficient samples)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    import paper_2212_11744_gb300 as lqt
+    import workloads as W
+
+    ws_, rank, local = dist_setup()
+    p = W.point_mass_2d(T=args.T, K=K_STEPS)
+    dp = lqt.DeviceProblem(p)
+    stream = torch.cuda.current_stream()
+    ws = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_SOLVE), dtype=torch.uint8, device="cuda")
+    out = lqt.new_solution(dp)
+
+    def step():
+        lqt.lqt_solve(dp, out=out, ws=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier(ws_)
+    st = lqt.lqt_get_status(stream)
+    if st != 0:
+        raise RuntimeError("device status: " + lqt.lqt_strerror(st))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws_)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches_per_step = lqt.lqt_last_launch_count()
+    ms = max_over_ranks(ms, ws_)
+    value = p.T * ws_ / (ms * 1e-3)
+
+    # dominant stage: element build, timed alone (same stream, events)
+    el = lqt.new_elements(dp)
+    wsb = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_BUILD), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        lqt.lqt_build_elements(dp, out=el, ws=wsb, stream=stream)
+    reps = max(3, args.steps)
+    e0.record(stream)
+    for _ in range(reps):
+        lqt.lqt_build_elements(dp, out=el, ws=wsb, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1) / reps
+    m_pad = 1 if p.m <= 1 else 2 if p.m <= 2 else 4 if p.m <= 4 else 8
+    fl_build = build_flops_per_block(p.n, m_pad, p.K, p.c is not None) * p.T
+    achieved = fl_build / (build_ms * 1e-3) / 1e12
+    del el, wsb
+
+    # end to end through the host-buffer entry point
+    hp = lqt.HostProblem(p, pinned=True)
+    hout = lqt.host_solution(hp, pinned=True)
+    wsh = torch.empty(lqt.lqt_workspace_size(hp, lqt.LQT_WS_SOLVE) + lqt.lqt_host_staging_size(hp) + 4096,
+                      dtype=torch.uint8, device="cuda")
+    lqt.lqt_solve_host(hp, wsh, out=hout, stream=stream)
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier(ws_)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lqt.lqt_solve_host(hp, wsh, out=hout, stream=stream)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws_)
+    h2d = sum(t.numel() * t.element_size() for t in hp.keep)
+    d2h = sum(t.numel() * t.element_size() for t in hout.values())
+    np.testing.assert_array_equal(hout["x"].numpy(), out["x"].cpu().numpy())
+    del wsh
+
+    # sequential one-thread GPU sweep on the first Ts sub-intervals (same grid)
+    Ts = min(2048, p.T)
+    sub = W.truncate(p, Ts)
+    dsub = lqt.DeviceProblem(sub)
+    seq = lqt.lqt_solve_sequential(dsub)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    seq = lqt.lqt_solve_sequential(dsub, out=seq)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    par = lqt.lqt_solve(dsub)
+    # same tolerance: both against a parallel solve with 8x the RK4 steps
+    ref = lqt.lqt_solve(lqt.DeviceProblem(W.resample(sub, 8 * K_STEPS)))
+    torch.cuda.synchronize()
+
+    def err(a):
+        return max(float((a[k] - ref[k]).abs().max() / ref[k].abs().max().clamp_min(1e-12)) for k in ("S", "v", "x"))
+
+    err_par, err_seq = err(par), err(seq)
+
+    if rank == 0:
+        cpu = cpu_baseline_sample(p)
+        traffic = profiled_traffic()
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(p), parallelism=f"replicas x{ws_}"),
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "alu", "kernel": "build_kernel<4,2> (stage a, with its prepare/terminal launches)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "peak_source": "FP64 pipe: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flop x 2.07 GHz",
+                         "stage_ms": build_ms},
+            "e2e": {"value": p.T * ws_ / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "sequential_gpu": {"value": Ts / (seq_ms * 1e-3), "unit": UNIT, "T_timed": Ts,
+                               "speedup_parallel_over_sequential": value / ws_ / (Ts / (seq_ms * 1e-3)),
+                               "rel_err_parallel": err_par, "rel_err_sequential": err_seq,
+                               "tol_note": "both with K=4 on the same grid, errors vs a K=32 parallel solve"},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--T", type=int, default=T_DEFAULT)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

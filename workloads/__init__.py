@@ -367,3 +367,22 @@ def refine(p: Problem, factor: int) -> Problem:
             co[k] = c
     return Problem(name=p.name + f"_x{factor}", n=p.n, m=p.m, nr=p.nr, T=T, K=p.K, t=t, Hf=p.Hf, Xf=p.Xf,
                    rf=p.rf, x0=p.x0, extra=p.extra, funcs=p.funcs, **co)
+
+
+def truncate(p: Problem, Ts: int) -> Problem:
+    """The first Ts sub-intervals of p as a problem of its own (same grid, same
+    coefficient samples, same terminal cost placed at t_Ts).  Used to time a
+    bounded sample of a workload with the same work per sub-interval."""
+    K = p.K
+    co = {}
+    for k, c in p.coefs().items():
+        if c is None:
+            co[k] = None
+        elif c.mode == PER_STAGE:
+            co[k] = Coef(c.values[: 2 * K * Ts + 1], PER_STAGE)
+        elif c.mode == PER_INTERVAL:
+            co[k] = Coef(c.values[:Ts], PER_INTERVAL)
+        else:
+            co[k] = c
+    return Problem(name=p.name + f"_first{Ts}", n=p.n, m=p.m, nr=p.nr, T=Ts, K=K, t=p.t[: Ts + 1].copy(), Hf=p.Hf,
+                   Xf=p.Xf, rf=p.rf, x0=p.x0, extra=p.extra, funcs=p.funcs, **co)
