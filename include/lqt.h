@@ -168,6 +168,31 @@ size_t lqt_host_staging_size(const lqt_problem *p);
 lqt_status lqt_solve_host(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
                           double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free value scan.  The paper has no counterpart: this is a
+ * deployment variant of lqt_scan_value for callers that may not allocate
+ * device memory while they run (a control loop whose memory budget is fixed at
+ * start-up, a plugin inside an application that owns the device allocator) and
+ * so cannot hand in a workspace.  It computes exactly what lqt_scan_value
+ * computes, with the scan's scratch in a fixed array inside the library of
+ * LQT_STATIC_SCRATCH_BYTES bytes, held on every device that loads the library
+ * until the process exits.
+ *  - Problems whose scan needs more scratch than that (see
+ *    lqt_workspace_size(p, LQT_WS_VALUE)) return LQT_EWORKSPACE before any
+ *    launch.  For n = 4 this admits T up to 2^19.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current) and caches it: make that first call before any stream
+ *    capture.
+ *  - All calls share the one array: calls that overlap on the GPU (several
+ *    streams or host threads at once) race and give wrong results.  Nothing
+ *    needs clearing between calls (every scratch byte read is written earlier
+ *    in the same call).
+ *  - Calls no allocator (no cudaMalloc/cudaFree, no library routine that
+ *    allocates).
+ * Arguments as for lqt_scan_value. */
+#define LQT_STATIC_SCRATCH_BYTES (16u << 20)
+lqt_status lqt_scan_value_noalloc(const lqt_problem *p, const lqt_elements *el, double *S, double *v, double *zeta,
+                                  void *stream);
+
 /* Waits for `stream` (polling, at most timeout_ms; < 0 waits forever), then
  * reads and clears the current device's status word.  Returns LQT_OK,
  * LQT_ENONFINITE, LQT_ESINGULAR, LQT_ETIMEOUT or LQT_ECUDA. */

@@ -23,7 +23,7 @@ from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BUILD, LQT
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
-    "lqt_scan_trajectory", "lqt_solve", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
+    "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_solve", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path",
 ]
 
@@ -150,6 +150,18 @@ def lqt_scan_value(dp: DeviceProblem, elements: dict, out: Optional[dict] = None
     _abi.check(_abi.lib().lqt_scan_value(dp.ref(), ct.byref(es), _ptr(out["S"]), _ptr(out["v"]),
                                          _ptr(out.get("zeta")), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
                "lqt_scan_value")
+    return out
+
+
+def lqt_scan_value_noalloc(dp: DeviceProblem, elements: dict, out: Optional[dict] = None, stream=None) -> dict:
+    """lqt_scan_value without a workspace: the scratch is a fixed array inside
+    the library (see include/lqt.h for its size limit and its sharing rules)."""
+    n, T1 = dp.n, dp.T + 1
+    out = out or {"S": _empty(dp, T1, n, n), "v": _empty(dp, T1, n), "zeta": _empty(dp, T1)}
+    es = _elements_struct(elements)
+    _abi.check(_abi.lib().lqt_scan_value_noalloc(dp.ref(), ct.byref(es), _ptr(out["S"]), _ptr(out["v"]),
+                                                 _ptr(out.get("zeta")), _stream_handle(stream)),
+               "lqt_scan_value_noalloc")
     return out
 
 
