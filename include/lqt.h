@@ -106,7 +106,8 @@ enum {
   LQT_WS_VALUE = 1,
   LQT_WS_TRAJ = 2,
   LQT_WS_SOLVE = 3,
-  LQT_WS_SEQUENTIAL = 4
+  LQT_WS_SEQUENTIAL = 4,
+  LQT_WS_BACKWARD = 5
 };
 
 /* Bytes of device workspace the call `which` needs for problem p (host call,
@@ -157,6 +158,30 @@ lqt_status lqt_solve(const lqt_problem *p, const double *x0, double *S, double *
  * interpolant of the backward solution.  Same outputs as lqt_solve. */
 lqt_status lqt_solve_sequential(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta,
                                 double *x, double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* Reverse mode of lqt_solve: gradients of a scalar loss with respect to the
+ * coefficients, given the forward outputs S, v, x of lqt_solve (device) and the
+ * loss's gradients with respect to them: gS [T+1][n][n], gv [T+1][n],
+ * gzeta [T+1], gx [T+1][n] (each may be NULL = zero) and g_cost (host scalar,
+ * the weight of the optimal cost V(x0,t0)).  gu must be NULL (controls are not
+ * differentiated).
+ * Outputs (device, each may be NULL): gF, gL, gX, gU, gr in the layout and
+ * sampling mode of F, L, X, U, r (one gradient per sample); gXf [n][n],
+ * grf [n]; gx0 [n].
+ * The elements and the optimal-state maps are recomputed from the problem and
+ * S, v; the RK4 stages of every sub-interval are recomputed from its start
+ * (checkpointing per sub-interval).  Steps: state adjoint (a reverse linear
+ * recurrence run as a forward affine scan), map adjoint, value adjoint (a
+ * forward congruence scan Sigma_{k+1} = P_k Sigma_k P_k^T + D_{k+1} with the
+ * homogeneous optimal-state maps P_k), element adjoint from the saddle point of
+ * the dual form (Sec. IV-A, eq. LQT_V_form2), and the discrete adjoint of the K
+ * RK4 steps of Theorem Backward_HJB_LQT (Sec. IV-B).
+ * Supported: n <= 8, K <= 8, H = Hf = c = NULL, F, L, X, U constant or per
+ * sub-interval (r any mode); otherwise LQT_EUNSUPPORTED. */
+lqt_status lqt_backward(const lqt_problem *p, const double *x0, const double *S, const double *v, const double *x,
+                        const double *gS, const double *gv, const double *gzeta, const double *gx, const double *gu,
+                        double g_cost, double *gF, double *gL, double *gX, double *gU, double *gr, double *gXf,
+                        double *grf, double *gx0, void *ws, size_t ws_bytes, void *stream);
 
 /* End-to-end convenience call on HOST buffers: the problem's pointers (t, the
  * coefficients, Hf, Xf, rf) and x0 point at host memory, and so do the

@@ -18,13 +18,13 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BUILD, LQT_WS_SEQUENTIAL, LQT_WS_SOLVE,
-                   LQT_WS_TRAJ, LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
+from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, LQT_WS_BUILD, LQT_WS_SEQUENTIAL,
+                   LQT_WS_SOLVE, LQT_WS_TRAJ, LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
     "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_solve", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
-    "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path",
+    "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
 ]
 
 _COEFS = ("F", "L", "c", "H", "X", "U", "r")
@@ -202,6 +202,33 @@ def lqt_solve_sequential(dp: DeviceProblem, x0=None, out: Optional[dict] = None,
                                                _ptr(out.get("zeta")), _ptr(out["x"]), _ptr(out.get("u")),
                                                _ptr(out.get("cost")), ws.data_ptr(), ws.numel(),
                                                _stream_handle(stream)), "lqt_solve_sequential")
+    return out
+
+
+def lqt_backward(dp: DeviceProblem, fwd: dict, gS=None, gv=None, gzeta=None, gx=None, g_cost: float = 0.0,
+                 x0=None, ws=None, stream=None) -> dict:
+    """Gradients of a scalar loss with respect to F, L, X, U, r (in their sample
+    layouts), Xf, rf and x0, given lqt_solve's outputs `fwd` and the loss's
+    gradients with respect to them (see lqt_backward in include/lqt.h)."""
+    x0 = dp.x0 if x0 is None else x0
+    s = dp.struct
+    n, m = dp.n, dp.m
+
+    def samples(c, per):
+        if c.ptr is None:
+            return None
+        cnt = {LQT_CONST: 1, LQT_PER_INTERVAL: dp.T, LQT_PER_STAGE: 2 * dp.K * dp.T + 1}[c.mode]
+        return _empty(dp, cnt, *per)
+
+    out = {"F": samples(s.F, (n, n)), "L": samples(s.L, (n, m)), "X": samples(s.X, (dp.nr, dp.nr)),
+           "U": samples(s.U, (m, m)), "r": samples(s.r, (dp.nr,)), "Xf": _empty(dp, dp.nr, dp.nr),
+           "rf": _empty(dp, dp.nr), "x0": _empty(dp, n)}
+    ws = _workspace(dp, LQT_WS_BACKWARD, ws)
+    _abi.check(_abi.lib().lqt_backward(
+        dp.ref(), _ptr(x0), _ptr(fwd["S"]), _ptr(fwd["v"]), _ptr(fwd["x"]), _ptr(gS), _ptr(gv), _ptr(gzeta), _ptr(gx),
+        None, float(g_cost), _ptr(out["F"]), _ptr(out["L"]), _ptr(out["X"]), _ptr(out["U"]), _ptr(out["r"]),
+        _ptr(out["Xf"]), _ptr(out["rf"]), _ptr(out["x0"]), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+        "lqt_backward")
     return out
 
 

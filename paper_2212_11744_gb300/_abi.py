@@ -14,13 +14,13 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblqt_gb300.so")
 
 LQT_OK, LQT_EINVAL, LQT_EWORKSPACE, LQT_ENONFINITE, LQT_ESINGULAR, LQT_ETIMEOUT, LQT_ECUDA, LQT_EUNSUPPORTED = range(8)
 LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE = 0, 1, 2
-LQT_WS_BUILD, LQT_WS_VALUE, LQT_WS_TRAJ, LQT_WS_SOLVE, LQT_WS_SEQUENTIAL = range(5)
+LQT_WS_BUILD, LQT_WS_VALUE, LQT_WS_TRAJ, LQT_WS_SOLVE, LQT_WS_SEQUENTIAL, LQT_WS_BACKWARD = range(6)
 LQT_STATIC_SCRATCH_BYTES = 16 << 20
 
 EXPORTED = (
     "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value", "lqt_scan_trajectory", "lqt_solve",
     "lqt_solve_sequential", "lqt_host_staging_size", "lqt_solve_host", "lqt_get_status", "lqt_strerror",
-    "lqt_last_launch_count", "lqt_scan_value_noalloc",
+    "lqt_last_launch_count", "lqt_scan_value_noalloc", "lqt_backward",
 )
 
 _dp = ct.POINTER(ct.c_double)
@@ -79,6 +79,8 @@ def lib():
     L.lqt_get_status.argtypes = [v, ct.c_int32]
     L.lqt_strerror.argtypes = [ct.c_int]
     L.lqt_strerror.restype = ct.c_char_p
+    L.lqt_backward.argtypes = [P, v, v, v, v, v, v, v, v, v, ct.c_double, v, v, v, v, v, v, v, v, v, ct.c_size_t, v]
+    L.lqt_backward.restype = ct.c_int
     L.lqt_scan_value_noalloc.argtypes = [P, E, v, v, v, v]
     L.lqt_scan_value_noalloc.restype = ct.c_int
     L.lqt_last_launch_count.argtypes = []

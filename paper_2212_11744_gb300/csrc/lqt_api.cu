@@ -60,7 +60,8 @@ static Layout make_layout(const lqt_problem& p) {
   L.off_Lt = off;
   off = align_up(off + sample_count(L.mode_Lt, p.T, p.K) * (size_t)p.n * L.M * sizeof(double));
   L.off_Q = off;
-  off = align_up(off + sample_count(L.mode_Q, p.T, p.K) * (size_t)(p.n * (p.n + 1) / 2) * sizeof(double));
+  if (p.H.ptr)  // H^T X H is derived only when H is given (otherwise X is used directly)
+    off = align_up(off + sample_count(L.mode_Q, p.T, p.K) * (size_t)p.n * p.n * sizeof(double));
   L.off_qr = off;
   off = align_up(off + sample_count(L.mode_qr, p.T, p.K) * (size_t)(p.n + 1) * sizeof(double));
   L.off_Ku = off;
@@ -88,6 +89,9 @@ static ElemPtrs carve_elements(const lqt_problem& p, char* base) {
   return e;
 }
 
+ElemPtrs carve_elements_at(const lqt_problem& p, char* base) { return carve_elements(p, base); }
+size_t element_region_bytes(const lqt_problem& p) { return element_bytes(p); }
+
 static lqt_status from_cuda(cudaError_t e) { return e == cudaSuccess ? LQT_OK : LQT_ECUDA; }
 
 }  // namespace lqt
@@ -107,6 +111,7 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
     case LQT_WS_SOLVE:
       return L.coef_bytes + element_bytes(*p) + align_up(T1 * 8) + scan_workspace_bytes(p->n, p->T, true);
     case LQT_WS_SEQUENTIAL: return L.coef_bytes + align_up(sequential_workspace_bytes(p->n, p->T, p->K));
+    case LQT_WS_BACKWARD: return backward_workspace_bytes(*p, L, element_bytes(*p)) + 4096;
     default: return 0;
   }
 }
@@ -195,6 +200,33 @@ lqt_status lqt_solve_sequential(const lqt_problem* p, const double* x0, double* 
   Coefs cf;
   if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
   return from_cuda(launch_sequential(*p, L, cf, x0, S, v, zeta, x, u, cost, (char*)ws + L.coef_bytes, st));
+}
+
+static lqt_status validate_backward(const lqt_problem* p) {
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (p->n > 8 || p->K > 8 || p->m > 16) return LQT_EUNSUPPORTED;
+  if (p->H.ptr || p->Hf || p->c.ptr) return LQT_EUNSUPPORTED;
+  const lqt_coef* blockconst[4] = {&p->F, &p->L, &p->X, &p->U};
+  for (const lqt_coef* c : blockconst)
+    if (c->mode == LQT_PER_STAGE) return LQT_EUNSUPPORTED;
+  return LQT_OK;
+}
+
+lqt_status lqt_backward(const lqt_problem* p, const double* x0, const double* S, const double* v, const double* x,
+                        const double* gS, const double* gv, const double* gzeta, const double* gx, const double* gu,
+                        double g_cost, double* gF, double* gL, double* gX, double* gU, double* gr, double* gXf,
+                        double* grf, double* gx0, void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate_backward(p);
+  if (s != LQT_OK) return s;
+  if (gu) return LQT_EUNSUPPORTED;
+  if (!x0 || !S || !v || !x) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_BACKWARD);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  const Layout L = make_layout(*p);
+  return from_cuda(run_backward(*p, L, element_bytes(*p), x0, S, v, x, gS, gv, gzeta, gx, g_cost, gF, gL, gX, gU, gr,
+                                gXf, grf, gx0, (char*)ws, (cudaStream_t)stream));
 }
 
 // ---------------------------------------------------------------------------

@@ -58,9 +58,10 @@ __device__ void cholesky_lower(double* R, int m) {
 constexpr int kMaxM = 16;
 constexpr int kMaxN = 16;
 
-// One thread per derived sample; blockIdx.y selects the quantity.
+// One thread per derived sample; blockIdx.y selects the quantity (with two
+// rows in the grid only Lt and Ku are made).
 __global__ void prepare_kernel(PrepArgs a) {
-  const int which = blockIdx.y;
+  const int which = gridDim.y == 2 ? (blockIdx.y == 0 ? 0 : 3) : blockIdx.y;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int n = a.n, m = a.m, nr = a.nr;
   if (which == 0) {  // Lt = L R^-T, zero-padded to M columns
@@ -81,27 +82,20 @@ __global__ void prepare_kernel(PrepArgs a) {
       }
       for (int c = 0; c < a.M; ++c) out[i * a.M + c] = c < m ? row[c] : 0.0;
     }
-  } else if (which == 1) {  // Q = H^T X H (packed upper)
+  } else if (which == 1) {  // Q = H^T X H (full n x n, symmetrised); only when H is given
     if (s >= a.cnt_Q) return;
     const double* X = a.X.ptr + input_index(a.X.mode, a.mode_Q, s, a.K, a.T) * nr * nr;
-    const double* H = a.H.ptr ? a.H.ptr + input_index(a.H.mode, a.mode_Q, s, a.K, a.T) * nr * n : nullptr;
-    double* out = a.Q + s * (n * (n + 1) / 2);
-    int o = 0;
+    const double* H = a.H.ptr + input_index(a.H.mode, a.mode_Q, s, a.K, a.T) * nr * n;
+    double* out = a.Q + s * (n * n);
     for (int i = 0; i < n; ++i)
       for (int j = i; j < n; ++j) {
-        double v;
-        if (!H) {
-          v = 0.5 * (X[i * nr + j] + X[j * nr + i]);
-        } else {
-          double vij = 0.0, vji = 0.0;
-          for (int k = 0; k < nr; ++k)
-            for (int l = 0; l < nr; ++l) {
-              vij += H[k * n + i] * X[k * nr + l] * H[l * n + j];
-              vji += H[k * n + j] * X[k * nr + l] * H[l * n + i];
-            }
-          v = 0.5 * (vij + vji);
-        }
-        out[o++] = v;
+        double vij = 0.0, vji = 0.0;
+        for (int k = 0; k < nr; ++k)
+          for (int l = 0; l < nr; ++l) {
+            vij += H[k * n + i] * X[k * nr + l] * H[l * n + j];
+            vji += H[k * n + j] * X[k * nr + l] * H[l * n + i];
+          }
+        out[i * n + j] = out[j * n + i] = 0.5 * (vij + vji);
       }
   } else if (which == 2) {  // qr = [H^T X r, r^T X r]
     if (s >= a.cnt_qr) return;
@@ -158,6 +152,47 @@ __global__ void prepare_kernel(PrepArgs a) {
   }
 }
 
+// q = X r, rho = r^T X r per sample when H is the identity (one thread per
+// sample, loops unrolled for the compiled n).
+template <int N>
+__global__ void __launch_bounds__(256) qr_identity_kernel(const double* __restrict__ X, int32_t X_mode,
+                                                          const double* __restrict__ r, int32_t r_mode, int32_t dmode,
+                                                          int64_t cnt, int32_t K, int64_t T, double* __restrict__ qr) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= cnt) return;
+  const double* Xs = X + input_index(X_mode, dmode, s, K, T) * N * N;
+  double rr[N], q[N];
+  if (r) {
+    const double* rs = r + input_index(r_mode, dmode, s, K, T) * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) rr[i] = rs[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) rr[i] = 0.0;
+  }
+  double rho = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double v = 0.0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) v = fma(Xs[i * N + l], rr[l], v);
+    q[i] = v;
+    rho = fma(rr[i], v, rho);
+  }
+  double* out = qr + s * (N + 1);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[i] = q[i];
+  out[N] = rho;
+}
+
+template <int N>
+static void launch_qr_identity(const PrepArgs& a, cudaStream_t st) {
+  const int threads = 256;
+  qr_identity_kernel<N><<<(unsigned)((a.cnt_qr + threads - 1) / threads), threads, 0, st>>>(
+      a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr, a.K, a.T, a.qr);
+  count_launch();
+}
+
 cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* ws, Coefs& cf, cudaStream_t st) {
   PrepArgs a;
   a.n = p.n; a.m = p.m; a.nr = p.nr; a.K = p.K; a.M = lay.M; a.T = p.T;
@@ -176,18 +211,36 @@ cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* 
   a.Q = (double*)(ws + lay.off_Q);
   a.qr = (double*)(ws + lay.off_qr);
   a.Ku = (double*)(ws + lay.off_Ku);
-  int64_t most = a.cnt_Lt;
-  if (a.cnt_Q > most) most = a.cnt_Q;
-  if (a.cnt_qr > most) most = a.cnt_qr;
-  if (a.cnt_Ku > most) most = a.cnt_Ku;
+  // Lt and Ku always; H^T X H only when H is given; H^T X r by the dedicated
+  // kernel when H is the identity.
+  const bool h_identity = p.H.ptr == nullptr;
+  int64_t most = a.cnt_Lt > a.cnt_Ku ? a.cnt_Lt : a.cnt_Ku;
+  if (!h_identity) {
+    if (a.cnt_Q > most) most = a.cnt_Q;
+    if (a.cnt_qr > most) most = a.cnt_qr;
+  }
   const int threads = 128;
   const int64_t blocks = (most + threads - 1) / threads;
-  prepare_kernel<<<dim3((unsigned)blocks, 4), threads, 0, st>>>(a);
-  count_launch();
+  if (h_identity) {
+    // which = 0 (Lt) and 3 (Ku): map blockIdx.y 0 -> 0, 1 -> 3
+    prepare_kernel<<<dim3((unsigned)blocks, 2), threads, 0, st>>>(a);
+    count_launch();
+    switch (p.n) {
+      case 1: launch_qr_identity<1>(a, st); break;
+      case 2: launch_qr_identity<2>(a, st); break;
+      case 3: launch_qr_identity<3>(a, st); break;
+      case 4: launch_qr_identity<4>(a, st); break;
+      case 8: launch_qr_identity<8>(a, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    prepare_kernel<<<dim3((unsigned)blocks, 4), threads, 0, st>>>(a);
+    count_launch();
+  }
   cf.F = {p.F.ptr, p.F.mode};
   cf.c = {p.c.ptr, p.c.ptr ? p.c.mode : kConst};
   cf.Lt = {a.Lt, lay.mode_Lt};
-  cf.Q = {a.Q, lay.mode_Q};
+  cf.Q = h_identity ? Coef{p.X.ptr, p.X.mode} : Coef{a.Q, lay.mode_Q};
   cf.qr = {a.qr, lay.mode_qr};
   cf.Ku = a.Ku;
   cf.Ku_per_boundary = ku_const ? 0 : 1;
@@ -297,7 +350,7 @@ __device__ __forceinline__ void element_rhs(const Elem<N>& y, const double* __re
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      double s = -Q[sidx<N>(i, j)] - JF[i * N + j] - JF[j * N + i];
+      double s = -Q[i * N + j] - JF[i * N + j] - JF[j * N + i];
 #pragma unroll
       for (int a = 0; a < M; ++a) s = fma(P[i * M + a], P[j * M + a], s);
       k.J[sidx<N>(i, j)] = s;
@@ -365,7 +418,6 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
   }
   y.zeta = 0.0;
   const Coefs& cf = a.cf;
-  constexpr int NS = Dim<N>::NS;
   for (int32_t i = K - 1; i >= 0; --i) {
     // stage times (in half steps from t_j): 2i+2, 2i+1, 2i+1, 2i
     const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
@@ -379,7 +431,7 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
       F[q] = coef_at<N>(cf.F, j, ps[q], K, N * N);
       c[q] = cf.c.ptr ? coef_at<N>(cf.c, j, ps[q], K, N) : nullptr;
       Lt[q] = coef_at<N>(cf.Lt, j, ps[q], K, N * M);
-      Q[q] = coef_at<N>(cf.Q, j, ps[q], K, NS);
+      Q[q] = coef_at<N>(cf.Q, j, ps[q], K, N * N);
       qr[q] = coef_at<N>(cf.qr, j, ps[q], K, N + 1);
     }
     element_rhs<N, M>(y, F[0], c[0], Lt[0], Q[0], qr[0], k);

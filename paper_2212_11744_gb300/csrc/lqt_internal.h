@@ -51,7 +51,7 @@ struct Coef {
 //   c   n, NULL = 0                 (input)
 //   Lt  n x M: B = L U^-1 L^T = Lt Lt^T (Lt = L R^-T, U = R R^T), zero-padded
 //       to M columns                (derived)
-//   Q   packed upper triangle of H^T X H (derived)
+//   Q   H^T X H, full n x n (derived; X itself when H is the identity)
 //   qr  [H^T X r (n), r^T X r]      (derived, n+1 per sample)
 //   Ku  U^-1 L^T (m x n) at the T+1 boundaries (derived; CONST or T+1)
 struct Coefs {
@@ -102,6 +102,18 @@ cudaError_t run_value_and_traj(const lqt_problem& p, const Layout& lay, const Co
                                double* S, double* v, double* zeta, const double* x0, double* x, double* u,
                                double* cost, bool do_value, bool do_traj, const double* S_in, const double* v_in,
                                char* ws, size_t ws_bytes, cudaStream_t s);
+size_t affine_scan_bytes(int n, int64_t cnt);
+cudaError_t affine_scan_states(int n, const double* maps, int64_t cnt, const double* x_in, double* states, char* ws,
+                               size_t& off, cudaStream_t st);
+cudaError_t launch_maps_from_values(const lqt_problem& p, const ElemPtrs& el, const double* S, const double* v,
+                                    double* maps, cudaStream_t st);
+ElemPtrs carve_elements_at(const lqt_problem& p, char* base);
+size_t element_region_bytes(const lqt_problem& p);
+size_t backward_workspace_bytes(const lqt_problem& p, const Layout& L, size_t elem_bytes);
+cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_bytes, const double* x0, const double* S,
+                         const double* v, const double* x, const double* gS, const double* gv, const double* gz,
+                         const double* gx, double g_cost, double* gF, double* gL, double* gX, double* gU, double* gr,
+                         double* gXf, double* grf, double* gx0, char* ws, cudaStream_t st);
 size_t sequential_workspace_bytes(int32_t n, int64_t T, int32_t K);
 cudaError_t launch_sequential(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* x0,
                               double* S, double* v, double* zeta, double* x, double* u, double* cost, char* ws,

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(128) maps_from_values_kernel(SrcPublic<N> src,
 #pragma unroll
     for (int i = 0; i < N * N; ++i) P[i] = P2[i];
   }
-  if (last + 1 <= T) {
+  if (composite != nullptr && last + 1 <= T) {
     double* cp = composite + g * PM;
 #pragma unroll
     for (int i = 0; i < N * N; ++i) cp[i] = P[i];
@@ -548,6 +548,97 @@ static cudaError_t run_n(const lqt_problem& p, const Coefs& cf, const ElemPtrs& 
     count_launch();
   }
   if (do_traj) traj_scan<N>(pl, x0, S, v, zeta, cf, p.m, x, u, cost, ws, st);
+  return cudaGetLastError();
+}
+
+// Generic forward affine-map scan: states[0] = x_in, states[k+1] = map_k(states[k])
+// for k < cnt (maps [cnt][N*N+N]), as pairwise reduce levels + down-sweeps.
+template <int N>
+static void affine_scan_n(const double* maps, int64_t cnt, const double* x_in, double* states, char* ws,
+                          size_t& off, cudaStream_t st) {
+  constexpr int PM = N * N + N;
+  const int G = kUpperGroup;
+  int nlev = 0;
+  int64_t c[64];
+  double* lv[64];
+  double* sv[64];
+  int64_t mc = cnt;
+  const double* prev = maps;
+  while (mc > G) {
+    const int64_t nc = ceil_div(mc, G);
+    double* out = (double*)(ws + off);
+    off = align_up(off + nc * PM * sizeof(double));
+    reduce_maps_kernel<N><<<blocks_for(nc), 128, 0, st>>>(prev, mc, G, out);
+    count_launch();
+    c[nlev] = nc;
+    lv[nlev] = out;
+    sv[nlev] = (double*)(ws + off);
+    off = align_up(off + (nc + 1) * N * sizeof(double));
+    prev = out;
+    mc = nc;
+    ++nlev;
+  }
+  {
+    const double* tm = nlev ? lv[nlev - 1] : maps;
+    const int64_t tc = nlev ? c[nlev - 1] : cnt;
+    double* ts = nlev ? sv[nlev - 1] : states;
+    down_maps_kernel<N><<<1, 128, 0, st>>>(tm, tc, (int)tc, nullptr, x_in, ts);
+    count_launch();
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    const double* mp = (l == 0) ? maps : lv[l - 1];
+    const int64_t mcnt = (l == 0) ? cnt : c[l - 1];
+    double* outst = (l == 0) ? states : sv[l - 1];
+    down_maps_kernel<N><<<blocks_for(ceil_div(mcnt, G)), 128, 0, st>>>(mp, mcnt, G, sv[l], x_in, outst);
+    count_launch();
+  }
+}
+
+size_t affine_scan_bytes(int n, int64_t cnt) {
+  const size_t PM = (size_t)(n * n + n) * sizeof(double);
+  size_t off = 0;
+  int64_t mc = cnt;
+  while (mc > kUpperGroup) {
+    const int64_t nc = ceil_div(mc, kUpperGroup);
+    off = align_up(off + nc * PM);
+    off = align_up(off + (nc + 1) * n * sizeof(double));
+    mc = nc;
+  }
+  return off + 256;
+}
+
+cudaError_t affine_scan_states(int n, const double* maps, int64_t cnt, const double* x_in, double* states, char* ws,
+                               size_t& off, cudaStream_t st) {
+  switch (n) {
+    case 1: affine_scan_n<1>(maps, cnt, x_in, states, ws, off, st); break;
+    case 2: affine_scan_n<2>(maps, cnt, x_in, states, ws, off, st); break;
+    case 3: affine_scan_n<3>(maps, cnt, x_in, states, ws, off, st); break;
+    case 4: affine_scan_n<4>(maps, cnt, x_in, states, ws, off, st); break;
+    case 8: affine_scan_n<8>(maps, cnt, x_in, states, ws, off, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maps_from_values(const lqt_problem& p, const ElemPtrs& el, const double* S, const double* v,
+                                    double* maps, cudaStream_t st) {
+  const int G = 2;
+  const int64_t groups = ceil_div(p.T + 1, G);
+  switch (p.n) {
+#define LQT_MFV(NN)                                                                                       \
+  case NN:                                                                                                \
+    maps_from_values_kernel<NN><<<blocks_for(groups), 128, 0, st>>>(SrcPublic<NN>{el}, p.T, G, S, v, maps, \
+                                                                    nullptr);                            \
+    break;
+    LQT_MFV(1)
+    LQT_MFV(2)
+    LQT_MFV(3)
+    LQT_MFV(4)
+    LQT_MFV(8)
+#undef LQT_MFV
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ __device__ __forceinline__ void riccati_rhs(const RicState<N>& y, const double* 
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      double s = -Q[sidx<N>(i, j)] - SF[i * N + j] - SF[j * N + i];
+      double s = -Q[i * N + j] - SF[i * N + j] - SF[j * N + i];
 #pragma unroll
       for (int a = 0; a < M; ++a) s = fma(SL[i * M + a], SL[j * M + a], s);
       k.S[sidx<N>(i, j)] = s;
@@ -181,7 +181,7 @@ __global__ void sequential_kernel(SeqArgs a) {
         F[q] = cf.F.ptr + sample_index(cf.F.mode, j, ps[q], K) * N * N;
         c[q] = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, ps[q], K) * N : nullptr;
         Lt[q] = cf.Lt.ptr + sample_index(cf.Lt.mode, j, ps[q], K) * N * M;
-        Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * NS;
+        Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * N * N;
         qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
       }
       riccati_rhs<N, M>(y, F[0], c[0], Lt[0], Q[0], qr[0], k);
@@ -225,7 +225,7 @@ __global__ void sequential_kernel(SeqArgs a) {
       const double* F = cf.F.ptr + sample_index(cf.F.mode, j, 0, K) * N * N;
       const double* c = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, 0, K) * N : nullptr;
       const double* Lt = cf.Lt.ptr + sample_index(cf.Lt.mode, j, 0, K) * N * M;
-      const double* Q = cf.Q.ptr + sample_index(cf.Q.mode, j, 0, K) * NS;
+      const double* Q = cf.Q.ptr + sample_index(cf.Q.mode, j, 0, K) * N * N;
       const double* qr = cf.qr.ptr + sample_index(cf.qr.mode, j, 0, K) * (N + 1);
       riccati_rhs<N, M>(y0, F, c, Lt, Q, qr, d0);
     }
@@ -240,7 +240,7 @@ __global__ void sequential_kernel(SeqArgs a) {
         Lt[q] = cf.Lt.ptr + sample_index(cf.Lt.mode, j, ps[q], K) * N * M;
       }
       {
-        const double* Q = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[2], K) * NS;
+        const double* Q = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[2], K) * N * N;
         const double* qr = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[2], K) * (N + 1);
         riccati_rhs<N, M>(y1, F[2], c[2], Lt[2], Q, qr, d1);
       }
