@@ -39,8 +39,9 @@
  *    returned directly.  Numerical trouble found on the device (a non-finite
  *    value in an output, a zero pivot) is recorded in a per-device status word
  *    read and cleared by lqt_get_status().
- *  - Supported state dimensions n: 1, 2, 3, 4, 8.  Other n return
- *    LQT_EUNSUPPORTED.
+ *  - Supported state dimensions n: 1, 2, 3, 4, 8 (one thread per element),
+ *    16 and 64 (a warp / a CTA per element).  Other n return
+ *    LQT_EUNSUPPORTED.  m <= 16, nr <= 64.
  */
 #ifndef LQT_H
 #define LQT_H

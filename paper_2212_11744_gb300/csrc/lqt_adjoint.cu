@@ -905,7 +905,7 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   cudaError_t e = launch_prepare_coefs(p, L, ws + b.coef, cf, st);
   if (e != cudaSuccess) return e;
   ElemPtrs el = carve_elements_at(p, ws + b.elems);
-  e = launch_build(p, L, cf, el, st);
+  e = launch_build(p, L, cf, el, st, nullptr);
   if (e != cudaSuccess) return e;
   double* maps = (double*)(ws + b.maps);
   e = launch_maps_from_values(p, el, S, v, maps, st);

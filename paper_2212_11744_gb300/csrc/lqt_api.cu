@@ -18,10 +18,14 @@ void count_launch(int k) { t_launches += k; }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static bool supported_n(int n) { return n == 1 || n == 2 || n == 3 || n == 4 || n == 8; }
+static bool supported_n(int n) { return n == 1 || n == 2 || n == 3 || n == 4 || n == 8 || n == 16 || n == 64; }
 
 // Largest padded factor width compiled for each n.
-static int max_M(int n) { return n == 1 ? 1 : n == 2 ? 2 : n <= 4 ? 4 : 8; }
+static int max_M(int n) { return n == 1 ? 1 : n == 2 ? 2 : n <= 4 ? 4 : n == 8 ? 8 : 16; }
+
+// Factor width used by the kernels (n = 64 is compiled for 16 columns only;
+// zero columns do not change B = Lt Lt^T).
+static int32_t factor_width(int n, int m) { return n == 64 ? 16 : padded_M(m); }
 
 static bool valid_mode(int32_t m) { return m == LQT_CONST || m == LQT_PER_INTERVAL || m == LQT_PER_STAGE; }
 
@@ -32,7 +36,7 @@ static lqt_status validate(const lqt_problem* p) {
   if (!p) return LQT_EINVAL;
   if (p->n < 1 || p->m < 1 || p->nr < 1 || p->T < 1 || p->K < 1) return LQT_EINVAL;
   if (!supported_n(p->n)) return LQT_EUNSUPPORTED;
-  if (p->m > 16 || p->nr > 16) return LQT_EUNSUPPORTED;
+  if (p->m > 16 || p->nr > 64) return LQT_EUNSUPPORTED;
   if (padded_M(p->m) > max_M(p->n)) return LQT_EUNSUPPORTED;
   if (!p->t || !p->F.ptr || !p->L.ptr || !p->X.ptr || !p->U.ptr || !p->Xf) return LQT_EINVAL;
   if (!p->H.ptr && p->nr != p->n) return LQT_EINVAL;
@@ -50,7 +54,7 @@ static lqt_status validate(const lqt_problem* p) {
 static Layout make_layout(const lqt_problem& p) {
   Layout L{};
   L.n = p.n; L.m = p.m; L.nr = p.nr; L.K = p.K; L.T = p.T;
-  L.M = padded_M(p.m);
+  L.M = factor_width(p.n, p.m);
   const int32_t mH = p.H.ptr ? p.H.mode : kConst;
   const int32_t mr = p.r.ptr ? p.r.mode : kConst;
   L.mode_Lt = combine_modes(p.L.mode, p.U.mode);
@@ -105,11 +109,12 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
   const Layout L = make_layout(*p);
   const size_t T1 = (size_t)p->T + 1;
   switch (which) {
-    case LQT_WS_BUILD: return L.coef_bytes;
+    case LQT_WS_BUILD: return L.coef_bytes + team_build_scratch_bytes(p->n);
     case LQT_WS_VALUE: return scan_workspace_bytes(p->n, p->T, false);
     case LQT_WS_TRAJ: return L.coef_bytes + scan_workspace_bytes(p->n, p->T, true);
     case LQT_WS_SOLVE:
-      return L.coef_bytes + element_bytes(*p) + align_up(T1 * 8) + scan_workspace_bytes(p->n, p->T, true);
+      return L.coef_bytes + element_bytes(*p) + align_up(T1 * 8) + team_build_scratch_bytes(p->n) +
+             scan_workspace_bytes(p->n, p->T, true);
     case LQT_WS_SEQUENTIAL: return L.coef_bytes + align_up(sequential_workspace_bytes(p->n, p->T, p->K));
     case LQT_WS_BACKWARD: return backward_workspace_bytes(*p, L, element_bytes(*p)) + 4096;
     default: return 0;
@@ -130,7 +135,7 @@ lqt_status lqt_build_elements(const lqt_problem* p, const lqt_elements* out, voi
   cudaError_t e = launch_prepare_coefs(*p, L, (char*)ws, cf, st);
   if (e != cudaSuccess) return LQT_ECUDA;
   ElemPtrs el{out->A, out->b, out->C, out->eta, out->J, out->zeta};
-  return from_cuda(launch_build(*p, L, cf, el, st));
+  return from_cuda(launch_build(*p, L, cf, el, st, (double*)((char*)ws + L.coef_bytes)));
 }
 
 lqt_status lqt_scan_value(const lqt_problem* p, const lqt_elements* el, double* S, double* v, double* zeta,
@@ -153,6 +158,7 @@ lqt_status lqt_scan_trajectory(const lqt_problem* p, const lqt_elements* el, con
   t_launches = 0;
   lqt_status s = validate(p);
   if (s != LQT_OK) return s;
+  if (p->n > 8) return LQT_EUNSUPPORTED;
   if (!el || !el->A || !el->b || !el->C || !el->eta || !el->J || !S || !v || !x0 || !x) return LQT_EINVAL;
   const size_t need = lqt_workspace_size(p, LQT_WS_TRAJ);
   if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
@@ -181,8 +187,9 @@ lqt_status lqt_solve(const lqt_problem* p, const double* x0, double* S, double* 
   ElemPtrs el = carve_elements(*p, base + L.coef_bytes);
   double* zbuf = (double*)(base + L.coef_bytes + element_bytes(*p));
   double* zout = zeta ? zeta : zbuf;
-  if (launch_build(*p, L, cf, el, st) != cudaSuccess) return LQT_ECUDA;
-  char* scan = base + L.coef_bytes + element_bytes(*p) + align_up(((size_t)p->T + 1) * 8);
+  char* team_scr = base + L.coef_bytes + element_bytes(*p) + align_up(((size_t)p->T + 1) * 8);
+  if (launch_build(*p, L, cf, el, st, (double*)team_scr) != cudaSuccess) return LQT_ECUDA;
+  char* scan = team_scr + team_build_scratch_bytes(p->n);
   return from_cuda(run_value_and_traj(*p, L, cf, el, S, v, zout, x0, x, u, cost, true, true, nullptr, nullptr, scan,
                                       ws_bytes - (scan - base), st));
 }
@@ -192,6 +199,7 @@ lqt_status lqt_solve_sequential(const lqt_problem* p, const double* x0, double* 
   t_launches = 0;
   lqt_status s = validate(p);
   if (s != LQT_OK) return s;
+  if (p->n > 8) return LQT_EUNSUPPORTED;
   if (!x0 || !S || !v || !x) return LQT_EINVAL;
   const size_t need = lqt_workspace_size(p, LQT_WS_SEQUENTIAL);
   if (!ws || ws_bytes < need) return LQT_EWORKSPACE;

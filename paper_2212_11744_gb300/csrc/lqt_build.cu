@@ -56,7 +56,7 @@ __device__ void cholesky_lower(double* R, int m) {
 }
 
 constexpr int kMaxM = 16;
-constexpr int kMaxN = 16;
+constexpr int kMaxN = 64;
 
 // One thread per derived sample; blockIdx.y selects the quantity (with two
 // rows in the grid only Lt and Ku are made).
@@ -231,6 +231,8 @@ cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* 
       case 3: launch_qr_identity<3>(a, st); break;
       case 4: launch_qr_identity<4>(a, st); break;
       case 8: launch_qr_identity<8>(a, st); break;
+      case 16: launch_qr_identity<16>(a, st); break;
+      case 64: launch_qr_identity<64>(a, st); break;
       default: return cudaErrorInvalidValue;
     }
   } else {
@@ -463,7 +465,7 @@ struct TermArgs {
 
 __global__ void terminal_kernel(TermArgs a) {
   const int n = a.n, nr = a.nr;
-  const int e = threadIdx.x;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
   const int i = e / n, j = e % n;
   double vij = 0.0, vji = 0.0;
@@ -504,7 +506,7 @@ __global__ void terminal_kernel(TermArgs a) {
 
 cudaError_t launch_terminal_values(const lqt_problem& p, double* J, double* eta, double* zeta, cudaStream_t st) {
   TermArgs t{p.n, p.nr, p.Hf, p.Xf, p.rf, nullptr, nullptr, nullptr, eta, J, zeta};
-  terminal_kernel<<<1, p.n * p.n, 0, st>>>(t);
+  terminal_kernel<<<(p.n * p.n + 255) / 256, 256, 0, st>>>(t);
   count_launch();
   return cudaGetLastError();
 }
@@ -530,7 +532,7 @@ static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st) {
 }
 
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
-                         cudaStream_t st) {
+                         cudaStream_t st, double* team_scratch) {
   BuildArgs a;
   a.T = p.T; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
   cudaError_t e;
@@ -540,6 +542,8 @@ cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& c
     case 3: e = launch_build_n<3>(a, lay.M, st); break;
     case 4: e = launch_build_n<4>(a, lay.M, st); break;
     case 8: e = launch_build_n<8>(a, lay.M, st); break;
+    case 16:
+    case 64: e = team_launch_build(p, lay, cf, out, team_scratch, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
@@ -547,7 +551,7 @@ cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& c
   const int n = p.n;
   TermArgs t{p.n, p.nr, p.Hf, p.Xf, p.rf, out.A + T * n * n, out.b + T * n, out.C + T * n * n,
              out.eta + T * n, out.J + T * n * n, out.zeta ? out.zeta + T : nullptr};
-  terminal_kernel<<<1, n * n, 0, st>>>(t);
+  terminal_kernel<<<(n * n + 255) / 256, 256, 0, st>>>(t);
   count_launch();
   return cudaGetLastError();
 }

@@ -94,7 +94,15 @@ void count_launch(int k = 1);
 // -------------------------------------------------------------------------
 cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* ws, Coefs& out, cudaStream_t s);
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
-                         cudaStream_t s);
+                         cudaStream_t s, double* team_scratch = nullptr);
+// n = 16, 64 (team kernels, lqt_team.cu)
+size_t team_build_scratch_bytes(int n);
+size_t team_scan_workspace_bytes(int32_t n, int64_t T, bool with_traj);
+cudaError_t team_launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                              double* gscratch, cudaStream_t st);
+cudaError_t team_run_value_and_traj(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
+                                    double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
+                                    bool do_traj, char* ws, cudaStream_t st);
 cudaError_t launch_terminal_values(const lqt_problem& p, double* J, double* eta, double* zeta, cudaStream_t s);
 
 size_t scan_workspace_bytes(int32_t n, int64_t T, bool with_traj);

@@ -649,6 +649,8 @@ size_t scan_workspace_bytes(int32_t n, int64_t T, bool with_traj) {
     case 3: return make_plan<3>(T, with_traj).bytes;
     case 4: return make_plan<4>(T, with_traj).bytes;
     case 8: return make_plan<8>(T, with_traj).bytes;
+    case 16:
+    case 64: return team_scan_workspace_bytes(n, T, with_traj);
     default: return 0;
   }
 }
@@ -667,6 +669,10 @@ cudaError_t run_value_and_traj(const lqt_problem& p, const Layout& lay, const Co
     case 3: return run_n<3>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
     case 4: return run_n<4>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
     case 8: return run_n<8>(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    case 16:
+    case 64:
+      if (!do_value) return cudaErrorNotSupported;
+      return team_run_value_and_traj(p, cf, el, Sx, vx, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
     default: return cudaErrorInvalidValue;
   }
 }

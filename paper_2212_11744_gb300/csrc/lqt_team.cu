@@ -1,0 +1,579 @@
+// Solve path for state dimensions 16 and 64: the same three stages as the
+// one-thread-per-element kernels (lqt_build.cu, lqt_scan.cu) with a team of
+// threads per element (lqt_team.cuh).  n = 16: one warp per element, every
+// buffer in shared memory.  n = 64: one CTA of 256 threads per element, the
+// element-sized buffers in a per-CTA slot of the workspace (they stay in L2),
+// grid = one CTA per SM looping over the work.
+#include <cuda_runtime.h>
+
+#include "lqt_device.cuh"
+#include "lqt_internal.h"
+#include "lqt_team.cuh"
+
+namespace lqt {
+
+using team::Rec;
+
+__host__ __device__ __forceinline__ int64_t tdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static size_t tal(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int N>
+struct TeamCfg;
+template <>
+struct TeamCfg<16> {
+  static constexpr int TEAM = 32;
+  static constexpr bool SMEM = true;
+  static constexpr int SLOTS = 152 * 8;
+};
+template <>
+struct TeamCfg<64> {
+  static constexpr int TEAM = 256;
+  static constexpr bool SMEM = false;
+  static constexpr int SLOTS = 152;
+};
+
+// Doubles of per-slot scratch of each kernel.
+template <int N, int M>
+constexpr int build_slot_doubles() { return 4 * Rec<N>::SIZE + 2 * N * M + M + 8; }
+template <int N>
+constexpr int reduce_slot_doubles() { return 2 * Rec<N>::SIZE + team::combine_scratch_doubles<N>() + 8; }
+template <int N>
+constexpr int down_slot_doubles() {
+  return 2 * team::val_doubles<N>() + team::value_scratch_doubles<N>() + 3 * (N * N + N) + N * N + N + 8;
+}
+template <int N>
+constexpr int maps_slot_doubles() { return 3 * (N * N + N) + 2 * N + 8; }
+
+template <int N>
+constexpr int max_slot_doubles() {
+  int a = build_slot_doubles<N, N>();
+  if (reduce_slot_doubles<N>() > a) a = reduce_slot_doubles<N>();
+  if (down_slot_doubles<N>() > a) a = down_slot_doubles<N>();
+  if (maps_slot_doubles<N>() > a) a = maps_slot_doubles<N>();
+  return a;
+}
+
+// Buffer base of this CTA: dynamic shared memory, or its workspace slot.
+template <int N>
+__device__ __forceinline__ double* slot_base(double* gscratch, int slot_doubles) {
+  extern __shared__ double dyn_smem[];
+  if constexpr (TeamCfg<N>::SMEM) {
+    (void)gscratch;
+    (void)slot_doubles;
+    return dyn_smem;
+  } else {
+    return gscratch + (size_t)blockIdx.x * slot_doubles;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage (a)
+// ---------------------------------------------------------------------------
+
+struct TeamBuildArgs {
+  int64_t T;
+  int32_t K;
+  const double* t;
+  Coefs cf;
+  ElemPtrs out;
+  double* gscratch;
+};
+
+template <int N, int M>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_kernel(TeamBuildArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int SD = build_slot_doubles<N, M>();
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(a.gscratch, SD);
+  double* yb = base;
+  double* ynb = yb + Rec<N>::SIZE;
+  double* ytb = ynb + Rec<N>::SIZE;
+  double* kb = ytb + Rec<N>::SIZE;
+  double* AL = kb + Rec<N>::SIZE;
+  double* P = AL + N * M;
+  double* w = P + N * M;
+  const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
+  const int32_t K = a.K;
+  const Coefs& cf = a.cf;
+  for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
+    const double h = (a.t[j + 1] - a.t[j]) / K;
+    for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
+    team::sync<TEAM>();
+    for (int32_t i = K - 1; i >= 0; --i) {
+      const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
+      const double *F[3], *c[3], *Lt[3], *Q[3], *qr[3];
+      for (int q = 0; q < 3; ++q) {
+        F[q] = cf.F.ptr + sample_index(cf.F.mode, j, ps[q], K) * N * N;
+        c[q] = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, ps[q], K) * N : nullptr;
+        Lt[q] = cf.Lt.ptr + sample_index(cf.Lt.mode, j, ps[q], K) * N * M;
+        Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * N * N;
+        qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
+      }
+      team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w);
+      team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
+      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
+      team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
+      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
+      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
+      team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
+      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
+      team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
+      team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w);
+      team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
+    }
+    double zz = 0.0;
+    Rec<N> dst = Rec<N>::pub(a.out, j, &zz);
+    team::copy_rec<N, TEAM>(lane, dst, y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage (b): reduce / down-sweep of the value scan
+// ---------------------------------------------------------------------------
+
+struct TeamScanArgs {
+  ElemPtrs el;           // level-0 elements (public layout)
+  const double* src;     // packed elements of the level (levels >= 1), or null at level 0
+  int64_t cnt;           // elements at this level
+  int G;                 // group length
+  double* agg;           // reduce output (packed)
+  const double* above;   // packed values of the level above (down), or null
+  int64_t cnt_above;
+  double* vals;          // packed values out (levels >= 1)
+  double *S, *v, *zeta;  // level-0 outputs
+  double *maps, *comp;   // level-0 maps [T][N^2+N] and chunk composites
+  int64_t T;
+  double* gscratch;
+};
+
+template <int N>
+__device__ __forceinline__ Rec<N> level_elem(const TeamScanArgs& a, int64_t k, double* zero) {
+  if (a.src) return Rec<N>::packed(const_cast<double*>(a.src) + k * Rec<N>::SIZE);
+  return Rec<N>::pub(a.el, k, zero);
+}
+
+template <int N>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_team_kernel(TeamScanArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int SD = reduce_slot_doubles<N>();
+  __shared__ double fs[TEAM];
+  __shared__ int is[TEAM];
+  __shared__ double zero;
+  const int lane = threadIdx.x;
+  if (lane == 0) zero = 0.0;
+  double* base = slot_base<N>(a.gscratch, SD);
+  double* bufA = base;
+  double* bufB = bufA + Rec<N>::SIZE;
+  double* scr = bufB + Rec<N>::SIZE;
+  team::sync<TEAM>();
+  const int64_t groups = tdiv(a.cnt, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.cnt ? first + a.G : a.cnt) - 1;
+    Rec<N> acc = Rec<N>::packed(bufA), nxt = Rec<N>::packed(bufB);
+    team::copy_rec<N, TEAM>(lane, acc, level_elem<N>(a, last, &zero));
+    for (int64_t k = last - 1; k >= first; --k) {
+      team::combine<N, TEAM>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is);
+      const Rec<N> t = acc;
+      acc = nxt;
+      nxt = t;
+    }
+    team::copy_rec<N, TEAM>(lane, Rec<N>::packed(a.agg + g * Rec<N>::SIZE), acc);
+  }
+}
+
+template <int N, bool Level0>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) down_team_kernel(TeamScanArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int SD = down_slot_doubles<N>();
+  constexpr int VS = team::val_doubles<N>();
+  constexpr int PM = N * N + N;
+  __shared__ double fs[TEAM];
+  __shared__ int is[TEAM];
+  __shared__ double zero;
+  const int lane = threadIdx.x;
+  if (lane == 0) zero = 0.0;
+  double* base = slot_base<N>(a.gscratch, SD);
+  double* c0 = base;
+  double* c1 = c0 + VS;
+  double* scr = c1 + VS;
+  double* Psi = scr + team::value_scratch_doubles<N>();
+  double* alpha = Psi + N * N;
+  double* P = alpha + N;
+  double* pv = P + N * N;
+  double* Tm = pv + N;
+  team::sync<TEAM>();
+  const int64_t groups = tdiv(a.cnt, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.cnt ? first + a.G : a.cnt) - 1;
+    double* carry = c0;
+    double* nv = c1;
+    for (int e = lane; e < VS; e += TEAM)
+      carry[e] = (a.above != nullptr && g + 1 < a.cnt_above) ? a.above[(g + 1) * VS + e] : 0.0;
+    if (Level0)
+      for (int e = lane; e < PM; e += TEAM) {
+        if (e < N * N) P[e] = (e % (N + 1) == 0) ? 1.0 : 0.0;
+        else pv[e - N * N] = 0.0;
+      }
+    team::sync<TEAM>();
+    for (int64_t k = last; k >= first; --k) {
+      team::combine_value<N, TEAM>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is);
+      if (Level0) {
+        bool ok = true;
+        for (int e = lane; e < VS; e += TEAM) {
+          const double x = nv[e];
+          ok = ok && isfinite(x);
+          if (e < N * N) a.S[k * N * N + e] = x;
+          else if (e < N * N + N) a.v[k * N + e - N * N] = x;
+          else if (a.zeta) a.zeta[k] = x;
+        }
+        if (!ok) flag(kStatusNonFinite);
+        if (a.maps != nullptr && k < a.T) {
+          for (int e = lane; e < PM; e += TEAM) a.maps[k * PM + e] = e < N * N ? Psi[e] : alpha[e - N * N];
+          team::compose_right<N, TEAM>(lane, P, pv, Psi, alpha, Tm);
+        }
+      } else {
+        for (int e = lane; e < VS; e += TEAM) a.vals[k * VS + e] = nv[e];
+      }
+      team::sync<TEAM>();
+      double* t = carry;
+      carry = nv;
+      nv = t;
+    }
+    if (Level0 && a.comp != nullptr && last + 1 <= a.T)
+      for (int e = lane; e < PM; e += TEAM) a.comp[g * PM + e] = e < N * N ? P[e] : pv[e - N * N];
+    team::sync<TEAM>();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage (c): affine-map scan and the final pass
+// ---------------------------------------------------------------------------
+
+struct TeamMapArgs {
+  const double* maps;  // [cnt][N^2+N]
+  int64_t cnt;
+  int G;
+  double* comp;         // reduce output
+  const double* above;  // starts of the level above (down), or null -> x_in
+  const double* x_in;
+  double* starts;       // [cnt+1][N]
+  double* gscratch;
+};
+
+template <int N>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_maps_team_kernel(TeamMapArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int PM = N * N + N;
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(a.gscratch, maps_slot_doubles<N>());
+  double* P = base;
+  double* p = P + N * N;
+  double* Tm = p + N;
+  const int64_t groups = tdiv(a.cnt, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.cnt ? first + a.G : a.cnt) - 1;
+    for (int e = lane; e < PM; e += TEAM) (e < N * N ? P[e] : p[e - N * N]) = a.maps[first * PM + e];
+    team::sync<TEAM>();
+    for (int64_t k = first + 1; k <= last; ++k)
+      team::compose_left<N, TEAM>(lane, P, p, a.maps + k * PM, a.maps + k * PM + N * N, Tm);
+    for (int e = lane; e < PM; e += TEAM) a.comp[g * PM + e] = e < N * N ? P[e] : p[e - N * N];
+    team::sync<TEAM>();
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) down_maps_team_kernel(TeamMapArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int PM = N * N + N;
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(a.gscratch, maps_slot_doubles<N>());
+  double* x = base;
+  double* y = x + N;
+  const int64_t groups = tdiv(a.cnt, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.cnt ? first + a.G : a.cnt) - 1;
+    const double* xs = a.above ? a.above + g * N : a.x_in;
+    for (int e = lane; e < N; e += TEAM) x[e] = xs[e];
+    team::sync<TEAM>();
+    for (int64_t k = first; k <= last; ++k) {
+      for (int e = lane; e < N; e += TEAM) a.starts[k * N + e] = x[e];
+      team::apply_map<N, TEAM>(lane, a.maps + k * PM, a.maps + k * PM + N * N, x, y);
+      for (int e = lane; e < N; e += TEAM) x[e] = y[e];
+      team::sync<TEAM>();
+    }
+    if (last == a.cnt - 1)
+      for (int e = lane; e < N; e += TEAM) a.starts[a.cnt * N + e] = x[e];
+    team::sync<TEAM>();
+  }
+}
+
+struct TeamFinalArgs {
+  const double* maps;
+  int64_t T;
+  int G;
+  const double *starts1, *x0, *S, *v, *zeta, *Ku;
+  int32_t Ku_per_boundary, m;
+  double *x, *u, *cost;
+  double* gscratch;
+};
+
+template <int N>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) final_team_kernel(TeamFinalArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int PM = N * N + N;
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(a.gscratch, maps_slot_doubles<N>());
+  double* x = base;
+  double* y = x + N;
+  const int64_t groups = tdiv(a.T + 1, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.T + 1 ? first + a.G : a.T + 1) - 1;
+    const double* xs = a.starts1 ? a.starts1 + g * N : a.x0;
+    for (int e = lane; e < N; e += TEAM) x[e] = xs[e];
+    team::sync<TEAM>();
+    for (int64_t k = first; k <= last; ++k) {
+      for (int e = lane; e < N; e += TEAM) a.x[k * N + e] = x[e];
+      if (a.u) {
+        // y = v_k - S_k x_k, then u = Ku y
+        const double* Sk = a.S + k * N * N;
+        for (int i = lane; i < N; i += TEAM) {
+          double s = a.v[k * N + i];
+          for (int l = 0; l < N; ++l) s = fma(-Sk[i * N + l], x[l], s);
+          y[i] = s;
+        }
+        team::sync<TEAM>();
+        const double* Kk = a.Ku + (a.Ku_per_boundary ? k * a.m * N : 0);
+        for (int q = lane; q < a.m; q += TEAM) {
+          double s = 0.0;
+          for (int l = 0; l < N; ++l) s = fma(Kk[q * N + l], y[l], s);
+          a.u[k * a.m + q] = s;
+        }
+        team::sync<TEAM>();
+      }
+      if (k < a.T) {
+        team::apply_map<N, TEAM>(lane, a.maps + k * PM, a.maps + k * PM + N * N, x, y);
+        for (int e = lane; e < N; e += TEAM) x[e] = y[e];
+        team::sync<TEAM>();
+      }
+    }
+    if (g == 0 && a.cost && lane == 0) {
+      double c = a.zeta ? a.zeta[0] : 0.0;
+      for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int l = 0; l < N; ++l) s = fma(a.S[i * N + l], a.x0[l], s);
+        c = fma(a.x0[i], fma(0.5, s, -a.v[i]), c);
+      }
+      *a.cost = c;
+    }
+    team::sync<TEAM>();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <int N>
+static int team_group0(int64_t T) {
+  const int64_t want = TeamCfg<N>::SLOTS;  // chunks that keep every slot busy
+  int g = 2;
+  while (g < 32 && (T + 1) / (2 * g) >= want) g *= 2;
+  return g;
+}
+
+template <int N>
+struct TeamPlan {
+  int G0;
+  int nlev;
+  int64_t cnt[64];
+  size_t off_agg[64], off_val[64];
+  size_t off_maps;
+  int tlev;
+  int64_t tcnt[64];
+  size_t off_tmap[64], off_tstart[64];
+  size_t off_scratch;
+  size_t bytes;
+};
+
+template <int N>
+static TeamPlan<N> team_plan(int64_t T, bool with_traj) {
+  TeamPlan<N> pl{};
+  pl.G0 = team_group0<N>(T);
+  size_t off = 0;
+  const size_t PE = sizeof(double) * Rec<N>::SIZE;
+  const size_t PV = sizeof(double) * team::val_doubles<N>();
+  const size_t PM = sizeof(double) * (N * N + N);
+  int64_t c = T + 1;
+  int G = pl.G0;
+  while (c > G) {
+    const int64_t nc = tdiv(c, G);
+    pl.cnt[pl.nlev] = nc;
+    pl.off_agg[pl.nlev] = off;
+    off = tal(off + nc * PE);
+    pl.off_val[pl.nlev] = off;
+    off = tal(off + nc * PV);
+    ++pl.nlev;
+    c = nc;
+    G = 2;
+  }
+  pl.off_maps = off;
+  if (with_traj) {
+    off = tal(off + (size_t)T * PM);
+    int64_t mc = tdiv(T + 1, pl.G0) - 1;
+    while (mc > 0) {
+      pl.tcnt[pl.tlev] = mc;
+      pl.off_tmap[pl.tlev] = off;
+      off = tal(off + mc * PM);
+      pl.off_tstart[pl.tlev] = off;
+      off = tal(off + (mc + 1) * sizeof(double) * N);
+      ++pl.tlev;
+      if (mc <= 2) break;
+      mc = tdiv(mc, 2);
+    }
+  }
+  pl.off_scratch = off;
+  if (!TeamCfg<N>::SMEM) off = tal(off + (size_t)TeamCfg<N>::SLOTS * max_slot_doubles<N>() * sizeof(double));
+  pl.bytes = tal(off);
+  return pl;
+}
+
+template <int N>
+static unsigned team_grid(int64_t work) {
+  const int64_t s = TeamCfg<N>::SLOTS;
+  return (unsigned)(work < s ? (work > 0 ? work : 1) : s);
+}
+
+template <int N, class Kern, class Args>
+static void team_launch(Kern k, int64_t work, size_t smem_doubles, const Args& a, cudaStream_t st) {
+  const size_t smem = TeamCfg<N>::SMEM ? smem_doubles * sizeof(double) : 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<team_grid<N>(work), TeamCfg<N>::TEAM, smem, st>>>(a);
+  count_launch();
+}
+
+template <int N, int M>
+static cudaError_t team_build_nm(const lqt_problem& p, const Coefs& cf, const ElemPtrs& out, double* gscratch,
+                                 cudaStream_t st) {
+  TeamBuildArgs a{p.T, p.K, p.t, cf, out, gscratch};
+  team_launch<N>(build_team_kernel<N, M>, p.T, build_slot_doubles<N, M>(), a, st);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
+                            double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
+                            bool do_traj, char* ws, cudaStream_t st) {
+  const TeamPlan<N> pl = team_plan<N>(p.T, do_traj);
+  double* gs = TeamCfg<N>::SMEM ? nullptr : (double*)(ws + pl.off_scratch);
+  double* maps0 = (double*)(ws + pl.off_maps);
+  double* comp1 = pl.tlev > 0 ? (double*)(ws + pl.off_tmap[0]) : nullptr;
+  if (do_value) {
+    int64_t c = p.T + 1;
+    int G = pl.G0;
+    for (int l = 0; l < pl.nlev; ++l) {
+      TeamScanArgs a{};
+      a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
+      a.agg = (double*)(ws + pl.off_agg[l]); a.T = p.T; a.gscratch = gs;
+      team_launch<N>(reduce_team_kernel<N>, pl.cnt[l], reduce_slot_doubles<N>(), a, st);
+      c = pl.cnt[l];
+      G = 2;
+    }
+    for (int l = pl.nlev; l >= 0; --l) {
+      TeamScanArgs a{};
+      a.el = el;
+      a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr;
+      a.cnt = l ? pl.cnt[l - 1] : p.T + 1;
+      a.G = l ? 2 : pl.G0;
+      a.above = l < pl.nlev ? (const double*)(ws + pl.off_val[l]) : nullptr;
+      a.cnt_above = l < pl.nlev ? pl.cnt[l] : 0;
+      a.T = p.T;
+      a.gscratch = gs;
+      const int64_t groups = tdiv(a.cnt, a.G);
+      if (l == 0) {
+        a.S = S; a.v = v; a.zeta = zeta;
+        a.maps = do_traj ? maps0 : nullptr;
+        a.comp = do_traj ? comp1 : nullptr;
+        team_launch<N>(down_team_kernel<N, true>, groups, down_slot_doubles<N>(), a, st);
+      } else {
+        a.vals = (double*)(ws + pl.off_val[l - 1]);
+        team_launch<N>(down_team_kernel<N, false>, groups, down_slot_doubles<N>(), a, st);
+      }
+    }
+  } else if (do_traj) {
+    return cudaErrorNotSupported;
+  }
+  if (!do_traj) return cudaGetLastError();
+  for (int l = 1; l < pl.tlev; ++l) {
+    TeamMapArgs a{};
+    a.maps = (const double*)(ws + pl.off_tmap[l - 1]); a.cnt = pl.tcnt[l - 1]; a.G = 2;
+    a.comp = (double*)(ws + pl.off_tmap[l]); a.gscratch = gs;
+    team_launch<N>(reduce_maps_team_kernel<N>, pl.tcnt[l], maps_slot_doubles<N>(), a, st);
+  }
+  for (int l = pl.tlev - 1; l >= 0; --l) {
+    TeamMapArgs a{};
+    a.maps = (const double*)(ws + pl.off_tmap[l]); a.cnt = pl.tcnt[l];
+    a.G = (l + 1 < pl.tlev) ? 2 : (int)pl.tcnt[l];
+    a.above = (l + 1 < pl.tlev) ? (const double*)(ws + pl.off_tstart[l + 1]) : nullptr;
+    a.x_in = x0; a.starts = (double*)(ws + pl.off_tstart[l]); a.gscratch = gs;
+    team_launch<N>(down_maps_team_kernel<N>, tdiv(pl.tcnt[l], a.G), maps_slot_doubles<N>(), a, st);
+  }
+  TeamFinalArgs f{};
+  f.maps = maps0; f.T = p.T; f.G = pl.G0;
+  f.starts1 = pl.tlev > 0 ? (const double*)(ws + pl.off_tstart[0]) : nullptr;
+  f.x0 = x0; f.S = S; f.v = v; f.zeta = zeta; f.Ku = cf.Ku; f.Ku_per_boundary = cf.Ku_per_boundary; f.m = p.m;
+  f.x = x; f.u = u; f.cost = cost; f.gscratch = gs;
+  team_launch<N>(final_team_kernel<N>, tdiv(p.T + 1, pl.G0), maps_slot_doubles<N>(), f, st);
+  return cudaGetLastError();
+}
+
+// Build scratch for n = 64 (per-slot element buffers).
+size_t team_build_scratch_bytes(int n) {
+  if (n == 64) return tal((size_t)TeamCfg<64>::SLOTS * build_slot_doubles<64, 16>() * sizeof(double));
+  return 0;
+}
+
+size_t team_scan_workspace_bytes(int32_t n, int64_t T, bool with_traj) {
+  switch (n) {
+    case 16: return team_plan<16>(T, with_traj).bytes;
+    case 64: return team_plan<64>(T, with_traj).bytes;
+    default: return 0;
+  }
+}
+
+cudaError_t team_launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                              double* gscratch, cudaStream_t st) {
+  switch (p.n) {
+    case 16:
+      switch (lay.M) {
+        case 1: return team_build_nm<16, 1>(p, cf, out, gscratch, st);
+        case 2: return team_build_nm<16, 2>(p, cf, out, gscratch, st);
+        case 4: return team_build_nm<16, 4>(p, cf, out, gscratch, st);
+        case 8: return team_build_nm<16, 8>(p, cf, out, gscratch, st);
+        case 16: return team_build_nm<16, 16>(p, cf, out, gscratch, st);
+        default: return cudaErrorInvalidValue;
+      }
+    case 64:
+      switch (lay.M) {
+        case 16: return team_build_nm<64, 16>(p, cf, out, gscratch, st);
+        default: return cudaErrorInvalidValue;
+      }
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t team_run_value_and_traj(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
+                                    double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
+                                    bool do_traj, char* ws, cudaStream_t st) {
+  switch (p.n) {
+    case 16: return team_run<16>(p, cf, el, S, v, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    case 64: return team_run<64>(p, cf, el, S, v, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lqt

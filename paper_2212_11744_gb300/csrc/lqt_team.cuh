@@ -1,0 +1,555 @@
+// Cooperative ("team") versions of the element build and the combination rule
+// for larger state dimensions (n = 16, 64), where one thread cannot hold an
+// element.  A team of TEAM threads (one warp for n = 16, one CTA of 256
+// threads for n = 64) owns one element; matrices are full n x n row-major in
+// buffers the caller places in shared or global memory; the team spreads the
+// entries of every product over its lanes.  On this GPU the FP64 pipe is the
+// limit (one FP64 warp instruction per 64 cycles per sub-partition), so
+// operands are read straight from the buffers without register blocking.
+//
+// Math: Sec. IV-B Theorem Backward_HJB_LQT (right-hand side, with the factor
+// B = Lt Lt^T), Sec. IV-A eq. lqt_comb (full and value-form combination),
+// Sec. IV-E (one-sub-interval optimal-state map).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lqt_internal.h"
+
+namespace lqt {
+namespace team {
+
+template <int TEAM>
+__device__ __forceinline__ void sync() {
+  if constexpr (TEAM <= 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+// (i, j) of the t-th entry of the upper triangle (row by row).
+__device__ __forceinline__ void upper_ij(int N, int t, int& i, int& j) {
+  int r = 0;
+  while (t >= N - r) {
+    t -= N - r;
+    ++r;
+  }
+  i = r;
+  j = r + t;
+}
+
+// An element as six field pointers (full n x n matrices), so that a record can
+// live in a packed buffer (A, b, C, eta, J, zeta back to back) or in the public
+// SoA arrays.
+template <int N>
+struct Rec {
+  static constexpr int SIZE = 3 * N * N + 2 * N + 1;
+  double *a_, *b_, *c_, *e_, *j_, *z_;
+  __device__ __forceinline__ double* A() const { return a_; }
+  __device__ __forceinline__ double* b() const { return b_; }
+  __device__ __forceinline__ double* C() const { return c_; }
+  __device__ __forceinline__ double* eta() const { return e_; }
+  __device__ __forceinline__ double* J() const { return j_; }
+  __device__ __forceinline__ double* zeta() const { return z_; }
+  // packed record at p
+  __device__ __forceinline__ static Rec packed(double* p) {
+    return Rec{p, p + N * N, p + N * N + N, p + 2 * N * N + N, p + 2 * N * N + 2 * N, p + 3 * N * N + 2 * N};
+  }
+  // element k of the public arrays
+  __device__ __forceinline__ static Rec pub(const ElemPtrs& el, int64_t k, double* zeta_fallback) {
+    return Rec{el.A + k * N * N, el.b + k * N, el.C + k * N * N, el.eta + k * N, el.J + k * N * N,
+               el.zeta ? el.zeta + k : zeta_fallback};
+  }
+};
+// ---------------------------------------------------------------------------
+// element build right-hand side (factor form, see build_kernel)
+// ---------------------------------------------------------------------------
+
+// k = f(y); scratch: AL, P (N x M), w (M).
+template <int N, int M, int TEAM>
+__device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
+                    const double* __restrict__ Lt, const double* __restrict__ Q, const double* __restrict__ qr,
+                    double* AL, double* P, double* w) {
+  const double* A = y.A();
+  const double* J = y.J();
+  const double* eta = y.eta();
+  for (int e = lane; e < 2 * N * M + M; e += TEAM) {
+    if (e < 2 * N * M) {
+      const int which = e / (N * M), r = e % (N * M), i = r / M, a = r % M;
+      const double* X = which ? J : A;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(X[i * N + l], Lt[l * M + a], s);
+      (which ? P : AL)[i * M + a] = s;
+    } else {
+      const int a = e - 2 * N * M;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
+      w[a] = s;
+    }
+  }
+  sync<TEAM>();
+  constexpr int NS = N * (N + 1) / 2;
+  constexpr int ITEMS = N * N + N + NS + N + NS + 1;
+  for (int e = lane; e < ITEMS; e += TEAM) {
+    int t = e;
+    if (t < N * N) {  // dA = AL P^T - A F
+      const int i = t / N, j = t % N;
+      double s = 0.0;
+      for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
+      for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
+      k.A()[t] = s;
+      continue;
+    }
+    t -= N * N;
+    if (t < N) {  // db = -AL w - A c
+      double s = 0.0;
+      for (int a = 0; a < M; ++a) s = fma(-AL[t * M + a], w[a], s);
+      if (c)
+        for (int l = 0; l < N; ++l) s = fma(-A[t * N + l], c[l], s);
+      k.b()[t] = s;
+      continue;
+    }
+    t -= N;
+    if (t < NS) {  // dC = -AL AL^T
+      int i, j;
+      upper_ij(N, t, i, j);
+      double s = 0.0;
+      for (int a = 0; a < M; ++a) s = fma(-AL[i * M + a], AL[j * M + a], s);
+      k.C()[i * N + j] = s;
+      k.C()[j * N + i] = s;
+      continue;
+    }
+    t -= NS;
+    if (t < N) {  // deta = -q - F^T eta + J c + P w
+      double s = -qr[t];
+      for (int l = 0; l < N; ++l) s = fma(-F[l * N + t], eta[l], s);
+      if (c)
+        for (int l = 0; l < N; ++l) s = fma(J[t * N + l], c[l], s);
+      for (int a = 0; a < M; ++a) s = fma(P[t * M + a], w[a], s);
+      k.eta()[t] = s;
+      continue;
+    }
+    t -= N;
+    if (t < NS) {  // dJ = -Q - JF - (JF)^T + P P^T
+      int i, j;
+      upper_ij(N, t, i, j);
+      double s = -Q[i * N + j];
+      for (int l = 0; l < N; ++l) {
+        s = fma(-J[i * N + l], F[l * N + j], s);
+        s = fma(-J[j * N + l], F[l * N + i], s);
+      }
+      for (int a = 0; a < M; ++a) s = fma(P[i * M + a], P[j * M + a], s);
+      k.J()[i * N + j] = s;
+      k.J()[j * N + i] = s;
+      continue;
+    }
+    {  // dzeta
+      double z = -0.5 * qr[N];
+      for (int a = 0; a < M; ++a) z = fma(0.5 * w[a], w[a], z);
+      if (c)
+        for (int l = 0; l < N; ++l) z = fma(eta[l], c[l], z);
+      *k.zeta() = z;
+    }
+  }
+  sync<TEAM>();
+}
+
+// out = base + s * k over a packed record (out may alias base).
+template <int N, int TEAM>
+__device__ __forceinline__ void axpy(int lane, double* out, const double* base, double s, const double* k) {
+  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) out[e] = fma(s, k[e], base[e]);
+  sync<TEAM>();
+}
+
+// copy a record (any layout) to another
+template <int N, int TEAM>
+__device__ __forceinline__ void copy_rec(int lane, Rec<N> dst, Rec<N> src) {
+  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) {
+    if (e < N * N) dst.A()[e] = src.A()[e];
+    else if (e < N * N + N) dst.b()[e - N * N] = src.b()[e - N * N];
+    else if (e < 2 * N * N + N) dst.C()[e - N * N - N] = src.C()[e - N * N - N];
+    else if (e < 2 * N * N + 2 * N) dst.eta()[e - 2 * N * N - N] = src.eta()[e - 2 * N * N - N];
+    else if (e < 3 * N * N + 2 * N) dst.J()[e - 2 * N * N - 2 * N] = src.J()[e - 2 * N * N - 2 * N];
+    else *dst.zeta() = *src.zeta();
+  }
+  sync<TEAM>();
+}
+
+// ---------------------------------------------------------------------------
+// LU with partial pivoting on W (N x N), applied to R (N x Q); both in the
+// caller's buffers.  piv_scratch: 2 * TEAM doubles + TEAM ints of scratch.
+// ---------------------------------------------------------------------------
+
+template <int N, int TEAM>
+__device__ void lu_solve(int lane, double* W, double* R, int Q, double* fscratch, int* iscratch) {
+  for (int k = 0; k < N; ++k) {
+    // arg max |W[i][k]|, i >= k (lowest index on ties)
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + lane; i < N; i += TEAM) {
+      const double a = fabs(W[i * N + k]);
+      if (a > best) { best = a; bi = i; }
+    }
+    if constexpr (TEAM <= 32) {
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+    } else {
+      fscratch[lane] = best;
+      iscratch[lane] = bi;
+      __syncthreads();
+      for (int w = TEAM / 2; w > 0; w >>= 1) {
+        if (lane < w) {
+          const double ob = fscratch[lane + w];
+          const int oi = iscratch[lane + w];
+          if (ob > fscratch[lane] || (ob == fscratch[lane] && oi < iscratch[lane])) {
+            fscratch[lane] = ob;
+            iscratch[lane] = oi;
+          }
+        }
+        __syncthreads();
+      }
+      bi = iscratch[0];
+      best = fscratch[0];
+      __syncthreads();
+    }
+    if (best == 0.0 && lane == 0) flag(kStatusSingular);
+    if (bi != k) {
+      for (int j = lane; j < N + Q; j += TEAM) {
+        double* a = j < N ? &W[k * N + j] : &R[k * Q + (j - N)];
+        double* b = j < N ? &W[bi * N + j] : &R[bi * Q + (j - N)];
+        const double t = *a;
+        *a = *b;
+        *b = t;
+      }
+    }
+    sync<TEAM>();
+    const double inv = 1.0 / W[k * N + k];
+    // multipliers into column k (below the diagonal)
+    for (int i = k + 1 + lane; i < N; i += TEAM) W[i * N + k] *= inv;
+    sync<TEAM>();
+    const int rows = N - k - 1, cols = N - k - 1 + Q;
+    for (int e = lane; e < rows * cols; e += TEAM) {
+      const int i = k + 1 + e / cols, c = e % cols;
+      const double f = W[i * N + k];
+      if (c < N - k - 1) {
+        const int j = k + 1 + c;
+        W[i * N + j] = fma(-f, W[k * N + j], W[i * N + j]);
+      } else {
+        const int j = c - (N - k - 1);
+        R[i * Q + j] = fma(-f, R[k * Q + j], R[i * Q + j]);
+      }
+    }
+    sync<TEAM>();
+  }
+  // back substitution, one pivot row at a time
+  for (int k = N - 1; k >= 0; --k) {
+    const double inv = 1.0 / W[k * N + k];
+    for (int j = lane; j < Q; j += TEAM) R[k * Q + j] *= inv;
+    sync<TEAM>();
+    for (int e = lane; e < k * Q; e += TEAM) {
+      const int i = e / Q, j = e % Q;
+      R[i * Q + j] = fma(-W[i * N + k], R[k * Q + j], R[i * Q + j]);
+    }
+    sync<TEAM>();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// combination rule
+// ---------------------------------------------------------------------------
+
+// Scratch needs for combine(): W (N^2), R (N (2N+1)), T1 (N^2), vectors 4N,
+// plus lu scratch (2 TEAM doubles, TEAM ints).
+template <int N>
+__host__ __device__ constexpr int combine_scratch_doubles() {
+  return N * N + N * (2 * N + 1) + N * N + 4 * N;
+}
+
+// out = e1 (x) e2 (full elements; out must not alias e1 or e2).
+template <int N, int TEAM>
+__device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr, double* fs, int* is) {
+  constexpr int Q = 2 * N + 1;
+  double* W = scr;
+  double* R = W + N * N;
+  double* T1 = R + N * Q;
+  double* z0 = T1 + N * N;
+  double* l0 = z0 + N;
+  double* J2z = l0 + N;
+  double* wv = J2z + N;
+  // W = I + C1 J2 ; R = [A1 | C1 | b1 + C1 eta2]
+  for (int e = lane; e < N * N + N * Q; e += TEAM) {
+    if (e < N * N) {
+      const int i = e / N, j = e % N;
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int l = 0; l < N; ++l) s = fma(e1.C()[i * N + l], e2.J()[l * N + j], s);
+      W[e] = s;
+    } else {
+      const int t = e - N * N, i = t / Q, j = t % Q;
+      double v;
+      if (j < N) v = e1.A()[i * N + j];
+      else if (j < 2 * N) v = e1.C()[i * N + (j - N)];
+      else {
+        v = e1.b()[i];
+        for (int l = 0; l < N; ++l) v = fma(e1.C()[i * N + l], e2.eta()[l], v);
+      }
+      R[t] = v;
+    }
+  }
+  sync<TEAM>();
+  lu_solve<N, TEAM>(lane, W, R, Q, fs, is);
+  // R = [K1 | MC1 | z0]
+  for (int i = lane; i < N; i += TEAM) z0[i] = R[i * Q + 2 * N];
+  sync<TEAM>();
+  // J2 z0, l0 = J2 z0 - eta2, w = eta2 - J2 b1 ; T1 = J2 A1
+  for (int e = lane; e < 2 * N + N * N; e += TEAM) {
+    if (e < N) {
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(e2.J()[e * N + l], z0[l], s);
+      J2z[e] = s;
+      l0[e] = s - e2.eta()[e];
+    } else if (e < 2 * N) {
+      const int i = e - N;
+      double s = e2.eta()[i];
+      for (int l = 0; l < N; ++l) s = fma(-e2.J()[i * N + l], e1.b()[l], s);
+      wv[i] = s;
+    } else {
+      const int t = e - 2 * N, i = t / N, j = t % N;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(e2.J()[i * N + l], e1.A()[l * N + j], s);
+      T1[t] = s;
+    }
+  }
+  sync<TEAM>();
+  // eta = K1^T w + eta1 ; J = K1^T T1 + J1 (upper, mirrored) ; b = A2 z0 + b2 ;
+  // A = A2 K1 ; zeta (lane 0)
+  constexpr int NS = N * (N + 1) / 2;
+  for (int e = lane; e < N + NS + N + N * N + 1; e += TEAM) {
+    int t = e;
+    if (t < N) {
+      double s = e1.eta()[t];
+      for (int l = 0; l < N; ++l) s = fma(R[l * Q + t], wv[l], s);
+      out.eta()[t] = s;
+      continue;
+    }
+    t -= N;
+    if (t < NS) {
+      int i, j;
+      upper_ij(N, t, i, j);
+      double s = e1.J()[i * N + j];
+      for (int l = 0; l < N; ++l) s = fma(R[l * Q + i], T1[l * N + j], s);
+      out.J()[i * N + j] = s;
+      out.J()[j * N + i] = s;
+      continue;
+    }
+    t -= NS;
+    if (t < N) {
+      double s = e2.b()[t];
+      for (int l = 0; l < N; ++l) s = fma(e2.A()[t * N + l], z0[l], s);
+      out.b()[t] = s;
+      continue;
+    }
+    t -= N;
+    if (t < N * N) {
+      const int i = t / N, j = t % N;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(e2.A()[i * N + l], R[l * Q + j], s);
+      out.A()[t] = s;
+      continue;
+    }
+    double z = *e1.zeta() + *e2.zeta();
+    for (int i = 0; i < N; ++i) {
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(e1.C()[i * N + l], l0[l], s);
+      z = fma(0.5 * l0[i], s, z);
+      z = fma(z0[i], fma(0.5, J2z[i], -e2.eta()[i]), z);
+    }
+    *out.zeta() = z;
+  }
+  sync<TEAM>();
+  // T1 = A2 MC1 ; then C = T1 A2^T + C2
+  for (int e = lane; e < N * N; e += TEAM) {
+    const int i = e / N, j = e % N;
+    double s = 0.0;
+    for (int l = 0; l < N; ++l) s = fma(e2.A()[i * N + l], R[l * Q + N + j], s);
+    T1[e] = s;
+  }
+  sync<TEAM>();
+  for (int t = lane; t < NS; t += TEAM) {
+    int i, j;
+    upper_ij(N, t, i, j);
+    double s = e2.C()[i * N + j];
+    for (int l = 0; l < N; ++l) s = fma(T1[i * N + l], e2.A()[j * N + l], s);
+    out.C()[i * N + j] = s;
+    out.C()[j * N + i] = s;
+  }
+  sync<TEAM>();
+}
+
+// Value form: out = e (x) V, V = (S2 full N^2, v2 N, zeta2); also Psi (N^2) and
+// alpha (N) of the one-sub-interval map.  Value record layout: S (N^2), v (N),
+// zeta.  Scratch: W (N^2), R (N (N+1)), T1 (N^2), 3 vectors.
+template <int N>
+__host__ __device__ constexpr int value_scratch_doubles() {
+  return N * N + N * (N + 1) + N * N + 3 * N;
+}
+template <int N>
+__host__ __device__ constexpr int val_doubles() {
+  return N * N + N + 1;
+}
+
+template <int N, int TEAM>
+__device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, double* Psi, double* alpha,
+                              double* scr, double* fs, int* is) {
+  constexpr int Q = N + 1;
+  const double* S2 = V;
+  const double* v2 = V + N * N;
+  const double zeta2 = V[N * N + N];
+  double* W = scr;
+  double* R = W + N * N;
+  double* T1 = R + N * Q;
+  double* Sz = T1 + N * N;
+  double* l0 = Sz + N;
+  double* wv = l0 + N;
+  for (int t = lane; t < N * N + N * Q; t += TEAM) {
+    if (t < N * N) {
+      const int i = t / N, j = t % N;
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int l = 0; l < N; ++l) s = fma(e.C()[i * N + l], S2[l * N + j], s);
+      W[t] = s;
+    } else {
+      const int u = t - N * N, i = u / Q, j = u % Q;
+      double v;
+      if (j < N) v = e.A()[i * N + j];
+      else {
+        v = e.b()[i];
+        for (int l = 0; l < N; ++l) v = fma(e.C()[i * N + l], v2[l], v);
+      }
+      R[u] = v;
+    }
+  }
+  sync<TEAM>();
+  lu_solve<N, TEAM>(lane, W, R, Q, fs, is);
+  for (int t = lane; t < N * N + N; t += TEAM) {
+    if (t < N * N) Psi[t] = R[(t / N) * Q + (t % N)];
+    else alpha[t - N * N] = R[(t - N * N) * Q + N];
+  }
+  sync<TEAM>();
+  // Sz = S2 alpha, l0 = Sz - v2, w = v2 - S2 b ; T1 = S2 A
+  for (int t = lane; t < 2 * N + N * N; t += TEAM) {
+    if (t < N) {
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(S2[t * N + l], alpha[l], s);
+      Sz[t] = s;
+      l0[t] = s - v2[t];
+    } else if (t < 2 * N) {
+      const int i = t - N;
+      double s = v2[i];
+      for (int l = 0; l < N; ++l) s = fma(-S2[i * N + l], e.b()[l], s);
+      wv[i] = s;
+    } else {
+      const int u = t - 2 * N, i = u / N, j = u % N;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(S2[i * N + l], e.A()[l * N + j], s);
+      T1[u] = s;
+    }
+  }
+  sync<TEAM>();
+  constexpr int NS = N * (N + 1) / 2;
+  double* So = out;
+  double* vo = out + N * N;
+  for (int t = lane; t < N + NS + 1; t += TEAM) {
+    if (t < N) {
+      double s = e.eta()[t];
+      for (int l = 0; l < N; ++l) s = fma(Psi[l * N + t], wv[l], s);
+      vo[t] = s;
+    } else if (t < N + NS) {
+      int i, j;
+      upper_ij(N, t - N, i, j);
+      double s = e.J()[i * N + j];
+      for (int l = 0; l < N; ++l) s = fma(Psi[l * N + i], T1[l * N + j], s);
+      So[i * N + j] = s;
+      So[j * N + i] = s;
+    } else {
+      double z = *e.zeta() + zeta2;
+      for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int l = 0; l < N; ++l) s = fma(e.C()[i * N + l], l0[l], s);
+        z = fma(0.5 * l0[i], s, z);
+        z = fma(alpha[i], fma(0.5, Sz[i], -v2[i]), z);
+      }
+      out[N * N + N] = z;
+    }
+  }
+  sync<TEAM>();
+}
+
+// (P, p) <- (P Psi, P alpha + p) ; T scratch N^2 + N.
+template <int N, int TEAM>
+__device__ void compose_right(int lane, double* P, double* p, const double* Psi, const double* alpha, double* Tm) {
+  for (int t = lane; t < N * N + N; t += TEAM) {
+    if (t < N * N) {
+      const int i = t / N, j = t % N;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(P[i * N + l], Psi[l * N + j], s);
+      Tm[t] = s;
+    } else {
+      const int i = t - N * N;
+      double s = p[i];
+      for (int l = 0; l < N; ++l) s = fma(P[i * N + l], alpha[l], s);
+      Tm[t] = s;
+    }
+  }
+  sync<TEAM>();
+  for (int t = lane; t < N * N + N; t += TEAM) {
+    if (t < N * N) P[t] = Tm[t];
+    else p[t - N * N] = Tm[t];
+  }
+  sync<TEAM>();
+}
+
+}  // namespace team
+}  // namespace lqt
+
+namespace lqt {
+namespace team {
+
+// (P, p) <- (Psi P, Psi p + alpha): apply the group's earlier maps first.
+template <int N, int TEAM>
+__device__ void compose_left(int lane, double* P, double* p, const double* Psi, const double* alpha, double* Tm) {
+  for (int t = lane; t < N * N + N; t += TEAM) {
+    if (t < N * N) {
+      const int i = t / N, j = t % N;
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(Psi[i * N + l], P[l * N + j], s);
+      Tm[t] = s;
+    } else {
+      const int i = t - N * N;
+      double s = alpha[i];
+      for (int l = 0; l < N; ++l) s = fma(Psi[i * N + l], p[l], s);
+      Tm[t] = s;
+    }
+  }
+  sync<TEAM>();
+  for (int t = lane; t < N * N + N; t += TEAM) {
+    if (t < N * N) P[t] = Tm[t];
+    else p[t - N * N] = Tm[t];
+  }
+  sync<TEAM>();
+}
+
+// y = Psi x + alpha
+template <int N, int TEAM>
+__device__ void apply_map(int lane, const double* Psi, const double* alpha, const double* x, double* y) {
+  for (int i = lane; i < N; i += TEAM) {
+    double s = alpha[i];
+    for (int l = 0; l < N; ++l) s = fma(Psi[i * N + l], x[l], s);
+    y[i] = s;
+  }
+  sync<TEAM>();
+}
+
+}  // namespace team
+}  // namespace lqt

@@ -58,6 +58,10 @@ CASES = [
     ("T1", lambda: W.general_time_varying(3, 1, 3, T=1, K=4, seed=26, tf=0.5)),
     ("T2", lambda: W.general_time_varying(2, 2, 2, T=2, K=1, seed=27)),
     ("T3", lambda: W.general_time_varying(4, 2, 4, T=3, K=2, seed=28)),
+    ("n16_m8_T40_general", lambda: W.general_time_varying(16, 8, 16, T=40, K=2, seed=81, tf=1.0)),
+    ("n16_batched_member_T300", lambda: W.batched_member(7, T=300, n=16)),
+    ("n64_m16_T64", lambda: W.large_state_n64(T=64)),
+    ("n64_m16_T129_ragged", lambda: W.large_state_n64(T=129)),
 ]
 
 
