@@ -184,6 +184,47 @@ lqt_status lqt_backward(const lqt_problem *p, const double *x0, const double *S,
                         double g_cost, double *gF, double *gL, double *gX, double *gU, double *gr, double *gXf,
                         double *grf, double *gx0, void *ws, size_t ws_bytes, void *stream);
 
+/* Batches: many independent problems of ONE state dimension n solved by one
+ * call (problems of several dimensions: one call per dimension, e.g. captured
+ * together in one CUDA graph).  All problems share n, m, nr = n, K and the
+ * sampling mode of r; F, L, X, U (and c, if given) are constant per problem;
+ * H = Hf = NULL.  Each problem keeps its own T, time grid and data.
+ * The problems are laid end to end: problem b's boundaries are
+ * [off_b, off_b + T_b] of the concatenated outputs, off_b = sum_{b'<b}
+ * (T_b' + 1): S [total][n][n], v [total][n], zeta [total], x [total][n],
+ * u [total][m] (may be NULL), cost [count] (may be NULL), total =
+ * lqt_batch_boundaries().  Internally one value scan and one state scan run
+ * over the whole concatenation: a terminal element (A = b = C = 0, Sec. IV-D)
+ * separates the problems' values exactly; the only leak, additive in zeta, is
+ * removed afterwards, and the state map at each problem's end is replaced by
+ * a jump to the next problem's x0. */
+typedef struct {
+  int32_t count;                 /* number of problems B >= 1 */
+  const lqt_problem *problems;   /* HOST array of B descriptors (their data pointers are device pointers) */
+  const double *const *x0;       /* HOST array of B device pointers, each [n] */
+} lqt_batch;
+
+/* Tunables of the batched solve, chosen by the caller's autotuner.
+ * chunk: sub-intervals per thread (per team for n >= 16) in the first scan
+ * level, a power of two in [2, 32]; 0 = built-in choice. */
+typedef struct {
+  int32_t chunk;
+  int32_t reserved;
+} lqt_tuning;
+
+size_t lqt_batch_workspace_size(const lqt_batch *b);
+int64_t lqt_batch_boundaries(const lqt_batch *b);
+
+/* Writes the batch's device-side tables (per-problem descriptors, offsets)
+ * into the workspace and synchronises the stream.  Call once per batch and
+ * workspace, before lqt_solve_batched (and before any stream capture). */
+lqt_status lqt_batch_plan(const lqt_batch *b, void *ws, size_t ws_bytes, void *stream);
+
+/* Solves the planned batch: launches only (no copies, no synchronisation), so
+ * it can be captured in a CUDA graph. */
+lqt_status lqt_solve_batched(const lqt_batch *b, const lqt_tuning *tune, double *S, double *v, double *zeta,
+                             double *x, double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
 /* End-to-end convenience call on HOST buffers: the problem's pointers (t, the
  * coefficients, Hf, Xf, rf) and x0 point at host memory, and so do the
  * outputs.  Copies the inputs to the caller's device workspace (its size from

@@ -20,7 +20,8 @@ LQT_STATIC_SCRATCH_BYTES = 16 << 20
 EXPORTED = (
     "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value", "lqt_scan_trajectory", "lqt_solve",
     "lqt_solve_sequential", "lqt_host_staging_size", "lqt_solve_host", "lqt_get_status", "lqt_strerror",
-    "lqt_last_launch_count", "lqt_scan_value_noalloc", "lqt_backward",
+    "lqt_last_launch_count", "lqt_scan_value_noalloc", "lqt_backward", "lqt_batch_workspace_size",
+    "lqt_batch_boundaries", "lqt_batch_plan", "lqt_solve_batched",
 )
 
 _dp = ct.POINTER(ct.c_double)
@@ -44,6 +45,14 @@ class lqt_problem(ct.Structure):
 class lqt_elements(ct.Structure):
     _fields_ = [("A", ct.c_void_p), ("b", ct.c_void_p), ("C", ct.c_void_p), ("eta", ct.c_void_p),
                 ("J", ct.c_void_p), ("zeta", ct.c_void_p)]
+
+
+class lqt_batch(ct.Structure):
+    _fields_ = [("count", ct.c_int32), ("problems", ct.POINTER(lqt_problem)), ("x0", ct.POINTER(ct.c_void_p))]
+
+
+class lqt_tuning(ct.Structure):
+    _fields_ = [("chunk", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class LQTError(RuntimeError):
@@ -81,6 +90,15 @@ def lib():
     L.lqt_strerror.restype = ct.c_char_p
     L.lqt_backward.argtypes = [P, v, v, v, v, v, v, v, v, v, ct.c_double, v, v, v, v, v, v, v, v, v, ct.c_size_t, v]
     L.lqt_backward.restype = ct.c_int
+    Bp = ct.POINTER(lqt_batch)
+    L.lqt_batch_workspace_size.argtypes = [Bp]
+    L.lqt_batch_workspace_size.restype = ct.c_size_t
+    L.lqt_batch_boundaries.argtypes = [Bp]
+    L.lqt_batch_boundaries.restype = ct.c_int64
+    L.lqt_batch_plan.argtypes = [Bp, v, ct.c_size_t, v]
+    L.lqt_batch_plan.restype = ct.c_int
+    L.lqt_solve_batched.argtypes = [Bp, ct.POINTER(lqt_tuning), v, v, v, v, v, v, v, ct.c_size_t, v]
+    L.lqt_solve_batched.restype = ct.c_int
     L.lqt_scan_value_noalloc.argtypes = [P, E, v, v, v, v]
     L.lqt_scan_value_noalloc.restype = ct.c_int
     L.lqt_last_launch_count.argtypes = []

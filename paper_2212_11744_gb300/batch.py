@@ -1,0 +1,136 @@
+"""Batched solves (lqt_solve_batched) and their autotuner.
+
+    b = Batch(problems)            # problems of one state dimension
+    out = b.solve()                # concatenated S, v, zeta, x, u and per-problem cost
+    b.autotune()                   # picks the first-level chunk length by timing
+
+Marshalling only: the per-problem arrays of a batch are packed into a few
+device tensors and the C descriptors point into them.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import lqt_batch, lqt_coef, lqt_problem, lqt_tuning
+
+_TUNED = {}
+
+
+class Batch:
+    def __init__(self, problems, device: str = "cuda"):
+        if not problems:
+            raise ValueError("empty batch")
+        self.device = torch.device(device)
+        self.B = len(problems)
+        p0 = problems[0]
+        self.n, self.m = p0.n, p0.m
+        # pack every per-problem array into one host buffer, upload once
+        chunks, offs = [], {}
+        pos = 0
+
+        def add(key, a):
+            nonlocal pos
+            if a is None:
+                offs[key] = None
+                return
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            offs[key] = pos
+            chunks.append(a)
+            pos += a.size
+
+        for b, p in enumerate(problems):
+            add((b, "t"), p.t)
+            for name in ("F", "L", "c", "X", "U", "r"):
+                co = getattr(p, name)
+                add((b, name), None if co is None else co.values)
+            add((b, "Xf"), p.Xf)
+            add((b, "rf"), p.rf)
+            add((b, "x0"), p.x0)
+        self.data = torch.from_numpy(np.concatenate(chunks)).to(self.device)
+        base = self.data.data_ptr()
+
+        def ptr(key):
+            o = offs[key]
+            return None if o is None else base + 8 * o
+
+        arr = (lqt_problem * self.B)()
+        x0s = (ct.c_void_p * self.B)()
+        self.T = np.zeros(self.B, dtype=np.int64)
+        for b, p in enumerate(problems):
+            s = arr[b]
+            s.n, s.m, s.nr, s.T, s.K = p.n, p.m, p.nr, p.T, p.K
+            s.t = ptr((b, "t"))
+            for name in ("F", "L", "c", "H", "X", "U", "r"):
+                co = getattr(p, name)
+                if name == "H" or co is None:
+                    setattr(s, name, lqt_coef(None, 0))
+                else:
+                    setattr(s, name, lqt_coef(ptr((b, name)), int(co.mode)))
+            s.Hf = None
+            s.Xf = ptr((b, "Xf"))
+            s.rf = ptr((b, "rf"))
+            x0s[b] = ptr((b, "x0"))
+            self.T[b] = p.T
+        self._arr, self._x0s = arr, x0s
+        self.struct = lqt_batch(self.B, ct.cast(arr, ct.POINTER(lqt_problem)), ct.cast(x0s, ct.POINTER(ct.c_void_p)))
+        L = _abi.lib()
+        self.total = int(L.lqt_batch_boundaries(ct.byref(self.struct)))
+        nbytes = int(L.lqt_batch_workspace_size(ct.byref(self.struct)))
+        if nbytes == 0 or self.total == 0:
+            raise _abi.LQTError(_abi.LQT_EINVAL, "lqt_batch_workspace_size")
+        self.offsets = np.concatenate([[0], np.cumsum(self.T + 1)])
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _abi.check(L.lqt_batch_plan(ct.byref(self.struct), self.ws.data_ptr(), self.ws.numel(),
+                                    torch.cuda.current_stream(self.device).cuda_stream), "lqt_batch_plan")
+        self.chunk = 0
+
+    def new_outputs(self):
+        n, m, N = self.n, self.m, self.total
+        e = lambda *s: torch.empty(*s, dtype=torch.float64, device=self.device)
+        return {"S": e(N, n, n), "v": e(N, n), "zeta": e(N), "x": e(N, n), "u": e(N, m), "cost": e(self.B)}
+
+    def solve(self, out=None, chunk=None, stream=None) -> dict:
+        out = self.new_outputs() if out is None else out
+        tune = lqt_tuning(self.chunk if chunk is None else chunk, 0)
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        _abi.check(_abi.lib().lqt_solve_batched(
+            ct.byref(self.struct), ct.byref(tune), out["S"].data_ptr(), out["v"].data_ptr(), out["zeta"].data_ptr(),
+            out["x"].data_ptr(), out["u"].data_ptr(), out["cost"].data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+            st.cuda_stream), "lqt_solve_batched")
+        return out
+
+    def problem_slice(self, out, b):
+        lo, hi = int(self.offsets[b]), int(self.offsets[b + 1])
+        return {k: (v[lo:hi] if k != "cost" else v[b]) for k, v in out.items()}
+
+    def autotune(self, candidates=(0, 2, 4, 8, 16, 32), reps: int = 3) -> int:
+        """Times the batched solve for each first-level chunk length and keeps
+        the fastest (cached per state dimension, problem count and total
+        boundaries)."""
+        key = (self.n, self.B, self.total)
+        if key in _TUNED:
+            self.chunk = _TUNED[key][0]
+            return self.chunk
+        out = self.new_outputs()
+        timings = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for c in candidates:
+            self.solve(out, chunk=c)
+            e0.record()
+            for _ in range(reps):
+                self.solve(out, chunk=c)
+            e1.record()
+            torch.cuda.synchronize()
+            timings[c] = e0.elapsed_time(e1) / reps
+        best = min(timings, key=timings.get)
+        _TUNED[key] = (best, timings)
+        self.chunk = best
+        return best
+
+    @staticmethod
+    def tuning_table():
+        return dict(_TUNED)

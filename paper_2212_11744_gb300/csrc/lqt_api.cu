@@ -15,6 +15,7 @@ __device__ unsigned g_status_word = 0;
 
 static thread_local int32_t t_launches = 0;
 void count_launch(int k) { t_launches += k; }
+void reset_launch_count() { t_launches = 0; }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 

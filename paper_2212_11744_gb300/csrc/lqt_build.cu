@@ -399,13 +399,13 @@ __device__ __forceinline__ const double* coef_at(const Coef& c, int64_t j, int32
   return c.ptr + sample_index(c.mode, j, p, K) * stride;
 }
 
+// K classical RK4 steps of the backward conditional HJB ODEs for sub-interval
+// j, from the boundary A = I, b = C = eta = J = 0, zeta = 0 at s = t_{j+1}
+// down to s = t_j (Sec. IV-B, eq. abcej_boundary).
 template <int N, int M>
-__global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.T) return;
-  const int32_t K = a.K;
-  const double h = (a.t[j + 1] - a.t[j]) / K;
-  Elem<N> y, yn, yt, k;
+__device__ __forceinline__ void build_one(const Coefs& cf, const double* t, int64_t j, int32_t K, Elem<N>& y) {
+  const double h = (t[j + 1] - t[j]) / K;
+  Elem<N> yn, yt, k;
 #pragma unroll
   for (int i = 0; i < N * N; ++i) y.A[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
 #pragma unroll
@@ -419,7 +419,6 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
     y.J[i] = 0.0;
   }
   y.zeta = 0.0;
-  const Coefs& cf = a.cf;
   for (int32_t i = K - 1; i >= 0; --i) {
     // stage times (in half steps from t_j): 2i+2, 2i+1, 2i+1, 2i
     const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
@@ -448,6 +447,14 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
     element_rhs<N, M>(yt, F[2], c[2], Lt[2], Q[2], qr[2], k);
     axpy_to(y, yn, -h / 6.0, k);
   }
+}
+
+template <int N, int M>
+__global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.T) return;
+  Elem<N> y;
+  build_one<N, M>(a.cf, a.t, j, a.K, y);
   store_public<N>(a.out, j, y);
 }
 
@@ -508,6 +515,148 @@ cudaError_t launch_terminal_values(const lqt_problem& p, double* J, double* eta,
   TermArgs t{p.n, p.nr, p.Hf, p.Xf, p.rf, nullptr, nullptr, nullptr, eta, J, zeta};
   terminal_kernel<<<(p.n * p.n + 255) / 256, 256, 0, st>>>(t);
   count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batches: coefficient preparation and element build over the concatenation
+// ---------------------------------------------------------------------------
+
+// which = 0: Lt and Ku of every problem (constant L, U); which = 1: q = X r,
+// rho = r'Xr of every qr sample (X constant, H = identity).
+__global__ void batch_prepare_kernel(BatchDev bd, int which) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = bd.n, m = bd.m;
+  if (which == 0) {
+    if (g >= bd.B) return;
+    const BatchProb& P = bd.probs[g];
+    double R[kMaxM * kMaxM];
+    for (int i = 0; i < m * m; ++i) R[i] = P.U[i];
+    cholesky_lower(R, m);
+    double* Lt = const_cast<double*>(P.cf.Lt.ptr);
+    for (int i = 0; i < n; ++i) {
+      double row[kMaxM];
+      for (int c = 0; c < m; ++c) {
+        double v = P.L[i * m + c];
+        for (int k = 0; k < c; ++k) v -= row[k] * R[c * m + k];
+        row[c] = v / R[c * m + c];
+      }
+      for (int c = 0; c < bd.M; ++c) Lt[i * bd.M + c] = c < m ? row[c] : 0.0;
+    }
+    double* Ku = const_cast<double*>(P.cf.Ku);
+    for (int col = 0; col < n; ++col) {
+      double y[kMaxM];
+      for (int i = 0; i < m; ++i) {
+        double v = P.L[col * m + i];
+        for (int k = 0; k < i; ++k) v -= R[i * m + k] * y[k];
+        y[i] = v / R[i * m + i];
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < m; ++k) v -= R[k * m + i] * y[k];
+        y[i] = v / R[i * m + i];
+      }
+      for (int i = 0; i < m; ++i) Ku[i * n + col] = y[i];
+    }
+  } else {
+    if (g >= bd.total_qr) return;
+    const int32_t b = batch_find(bd.off_qr, bd.B, g);
+    const BatchProb& P = bd.probs[b];
+    const int64_t s = g - bd.off_qr[b];
+    const double* r = P.r ? P.r + (P.r_mode == kConst ? 0 : s) * n : nullptr;
+    double* out = const_cast<double*>(P.cf.qr.ptr) + s * (n + 1);
+    double rho = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double v = 0.0;
+      if (r)
+        for (int l = 0; l < n; ++l) v = fma(P.X[i * n + l], r[l], v);
+      out[i] = v;
+      if (r) rho = fma(r[i], v, rho);
+    }
+    out[n] = rho;
+  }
+}
+
+cudaError_t batch_prepare(const BatchDev& bd, cudaStream_t st) {
+  batch_prepare_kernel<<<(unsigned)((bd.B + 127) / 128), 128, 0, st>>>(bd, 0);
+  count_launch();
+  batch_prepare_kernel<<<(unsigned)((bd.total_qr + 127) / 128), 128, 0, st>>>(bd, 1);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// One thread per boundary of the concatenation: element j of problem b, or its
+// terminal element (j = T_b; Hf = identity: J = Xf, eta = Xf rf,
+// zeta = rf'Xf rf / 2).
+template <int N, int M>
+__global__ void __launch_bounds__(128) batch_build_kernel(BatchDev bd, ElemPtrs out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= bd.total) return;
+  const int32_t b = batch_find(bd.off, bd.B, g);
+  const BatchProb& P = bd.probs[b];
+  const int64_t j = g - P.off;
+  Elem<N> y;
+  if (j < P.T) {
+    build_one<N, M>(P.cf, P.t, j, bd.K, y);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) y.A[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      y.b[i] = 0.0;
+      double e = 0.0;
+      if (P.rf)
+        for (int l = 0; l < N; ++l) e = fma(P.Xf[i * N + l], P.rf[l], e);
+      y.eta[i] = e;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int c = i; c < N; ++c) {
+        y.C[sidx<N>(i, c)] = 0.0;
+        y.J[sidx<N>(i, c)] = 0.5 * (P.Xf[i * N + c] + P.Xf[c * N + i]);
+      }
+    double z = 0.0;
+    if (P.rf)
+      for (int i = 0; i < N; ++i) z = fma(P.rf[i], y.eta[i], z);
+    y.zeta = 0.5 * z;
+  }
+  store_public<N>(out, g, y);
+}
+
+template <int N, int M>
+static void launch_batch_build_nm(const BatchDev& bd, const ElemPtrs& el, cudaStream_t st) {
+  batch_build_kernel<N, M><<<(unsigned)((bd.total + 127) / 128), 128, 0, st>>>(bd, el);
+  count_launch();
+}
+
+cudaError_t batch_build(const BatchDev& bd, const ElemPtrs& el, char* team_scratch, cudaStream_t st) {
+  switch (bd.n) {
+    case 1: launch_batch_build_nm<1, 1>(bd, el, st); break;
+    case 2:
+      if (bd.M == 1) launch_batch_build_nm<2, 1>(bd, el, st);
+      else launch_batch_build_nm<2, 2>(bd, el, st);
+      break;
+    case 3:
+      if (bd.M == 1) launch_batch_build_nm<3, 1>(bd, el, st);
+      else if (bd.M == 2) launch_batch_build_nm<3, 2>(bd, el, st);
+      else launch_batch_build_nm<3, 4>(bd, el, st);
+      break;
+    case 4:
+      if (bd.M == 1) launch_batch_build_nm<4, 1>(bd, el, st);
+      else if (bd.M == 2) launch_batch_build_nm<4, 2>(bd, el, st);
+      else launch_batch_build_nm<4, 4>(bd, el, st);
+      break;
+    case 8:
+      if (bd.M == 1) launch_batch_build_nm<8, 1>(bd, el, st);
+      else if (bd.M == 2) launch_batch_build_nm<8, 2>(bd, el, st);
+      else if (bd.M == 4) launch_batch_build_nm<8, 4>(bd, el, st);
+      else launch_batch_build_nm<8, 8>(bd, el, st);
+      break;
+    case 16:
+    case 64: return batch_build_team(bd, el, (double*)team_scratch, st);
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ inline int32_t combine_modes(int32_t a, int32_t b) {
 
 // Launch-count accounting (per host thread).
 void count_launch(int k = 1);
+void reset_launch_count();
 
 // -------------------------------------------------------------------------
 // launchers (defined in the .cu files, dispatched on n)
@@ -126,5 +127,66 @@ size_t sequential_workspace_bytes(int32_t n, int64_t T, int32_t K);
 cudaError_t launch_sequential(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* x0,
                               double* S, double* v, double* zeta, double* x, double* u, double* cost, char* ws,
                               cudaStream_t s);
+
+// -------------------------------------------------------------------------
+// batches of independent problems of one state dimension (lqt_batched.cu)
+// -------------------------------------------------------------------------
+
+// One problem of a batch, as the kernels see it.
+struct BatchProb {
+  int64_t T;    // sub-intervals
+  int64_t off;  // its first boundary in the concatenation
+  const double* t;
+  Coefs cf;     // coefficients in kernel form (derived ones in the workspace)
+  const double *Xf, *rf, *x0;
+  // inputs of the coefficient preparation
+  const double *L, *U, *X, *r;
+  int32_t r_mode;
+  int64_t off_qr;  // first qr sample of this problem in the concatenated qr array
+};
+
+struct BatchDev {
+  int32_t B, n, m, K, M;
+  const BatchProb* probs;  // device [B]
+  const int64_t* off;      // device [B+1]: boundary offsets, off[B] = total boundaries
+  const int64_t* off_qr;   // device [B+1]: qr sample offsets
+  int64_t total;           // sum of (T_b + 1)
+  int64_t total_qr;
+};
+
+__host__ __device__ __forceinline__ int32_t batch_find(const int64_t* off, int32_t B, int64_t g) {
+  int32_t lo = 0, hi = B;  // off[lo] <= g < off[hi]
+  while (hi - lo > 1) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+cudaError_t batch_prepare(const BatchDev& bd, cudaStream_t st);
+cudaError_t batch_build(const BatchDev& bd, const ElemPtrs& el, char* team_scratch, cudaStream_t st);
+cudaError_t batch_build_team(const BatchDev& bd, const ElemPtrs& el, double* gscratch, cudaStream_t st);
+
+// Concatenated scan: value scan over `Tcat + 1` elements, then the boundary maps
+// of every problem but the last replaced by x -> x0 of the next problem, then
+// the state scan from x0 of the first problem (controls not computed).
+struct BoundaryPatch {
+  int32_t B;
+  const int64_t* off;       // device [B+1]
+  const BatchProb* probs;   // device [B] (x0 of each problem)
+};
+size_t concat_workspace_bytes(int32_t n, int64_t Tcat);
+cudaError_t concat_scan(int32_t n, int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,
+                        const double* x0_first, double* x, const BoundaryPatch& patch, char* ws, cudaStream_t st);
+size_t team_concat_workspace_bytes(int32_t n, int64_t Tcat);
+cudaError_t team_concat_scan(int32_t n, int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,
+                             const double* x0_first, double* x, const BoundaryPatch& patch, char* ws,
+                             cudaStream_t st);
+void launch_boundary_patch(int n, double* maps, const BoundaryPatch& patch, cudaStream_t st);
+
+// Level-0 chunk length override for the scans (0 = built-in heuristic); set by
+// the batched entry point from its tuning argument.
+void set_scan_chunk(int g);
 
 }  // namespace lqt

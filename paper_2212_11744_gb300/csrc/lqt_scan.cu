@@ -26,9 +26,15 @@ namespace lqt {
 
 constexpr int kUpperGroup = 2;
 
+static thread_local int t_chunk_override = 0;
+void set_scan_chunk(int g) { t_chunk_override = g; }
+int scan_chunk_override() { return t_chunk_override; }
+
 // Level-0 chunk length from T: longest power of two <= 32 that still leaves
-// >= 16384 chunks (so every sub-partition has a warp), at least 2.
+// >= 16384 chunks (so every sub-partition has a warp), at least 2; or the
+// caller's override.
 static int level0_group(int64_t T) {
+  if (t_chunk_override >= 2) return t_chunk_override;
   int g = 2;
   while (g < 32 && (T + 1) / (2 * g) >= 16384) g *= 2;
   return g;
@@ -591,6 +597,63 @@ static void affine_scan_n(const double* maps, int64_t cnt, const double* x_in, d
     double* outst = (l == 0) ? states : sv[l - 1];
     down_maps_kernel<N><<<blocks_for(ceil_div(mcnt, G)), 128, 0, st>>>(mp, mcnt, G, sv[l], x_in, outst);
     count_launch();
+  }
+}
+
+// Problem b's boundary map (index off[b+1] - 1 of the concatenation, its
+// terminal element) becomes x -> x0 of problem b+1.
+__global__ void boundary_patch_kernel(int n, double* maps, BoundaryPatch pt) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b + 1 >= pt.B) return;
+  const int64_t k = pt.off[b + 1] - 1;
+  double* mp = maps + k * (n * n + n);
+  for (int i = 0; i < n * n; ++i) mp[i] = 0.0;
+  const double* x0 = pt.probs[b + 1].x0;
+  for (int i = 0; i < n; ++i) mp[n * n + i] = x0[i];
+}
+
+void launch_boundary_patch(int n, double* maps, const BoundaryPatch& patch, cudaStream_t st) {
+  if (patch.B < 2) return;
+  boundary_patch_kernel<<<(unsigned)ceil_div(patch.B, 128), 128, 0, st>>>(n, maps, patch);
+  count_launch();
+}
+
+template <int N>
+static cudaError_t concat_n(int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,
+                            const double* x0_first, double* x, const BoundaryPatch& patch, char* ws,
+                            cudaStream_t st) {
+  const ScanPlan pl = make_plan<N>(Tcat, true);
+  double* maps0 = (double*)(ws + pl.off_maps);
+  DownOut o{};
+  o.S = S; o.v = v; o.zeta = zeta; o.T = Tcat; o.maps = maps0; o.composite = nullptr;
+  value_scan<N>(pl, el, o, ws, st);
+  launch_boundary_patch(N, maps0, patch, st);
+  if (pl.tlev > 0) {
+    const int64_t cnt = pl.tcnt[0] * pl.G0 < Tcat ? pl.tcnt[0] * pl.G0 : Tcat;
+    reduce_maps_kernel<N><<<blocks_for(pl.tcnt[0]), 128, 0, st>>>(maps0, cnt, pl.G0, (double*)(ws + pl.off_tmap[0]));
+    count_launch();
+  }
+  Coefs cf{};
+  traj_scan<N>(pl, x0_first, S, v, zeta, cf, 0, x, nullptr, nullptr, ws, st);
+  return cudaGetLastError();
+}
+
+size_t concat_workspace_bytes(int32_t n, int64_t Tcat) {
+  if (n == 16 || n == 64) return team_concat_workspace_bytes(n, Tcat);
+  return scan_workspace_bytes(n, Tcat, true);
+}
+
+cudaError_t concat_scan(int32_t n, int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,
+                        const double* x0_first, double* x, const BoundaryPatch& patch, char* ws, cudaStream_t st) {
+  switch (n) {
+    case 1: return concat_n<1>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    case 2: return concat_n<2>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    case 3: return concat_n<3>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    case 4: return concat_n<4>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    case 8: return concat_n<8>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    case 16:
+    case 64: return team_concat_scan(n, Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -79,6 +79,40 @@ struct TeamBuildArgs {
   double* gscratch;
 };
 
+// Element j of a problem (coefficients cf, grid t) into the packed record at
+// yb; the other buffers are scratch.
+template <int N, int M>
+__device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64_t j, int32_t K, double* yb,
+                               double* ynb, double* ytb, double* kb, double* AL, double* P, double* w) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
+  const double h = (t[j + 1] - t[j]) / K;
+  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
+  team::sync<TEAM>();
+  for (int32_t i = K - 1; i >= 0; --i) {
+    const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
+    const double *F[3], *c[3], *Lt[3], *Q[3], *qr[3];
+    for (int q = 0; q < 3; ++q) {
+      F[q] = cf.F.ptr + sample_index(cf.F.mode, j, ps[q], K) * N * N;
+      c[q] = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, ps[q], K) * N : nullptr;
+      Lt[q] = cf.Lt.ptr + sample_index(cf.Lt.mode, j, ps[q], K) * N * M;
+      Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * N * N;
+      qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
+    }
+    team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w);
+    team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
+    team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
+    team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
+    team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
+    team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
+    team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w);
+    team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
+  }
+}
+
 template <int N, int M>
 __global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_kernel(TeamBuildArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
@@ -92,38 +126,65 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_kernel(TeamBuildA
   double* AL = kb + Rec<N>::SIZE;
   double* P = AL + N * M;
   double* w = P + N * M;
-  const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
-  const int32_t K = a.K;
-  const Coefs& cf = a.cf;
   for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
-    const double h = (a.t[j + 1] - a.t[j]) / K;
-    for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
-    team::sync<TEAM>();
-    for (int32_t i = K - 1; i >= 0; --i) {
-      const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
-      const double *F[3], *c[3], *Lt[3], *Q[3], *qr[3];
-      for (int q = 0; q < 3; ++q) {
-        F[q] = cf.F.ptr + sample_index(cf.F.mode, j, ps[q], K) * N * N;
-        c[q] = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, ps[q], K) * N : nullptr;
-        Lt[q] = cf.Lt.ptr + sample_index(cf.Lt.mode, j, ps[q], K) * N * M;
-        Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * N * N;
-        qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
-      }
-      team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w);
-      team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
-      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
-      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
-      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
-      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
-      team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w);
-      team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
-    }
+    team_build_one<N, M>(lane, a.cf, a.t, j, a.K, yb, ynb, ytb, kb, AL, P, w);
     double zz = 0.0;
     Rec<N> dst = Rec<N>::pub(a.out, j, &zz);
-    team::copy_rec<N, TEAM>(lane, dst, y);
+    team::copy_rec<N, TEAM>(lane, dst, Rec<N>::packed(yb));
+  }
+}
+
+// Batches: one team per boundary of the concatenation (element or terminal).
+template <int N, int M>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) batch_build_team_kernel(BatchDev bd, ElemPtrs out,
+                                                                           double* gscratch) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int SD = build_slot_doubles<N, M>();
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(gscratch, SD);
+  double* yb = base;
+  double* ynb = yb + Rec<N>::SIZE;
+  double* ytb = ynb + Rec<N>::SIZE;
+  double* kb = ytb + Rec<N>::SIZE;
+  double* AL = kb + Rec<N>::SIZE;
+  double* P = AL + N * M;
+  double* w = P + N * M;
+  for (int64_t g = blockIdx.x; g < bd.total; g += gridDim.x) {
+    const int32_t b = batch_find(bd.off, bd.B, g);
+    const BatchProb& pb = bd.probs[b];
+    const int64_t j = g - pb.off;
+    if (j < pb.T) {
+      team_build_one<N, M>(lane, pb.cf, pb.t, j, bd.K, yb, ynb, ytb, kb, AL, P, w);
+    } else {
+      const Rec<N> y = Rec<N>::packed(yb);
+      for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = 0.0;
+      team::sync<TEAM>();
+      for (int e = lane; e < N * N + N + 1; e += TEAM) {
+        if (e < N * N) {
+          const int i = e / N, c = e % N;
+          y.J()[e] = 0.5 * (pb.Xf[i * N + c] + pb.Xf[c * N + i]);
+        } else if (e < N * N + N) {
+          const int i = e - N * N;
+          double v = 0.0;
+          if (pb.rf)
+            for (int l = 0; l < N; ++l) v = fma(pb.Xf[i * N + l], pb.rf[l], v);
+          y.eta()[i] = v;
+        } else {
+          double z = 0.0;
+          if (pb.rf)
+            for (int i = 0; i < N; ++i) {
+              double v = 0.0;
+              for (int l = 0; l < N; ++l) v = fma(pb.Xf[i * N + l], pb.rf[l], v);
+              z = fma(pb.rf[i], v, z);
+            }
+          *y.zeta() = 0.5 * z;
+        }
+      }
+      team::sync<TEAM>();
+    }
+    double zz = 0.0;
+    Rec<N> dst = Rec<N>::pub(out, g, &zz);
+    team::copy_rec<N, TEAM>(lane, dst, Rec<N>::packed(yb));
   }
 }
 
@@ -378,8 +439,11 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) final_team_kernel(TeamFinalA
 // host side
 // ---------------------------------------------------------------------------
 
+int scan_chunk_override();
+
 template <int N>
 static int team_group0(int64_t T) {
+  if (scan_chunk_override() >= 2) return scan_chunk_override();
   const int64_t want = TeamCfg<N>::SLOTS;  // chunks that keep every slot busy
   int g = 2;
   while (g < 32 && (T + 1) / (2 * g) >= want) g *= 2;
@@ -528,6 +592,114 @@ static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtr
   f.x0 = x0; f.S = S; f.v = v; f.zeta = zeta; f.Ku = cf.Ku; f.Ku_per_boundary = cf.Ku_per_boundary; f.m = p.m;
   f.x = x; f.u = u; f.cost = cost; f.gscratch = gs;
   team_launch<N>(final_team_kernel<N>, tdiv(p.T + 1, pl.G0), maps_slot_doubles<N>(), f, st);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t team_concat(int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,
+                               const double* x0_first, double* x, const BoundaryPatch& patch, char* ws,
+                               cudaStream_t st) {
+  const TeamPlan<N> pl = team_plan<N>(Tcat, true);
+  double* gs = TeamCfg<N>::SMEM ? nullptr : (double*)(ws + pl.off_scratch);
+  double* maps0 = (double*)(ws + pl.off_maps);
+  // value scan with the level-0 maps
+  int64_t c = Tcat + 1;
+  int G = pl.G0;
+  for (int l = 0; l < pl.nlev; ++l) {
+    TeamScanArgs a{};
+    a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
+    a.agg = (double*)(ws + pl.off_agg[l]); a.T = Tcat; a.gscratch = gs;
+    team_launch<N>(reduce_team_kernel<N>, pl.cnt[l], reduce_slot_doubles<N>(), a, st);
+    c = pl.cnt[l];
+    G = 2;
+  }
+  for (int l = pl.nlev; l >= 0; --l) {
+    TeamScanArgs a{};
+    a.el = el;
+    a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr;
+    a.cnt = l ? pl.cnt[l - 1] : Tcat + 1;
+    a.G = l ? 2 : pl.G0;
+    a.above = l < pl.nlev ? (const double*)(ws + pl.off_val[l]) : nullptr;
+    a.cnt_above = l < pl.nlev ? pl.cnt[l] : 0;
+    a.T = Tcat;
+    a.gscratch = gs;
+    const int64_t groups = tdiv(a.cnt, a.G);
+    if (l == 0) {
+      a.S = S; a.v = v; a.zeta = zeta; a.maps = maps0; a.comp = nullptr;
+      team_launch<N>(down_team_kernel<N, true>, groups, down_slot_doubles<N>(), a, st);
+    } else {
+      a.vals = (double*)(ws + pl.off_val[l - 1]);
+      team_launch<N>(down_team_kernel<N, false>, groups, down_slot_doubles<N>(), a, st);
+    }
+  }
+  launch_boundary_patch(N, maps0, patch, st);
+  // chunk composites of the patched maps, then the state scan
+  if (pl.tlev > 0) {
+    TeamMapArgs a{};
+    a.maps = maps0;
+    a.cnt = pl.tcnt[0] * pl.G0 < Tcat ? pl.tcnt[0] * pl.G0 : Tcat;
+    a.G = pl.G0;
+    a.comp = (double*)(ws + pl.off_tmap[0]);
+    a.gscratch = gs;
+    team_launch<N>(reduce_maps_team_kernel<N>, pl.tcnt[0], maps_slot_doubles<N>(), a, st);
+  }
+  for (int l = 1; l < pl.tlev; ++l) {
+    TeamMapArgs a{};
+    a.maps = (const double*)(ws + pl.off_tmap[l - 1]); a.cnt = pl.tcnt[l - 1]; a.G = 2;
+    a.comp = (double*)(ws + pl.off_tmap[l]); a.gscratch = gs;
+    team_launch<N>(reduce_maps_team_kernel<N>, pl.tcnt[l], maps_slot_doubles<N>(), a, st);
+  }
+  for (int l = pl.tlev - 1; l >= 0; --l) {
+    TeamMapArgs a{};
+    a.maps = (const double*)(ws + pl.off_tmap[l]); a.cnt = pl.tcnt[l];
+    a.G = (l + 1 < pl.tlev) ? 2 : (int)pl.tcnt[l];
+    a.above = (l + 1 < pl.tlev) ? (const double*)(ws + pl.off_tstart[l + 1]) : nullptr;
+    a.x_in = x0_first; a.starts = (double*)(ws + pl.off_tstart[l]); a.gscratch = gs;
+    team_launch<N>(down_maps_team_kernel<N>, tdiv(pl.tcnt[l], a.G), maps_slot_doubles<N>(), a, st);
+  }
+  TeamFinalArgs f{};
+  f.maps = maps0; f.T = Tcat; f.G = pl.G0;
+  f.starts1 = pl.tlev > 0 ? (const double*)(ws + pl.off_tstart[0]) : nullptr;
+  f.x0 = x0_first; f.S = S; f.v = v; f.zeta = zeta; f.Ku = nullptr; f.m = 0;
+  f.x = x; f.u = nullptr; f.cost = nullptr; f.gscratch = gs;
+  team_launch<N>(final_team_kernel<N>, tdiv(Tcat + 1, pl.G0), maps_slot_doubles<N>(), f, st);
+  return cudaGetLastError();
+}
+
+size_t team_concat_workspace_bytes(int32_t n, int64_t Tcat) { return team_scan_workspace_bytes(n, Tcat, true); }
+
+cudaError_t team_concat_scan(int32_t n, int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,
+                             const double* x0_first, double* x, const BoundaryPatch& patch, char* ws,
+                             cudaStream_t st) {
+  switch (n) {
+    case 16: return team_concat<16>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    case 64: return team_concat<64>(Tcat, el, S, v, zeta, x0_first, x, patch, ws, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, int M>
+static void batch_build_team_nm(const BatchDev& bd, const ElemPtrs& el, double* gs, cudaStream_t st) {
+  const size_t smem = TeamCfg<N>::SMEM ? build_slot_doubles<N, M>() * sizeof(double) : 0;
+  batch_build_team_kernel<N, M><<<team_grid<N>(bd.total), TeamCfg<N>::TEAM, smem, st>>>(bd, el, gs);
+  count_launch();
+}
+
+cudaError_t batch_build_team(const BatchDev& bd, const ElemPtrs& el, double* gscratch, cudaStream_t st) {
+  if (bd.n == 16) {
+    switch (bd.M) {
+      case 1: batch_build_team_nm<16, 1>(bd, el, gscratch, st); break;
+      case 2: batch_build_team_nm<16, 2>(bd, el, gscratch, st); break;
+      case 4: batch_build_team_nm<16, 4>(bd, el, gscratch, st); break;
+      case 8: batch_build_team_nm<16, 8>(bd, el, gscratch, st); break;
+      case 16: batch_build_team_nm<16, 16>(bd, el, gscratch, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (bd.n == 64) {
+    batch_build_team_nm<64, 16>(bd, el, gscratch, st);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

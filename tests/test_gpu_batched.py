@@ -1,0 +1,78 @@
+"""Batched solves against the oracle, problem by problem."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-12))
+
+
+def members(n, Ts, first_seed):
+    return [W.batched_member(first_seed + i, T=T, n=n) for i, T in enumerate(Ts)]
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16])
+def test_batch_matches_oracle_per_problem(n):
+    from paper_2212_11744_gb300.batch import Batch
+    probs = members(n, [37, 123, 300, 64], 100 * n)
+    bt = Batch(probs)
+    out = bt.solve()
+    torch.cuda.synchronize()
+    for b, p in enumerate(probs):
+        ref = oracle.solve(p)
+        got = bt.problem_slice(out, b)
+        for k in ("S", "v", "zeta", "x", "u"):
+            assert rel(got[k].cpu().numpy(), ref[k]) <= TOL, (n, b, k)
+        assert abs(float(got["cost"]) - ref["cost"]) <= TOL * max(1.0, abs(ref["cost"])), (n, b)
+
+
+def test_batch_chunk_choices_agree_and_graph_replay():
+    """Every first-level chunk length gives the same solution (to rounding);
+    the batched solves of several dimensions captured in one CUDA graph and
+    replayed give the same outputs as direct calls."""
+    from paper_2212_11744_gb300.batch import Batch
+    batches = [Batch(members(n, [90, 211, 45], 7 * n)) for n in (2, 4, 8, 16)]
+    for bt in batches:
+        base = bt.solve()
+        for c in (2, 4, 16, 32):
+            o = bt.solve(chunk=c)
+            for k in ("S", "v", "zeta", "x"):
+                assert rel(o[k].cpu().numpy(), base[k].cpu().numpy()) <= 1e-12, (bt.n, c, k)
+    outs = [bt.new_outputs() for bt in batches]
+    for bt, o in zip(batches, outs):  # warm-up outside capture
+        bt.solve(out=o)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for bt, o in zip(batches, outs):
+                bt.solve(out=o, stream=s)
+    for o in outs:
+        for v in o.values():
+            v.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for bt, o in zip(batches, outs):
+        ref = bt.solve()
+        torch.cuda.synchronize()
+        for k in ("S", "v", "zeta", "x", "u", "cost"):
+            assert torch.equal(o[k], ref[k]), (bt.n, k)
+
+
+def test_autotuner_picks_a_candidate():
+    from paper_2212_11744_gb300.batch import Batch
+    bt = Batch(members(4, [500, 800, 300], 3))
+    best = bt.autotune(candidates=(0, 4, 16), reps=2)
+    assert best in (0, 4, 16)
+    assert Batch.tuning_table()[(4, 3, bt.total)][0] == best
