@@ -151,6 +151,16 @@ lqt_status lqt_scan_trajectory(const lqt_problem *p, const lqt_elements *el, con
 lqt_status lqt_solve(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
                      double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
 
+/* Mixed-precision variant of lqt_solve (same arguments, same workspace size):
+ * the element build (RK4 of the conditional HJB ODEs) and the LU solves of
+ * I + C J inside every combination stay FP64, while the matrix products of the
+ * combinations in both scans (forming I + C J, and every product after the
+ * solve) run in FP32 with FP32 accumulation.  Results are FP64 arrays; their
+ * error against the FP64 path is a property of the problem (reported by the
+ * benchmark and tested against a 1e-4 relative target). */
+lqt_status lqt_solve_mixed(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
+                           double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
 /* The sequential method of Sec. VI-A as ONE GPU thread (the comparison
  * baseline): K RK4 steps per sub-interval of the Riccati ODEs for S, v, zeta
  * (Sec. II-B, eq. LQT_differential_S_v) backward from t_T, then K RK4 steps

@@ -23,7 +23,7 @@ from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, 
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
-    "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_solve", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
+    "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_solve", "lqt_solve_mixed", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
 ]
 
@@ -191,6 +191,18 @@ def lqt_solve(dp: DeviceProblem, x0=None, out: Optional[dict] = None, ws=None, s
     _abi.check(_abi.lib().lqt_solve(dp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]), _ptr(out.get("zeta")),
                                     _ptr(out["x"]), _ptr(out.get("u")), _ptr(out.get("cost")), ws.data_ptr(),
                                     ws.numel(), _stream_handle(stream)), "lqt_solve")
+    return out
+
+
+def lqt_solve_mixed(dp: DeviceProblem, x0=None, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    """lqt_solve with the combination products in FP32 (LU solves and the
+    element build in FP64)."""
+    x0 = dp.x0 if x0 is None else x0
+    out = new_solution(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_SOLVE, ws)
+    _abi.check(_abi.lib().lqt_solve_mixed(dp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]), _ptr(out.get("zeta")),
+                                          _ptr(out["x"]), _ptr(out.get("u")), _ptr(out.get("cost")), ws.data_ptr(),
+                                          ws.numel(), _stream_handle(stream)), "lqt_solve_mixed")
     return out
 
 

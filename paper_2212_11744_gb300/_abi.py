@@ -21,7 +21,7 @@ EXPORTED = (
     "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value", "lqt_scan_trajectory", "lqt_solve",
     "lqt_solve_sequential", "lqt_host_staging_size", "lqt_solve_host", "lqt_get_status", "lqt_strerror",
     "lqt_last_launch_count", "lqt_scan_value_noalloc", "lqt_backward", "lqt_batch_workspace_size",
-    "lqt_batch_boundaries", "lqt_batch_plan", "lqt_solve_batched",
+    "lqt_batch_boundaries", "lqt_batch_plan", "lqt_solve_batched", "lqt_solve_mixed",
 )
 
 _dp = ct.POINTER(ct.c_double)
@@ -82,6 +82,8 @@ def lib():
     L.lqt_scan_trajectory.argtypes = [P, E, v, v, v, v, v, v, ct.c_size_t, v]
     L.lqt_solve.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]
     L.lqt_solve_sequential.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]
+    L.lqt_solve_mixed.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]
+    L.lqt_solve_mixed.restype = ct.c_int
     L.lqt_host_staging_size.argtypes = [P]
     L.lqt_host_staging_size.restype = ct.c_size_t
     L.lqt_solve_host.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]

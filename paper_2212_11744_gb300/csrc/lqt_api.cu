@@ -195,6 +195,14 @@ lqt_status lqt_solve(const lqt_problem* p, const double* x0, double* S, double* 
                                       ws_bytes - (scan - base), st));
 }
 
+lqt_status lqt_solve_mixed(const lqt_problem* p, const double* x0, double* S, double* v, double* zeta, double* x,
+                           double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
+  set_mixed_precision(true);
+  const lqt_status s = lqt_solve(p, x0, S, v, zeta, x, u, cost, ws, ws_bytes, stream);
+  set_mixed_precision(false);
+  return s;
+}
+
 lqt_status lqt_solve_sequential(const lqt_problem* p, const double* x0, double* S, double* v, double* zeta,
                                 double* x, double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
   t_launches = 0;

@@ -236,6 +236,14 @@ __device__ __forceinline__ void lu_solve(double (&W)[N * N], double (&R)[N * Q])
 // combination rule (Sec. IV-A, eq. lqt_comb)
 // ---------------------------------------------------------------------------
 
+// G is the type the matrix products are accumulated in: double for the FP64
+// path; float for the mixed-precision path, where every product runs in FP32
+// while W = I + C J is promoted to FP64 for the LU solve, which stays FP64.
+template <typename G>
+__device__ __forceinline__ G gf(double x) {
+  return (G)x;
+}
+
 // out = e1 (x) e2 for general elements.  With W = I + C1 J2 and
 // M = W^-1, (I + J2 C1)^-1 = M^T:
 //   K1 = M A1, MC1 = M C1, z0 = M (b1 + C1 eta2)          (one LU, 2N+1 rhs)
@@ -244,7 +252,7 @@ __device__ __forceinline__ void lu_solve(double (&W)[N * N], double (&R)[N * Q])
 //   zeta = zeta1 + zeta2 + 1/2 l0'C1 l0 + 1/2 z0'J2 z0 - z0'eta2,
 //          l0 = J2 z0 - eta2                                 (minimiser at x=0)
 // `out` may alias e2 (it is written after e2's last read of each field).
-template <int N>
+template <int N, typename G = double>
 __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, Elem<N>& out) {
   constexpr int Q = 2 * N + 1;
   double W[N * N];
@@ -254,67 +262,67 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
   for (int i = 0; i < N; ++i) {
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      double s = (i == j) ? 1.0 : 0.0;
+      G s = (i == j) ? G(1) : G(0);
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(e1.C[sidx<N>(i, l)], e2.J[sidx<N>(l, j)], s);
-      W[i * N + j] = s;
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(e1.C[sidx<N>(i, l)]), gf<G>(e2.J[sidx<N>(l, j)]), s);
+      W[i * N + j] = (double)s;
       R[i * Q + j] = e1.A[i * N + j];
       R[i * Q + N + j] = e1.C[sidx<N>(i, j)];
     }
-    double s = e1.b[i];
+    G s = gf<G>(e1.b[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(e1.C[sidx<N>(i, l)], e2.eta[l], s);
-    R[i * Q + 2 * N] = s;
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(e1.C[sidx<N>(i, l)]), gf<G>(e2.eta[l]), s);
+    R[i * Q + 2 * N] = (double)s;
   }
   lu_solve<N, Q>(W, R);
   // R = [K1 | MC1 | z0]
-  double z0[N], l0[N], J2z0[N];
+  G z0[N], l0[N], J2z0[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) z0[i] = R[i * Q + 2 * N];
+  for (int i = 0; i < N; ++i) z0[i] = gf<G>(R[i * Q + 2 * N]);
   // zeta
-  double zeta = e1.zeta + e2.zeta;
+  G zeta = gf<G>(e1.zeta) + gf<G>(e2.zeta);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = 0.0;
+    G s = 0;
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(e2.J[sidx<N>(i, l)], z0[l], s);
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(e2.J[sidx<N>(i, l)]), z0[l], s);
     J2z0[i] = s;
-    l0[i] = s - e2.eta[i];
+    l0[i] = s - gf<G>(e2.eta[i]);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = 0.0;
+    G s = 0;
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(e1.C[sidx<N>(i, l)], l0[l], s);
-    zeta = fma(0.5 * l0[i], s, zeta);
-    zeta = fma(z0[i], fma(0.5, J2z0[i], -e2.eta[i]), zeta);
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(e1.C[sidx<N>(i, l)]), l0[l], s);
+    zeta = fma(G(0.5) * l0[i], s, zeta);
+    zeta = fma(z0[i], fma(G(0.5), J2z0[i], -gf<G>(e2.eta[i])), zeta);
   }
   // eta = K1^T (eta2 - J2 b1) + eta1
-  double w[N];
+  G w[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = e2.eta[i];
+    G s = gf<G>(e2.eta[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(-e2.J[sidx<N>(i, l)], e1.b[l], s);
+    for (int l = 0; l < N; ++l) s = fma(-gf<G>(e2.J[sidx<N>(i, l)]), gf<G>(e1.b[l]), s);
     w[i] = s;
   }
   double eta_new[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = e1.eta[i];
+    G s = gf<G>(e1.eta[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(R[l * Q + i], w[l], s);
-    eta_new[i] = s;
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(R[l * Q + i]), w[l], s);
+    eta_new[i] = (double)s;
   }
   // J = K1^T (J2 A1) + J1   (upper triangle)
-  double T1[N * N];
+  G T1[N * N];
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      double s = 0.0;
+      G s = 0;
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(e2.J[sidx<N>(i, l)], e1.A[l * N + j], s);
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(e2.J[sidx<N>(i, l)]), gf<G>(e1.A[l * N + j]), s);
       T1[i * N + j] = s;
     }
   double J_new[Dim<N>::NS];
@@ -322,28 +330,28 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      double s = e1.J[sidx<N>(i, j)];
+      G s = gf<G>(e1.J[sidx<N>(i, j)]);
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(R[l * Q + i], T1[l * N + j], s);
-      J_new[sidx<N>(i, j)] = s;
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(R[l * Q + i]), T1[l * N + j], s);
+      J_new[sidx<N>(i, j)] = (double)s;
     }
   // b = A2 z0 + b2
   double b_new[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = e2.b[i];
+    G s = gf<G>(e2.b[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(e2.A[i * N + l], z0[l], s);
-    b_new[i] = s;
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(e2.A[i * N + l]), z0[l], s);
+    b_new[i] = (double)s;
   }
   // T1 = A2 MC1 ; C = T1 A2^T + C2 (upper triangle)
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      double s = 0.0;
+      G s = 0;
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(e2.A[i * N + l], R[l * Q + N + j], s);
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(e2.A[i * N + l]), gf<G>(R[l * Q + N + j]), s);
       T1[i * N + j] = s;
     }
   double C_new[Dim<N>::NS];
@@ -351,10 +359,10 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      double s = e2.C[sidx<N>(i, j)];
+      G s = gf<G>(e2.C[sidx<N>(i, j)]);
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(T1[i * N + l], e2.A[j * N + l], s);
-      C_new[sidx<N>(i, j)] = s;
+      for (int l = 0; l < N; ++l) s = fma(T1[i * N + l], gf<G>(e2.A[j * N + l]), s);
+      C_new[sidx<N>(i, j)] = (double)s;
     }
   // A = A2 K1
   double A_new[N * N];
@@ -362,10 +370,10 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      double s = 0.0;
+      G s = 0;
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(e2.A[i * N + l], R[l * Q + j], s);
-      A_new[i * N + j] = s;
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(e2.A[i * N + l]), gf<G>(R[l * Q + j]), s);
+      A_new[i * N + j] = (double)s;
     }
 #pragma unroll
   for (int i = 0; i < N * N; ++i) out.A[i] = A_new[i];
@@ -379,7 +387,7 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
     out.C[i] = C_new[i];
     out.J[i] = J_new[i];
   }
-  out.zeta = zeta;
+  out.zeta = (double)zeta;
 }
 
 // Value-form combination: e (x) V where V = (S2, v2, zeta2) is a value
@@ -390,7 +398,7 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
 //   S    = Psi^T (S2 A) + J,   v = Psi^T (v2 - S2 b) + eta
 //   zeta = zeta_e + zeta2 + 1/2 l0'C l0 + 1/2 z0'S2 z0 - z0'v2,
 //          z0 = alpha, l0 = S2 z0 - v2
-template <int N>
+template <int N, typename G = double>
 __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V, Val<N>& out, double (&Psi)[N * N],
                                               double (&alpha)[N]) {
   constexpr int Q = N + 1;
@@ -400,16 +408,16 @@ __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V,
   for (int i = 0; i < N; ++i) {
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      double s = (i == j) ? 1.0 : 0.0;
+      G s = (i == j) ? G(1) : G(0);
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(e.C[sidx<N>(i, l)], V.S[sidx<N>(l, j)], s);
-      W[i * N + j] = s;
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(e.C[sidx<N>(i, l)]), gf<G>(V.S[sidx<N>(l, j)]), s);
+      W[i * N + j] = (double)s;
       R[i * Q + j] = e.A[i * N + j];
     }
-    double s = e.b[i];
+    G s = gf<G>(e.b[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(e.C[sidx<N>(i, l)], V.v[l], s);
-    R[i * Q + N] = s;
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(e.C[sidx<N>(i, l)]), gf<G>(V.v[l]), s);
+    R[i * Q + N] = (double)s;
   }
   lu_solve<N, Q>(W, R);
 #pragma unroll
@@ -418,61 +426,61 @@ __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V,
     for (int j = 0; j < N; ++j) Psi[i * N + j] = R[i * Q + j];
     alpha[i] = R[i * Q + N];
   }
-  double Sz[N], l0[N];
-  double zeta = e.zeta + V.zeta;
+  G Sz[N], l0[N];
+  G zeta = gf<G>(e.zeta) + gf<G>(V.zeta);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = 0.0;
+    G s = 0;
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(V.S[sidx<N>(i, l)], alpha[l], s);
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(V.S[sidx<N>(i, l)]), gf<G>(alpha[l]), s);
     Sz[i] = s;
-    l0[i] = s - V.v[i];
+    l0[i] = s - gf<G>(V.v[i]);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = 0.0;
+    G s = 0;
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(e.C[sidx<N>(i, l)], l0[l], s);
-    zeta = fma(0.5 * l0[i], s, zeta);
-    zeta = fma(alpha[i], fma(0.5, Sz[i], -V.v[i]), zeta);
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(e.C[sidx<N>(i, l)]), l0[l], s);
+    zeta = fma(G(0.5) * l0[i], s, zeta);
+    zeta = fma(gf<G>(alpha[i]), fma(G(0.5), Sz[i], -gf<G>(V.v[i])), zeta);
   }
   // w = v2 - S2 b
-  double w[N];
+  G w[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = V.v[i];
+    G s = gf<G>(V.v[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(-V.S[sidx<N>(i, l)], e.b[l], s);
+    for (int l = 0; l < N; ++l) s = fma(-gf<G>(V.S[sidx<N>(i, l)]), gf<G>(e.b[l]), s);
     w[i] = s;
   }
   // T1 = S2 A
-  double T1[N * N];
+  G T1[N * N];
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      double s = 0.0;
+      G s = 0;
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(V.S[sidx<N>(i, l)], e.A[l * N + j], s);
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(V.S[sidx<N>(i, l)]), gf<G>(e.A[l * N + j]), s);
       T1[i * N + j] = s;
     }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double s = e.eta[i];
+    G s = gf<G>(e.eta[i]);
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(Psi[l * N + i], w[l], s);
-    out.v[i] = s;
+    for (int l = 0; l < N; ++l) s = fma(gf<G>(Psi[l * N + i]), w[l], s);
+    out.v[i] = (double)s;
   }
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      double s = e.J[sidx<N>(i, j)];
+      G s = gf<G>(e.J[sidx<N>(i, j)]);
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(Psi[l * N + i], T1[l * N + j], s);
-      out.S[sidx<N>(i, j)] = s;
+      for (int l = 0; l < N; ++l) s = fma(gf<G>(Psi[l * N + i]), T1[l * N + j], s);
+      out.S[sidx<N>(i, j)] = (double)s;
     }
-  out.zeta = zeta;
+  out.zeta = (double)zeta;
 }
 
 }  // namespace lqt

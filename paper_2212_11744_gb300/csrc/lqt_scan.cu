@@ -66,7 +66,7 @@ struct SrcPacked {
 // ---------------------------------------------------------------------------
 
 // agg[g] = e[gG] (x) e[gG+1] (x) ... (x) e[min(gG+G, cnt)-1]
-template <int N, class Src>
+template <int N, class Src, typename GT = double>
 __global__ void __launch_bounds__(128) reduce_elems_kernel(Src src, int64_t cnt, int G, double* __restrict__ agg) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t first = g * G;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) reduce_elems_kernel(Src src, int64_t cnt,
   src.load(last, acc);
   for (int64_t k = last - 1; k >= first; --k) {
     src.load(k, e);
-    combine<N>(e, acc, acc);
+    combine<N, GT>(e, acc, acc);
   }
   store_packed<N>(agg + g * packed_elem_doubles<N>(), acc);
 }
@@ -110,7 +110,7 @@ __device__ __forceinline__ void store_val_public(const DownOut& o, int64_t k, co
 
 // Suffix values of one group, right to left, from the carry `above` (the
 // value of everything after the group; zero value at the right end).
-template <int N, class Src, bool Level0>
+template <int N, class Src, bool Level0, typename GT = double>
 __global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, int G, const double* __restrict__ above,
                                                           int64_t cnt_above, DownOut o) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, 
   double Psi[N * N], alpha[N];
   for (int64_t k = last; k >= first; --k) {
     src.load(k, e);
-    combine_value<N>(e, carry, nv, Psi, alpha);
+    combine_value<N, GT>(e, carry, nv, Psi, alpha);
     if (Level0) {
       store_val_public<N>(o, k, nv);
       if (o.maps != nullptr && k < o.T) {
@@ -469,7 +469,7 @@ static ScanPlan make_plan(int64_t T, bool with_traj) {
   return pl;
 }
 
-template <int N>
+template <int N, typename GT = double>
 static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& out0, char* ws, cudaStream_t st) {
   const int64_t T = pl.T;
   SrcPublic<N> s0{el};
@@ -479,10 +479,10 @@ static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& ou
   for (int l = 0; l < pl.nlev; ++l) {
     double* agg = (double*)(ws + pl.off_agg[l]);
     if (l == 0) {
-      reduce_elems_kernel<N, SrcPublic<N>><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, G, agg);
+      reduce_elems_kernel<N, SrcPublic<N>, GT><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, G, agg);
     } else {
       SrcPacked<N> sp{(const double*)(ws + pl.off_agg[l - 1])};
-      reduce_elems_kernel<N, SrcPacked<N>><<<blocks_for(pl.cnt[l]), 128, 0, st>>>(sp, c, G, agg);
+      reduce_elems_kernel<N, SrcPacked<N>, GT><<<blocks_for(pl.cnt[l]), 128, 0, st>>>(sp, c, G, agg);
     }
     count_launch();
     c = pl.cnt[l];
@@ -496,13 +496,15 @@ static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& ou
     const int64_t cabove = (l < pl.nlev) ? pl.cnt[l] : 0;
     const int64_t groups = ceil_div(cl, Gl);
     if (l == 0) {
-      down_values_kernel<N, SrcPublic<N>, true><<<blocks_for(groups), 128, 0, st>>>(s0, cl, Gl, above, cabove, out0);
+      down_values_kernel<N, SrcPublic<N>, true, GT><<<blocks_for(groups), 128, 0, st>>>(s0, cl, Gl, above, cabove,
+                                                                                      out0);
     } else {
       SrcPacked<N> sp{(const double*)(ws + pl.off_agg[l - 1])};
       DownOut o{};
       o.vals = (double*)(ws + pl.off_val[l - 1]);
       o.T = T;
-      down_values_kernel<N, SrcPacked<N>, false><<<blocks_for(groups), 128, 0, st>>>(sp, cl, Gl, above, cabove, o);
+      down_values_kernel<N, SrcPacked<N>, false, GT><<<blocks_for(groups), 128, 0, st>>>(sp, cl, Gl, above, cabove,
+                                                                                       o);
     }
     count_launch();
   }
@@ -534,6 +536,10 @@ static void traj_scan(const ScanPlan& pl, const double* x0, const double* S, con
   count_launch();
 }
 
+static thread_local bool t_mixed = false;
+void set_mixed_precision(bool on) { t_mixed = on; }
+bool mixed_precision() { return t_mixed; }
+
 template <int N>
 static cudaError_t run_n(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
                          double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
@@ -546,7 +552,10 @@ static cudaError_t run_n(const lqt_problem& p, const Coefs& cf, const ElemPtrs& 
     o.S = S; o.v = v; o.zeta = zeta; o.T = p.T;
     o.maps = do_traj ? maps0 : nullptr;
     o.composite = do_traj ? comp1 : nullptr;
-    value_scan<N>(pl, el, o, ws, st);
+    if (t_mixed)
+      value_scan<N, float>(pl, el, o, ws, st);
+    else
+      value_scan<N, double>(pl, el, o, ws, st);
   } else if (do_traj) {
     SrcPublic<N> s0{el};
     maps_from_values_kernel<N><<<blocks_for(ceil_div(p.T + 1, pl.G0)), 128, 0, st>>>(s0, p.T, pl.G0, S, v, maps0,

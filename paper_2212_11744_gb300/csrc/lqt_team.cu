@@ -213,7 +213,7 @@ __device__ __forceinline__ Rec<N> level_elem(const TeamScanArgs& a, int64_t k, d
   return Rec<N>::pub(a.el, k, zero);
 }
 
-template <int N>
+template <int N, typename GT = double>
 __global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_team_kernel(TeamScanArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = reduce_slot_doubles<N>();
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_team_kernel(TeamScanA
     Rec<N> acc = Rec<N>::packed(bufA), nxt = Rec<N>::packed(bufB);
     team::copy_rec<N, TEAM>(lane, acc, level_elem<N>(a, last, &zero));
     for (int64_t k = last - 1; k >= first; --k) {
-      team::combine<N, TEAM>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is);
+      team::combine<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is);
       const Rec<N> t = acc;
       acc = nxt;
       nxt = t;
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_team_kernel(TeamScanA
   }
 }
 
-template <int N, bool Level0>
+template <int N, bool Level0, typename GT = double>
 __global__ void __launch_bounds__(TeamCfg<N>::TEAM) down_team_kernel(TeamScanArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = down_slot_doubles<N>();
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) down_team_kernel(TeamScanArg
       }
     team::sync<TEAM>();
     for (int64_t k = last; k >= first; --k) {
-      team::combine_value<N, TEAM>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is);
+      team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is);
       if (Level0) {
         bool ok = true;
         for (int e = lane; e < VS; e += TEAM) {
@@ -528,8 +528,8 @@ static cudaError_t team_build_nm(const lqt_problem& p, const Coefs& cf, const El
   return cudaGetLastError();
 }
 
-template <int N>
-static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
+template <int N, typename GT>
+static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
                             double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
                             bool do_traj, char* ws, cudaStream_t st) {
   const TeamPlan<N> pl = team_plan<N>(p.T, do_traj);
@@ -543,7 +543,7 @@ static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtr
       TeamScanArgs a{};
       a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
       a.agg = (double*)(ws + pl.off_agg[l]); a.T = p.T; a.gscratch = gs;
-      team_launch<N>(reduce_team_kernel<N>, pl.cnt[l], reduce_slot_doubles<N>(), a, st);
+      team_launch<N>(reduce_team_kernel<N, GT>, pl.cnt[l], reduce_slot_doubles<N>(), a, st);
       c = pl.cnt[l];
       G = 2;
     }
@@ -562,10 +562,10 @@ static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtr
         a.S = S; a.v = v; a.zeta = zeta;
         a.maps = do_traj ? maps0 : nullptr;
         a.comp = do_traj ? comp1 : nullptr;
-        team_launch<N>(down_team_kernel<N, true>, groups, down_slot_doubles<N>(), a, st);
+        team_launch<N>(down_team_kernel<N, true, GT>, groups, down_slot_doubles<N>(), a, st);
       } else {
         a.vals = (double*)(ws + pl.off_val[l - 1]);
-        team_launch<N>(down_team_kernel<N, false>, groups, down_slot_doubles<N>(), a, st);
+        team_launch<N>(down_team_kernel<N, false, GT>, groups, down_slot_doubles<N>(), a, st);
       }
     }
   } else if (do_traj) {
@@ -701,6 +701,15 @@ cudaError_t batch_build_team(const BatchDev& bd, const ElemPtrs& el, double* gsc
     return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtrs& el, double* S, double* v,
+                            double* zeta, const double* x0, double* x, double* u, double* cost, bool do_value,
+                            bool do_traj, char* ws, cudaStream_t st) {
+  if (mixed_precision())
+    return team_run_g<N, float>(p, cf, el, S, v, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
+  return team_run_g<N, double>(p, cf, el, S, v, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
 }
 
 // Build scratch for n = 64 (per-slot element buffers).

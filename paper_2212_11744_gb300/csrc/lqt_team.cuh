@@ -269,7 +269,7 @@ __host__ __device__ constexpr int combine_scratch_doubles() {
 }
 
 // out = e1 (x) e2 (full elements; out must not alias e1 or e2).
-template <int N, int TEAM>
+template <int N, int TEAM, typename G = double>
 __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr, double* fs, int* is) {
   constexpr int Q = 2 * N + 1;
   double* W = scr;
@@ -283,8 +283,8 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   for (int e = lane; e < N * N + N * Q; e += TEAM) {
     if (e < N * N) {
       const int i = e / N, j = e % N;
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int l = 0; l < N; ++l) s = fma(e1.C()[i * N + l], e2.J()[l * N + j], s);
+      G s = (G)((i == j) ? 1.0 : 0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(e2.J()[l * N + j]), s);
       W[e] = s;
     } else {
       const int t = e - N * N, i = t / Q, j = t % Q;
@@ -292,8 +292,9 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
       if (j < N) v = e1.A()[i * N + j];
       else if (j < 2 * N) v = e1.C()[i * N + (j - N)];
       else {
-        v = e1.b()[i];
-        for (int l = 0; l < N; ++l) v = fma(e1.C()[i * N + l], e2.eta()[l], v);
+        G g = (G)(e1.b()[i]);
+        for (int l = 0; l < N; ++l) g = fma((G)(e1.C()[i * N + l]), (G)(e2.eta()[l]), g);
+        v = (double)g;
       }
       R[t] = v;
     }
@@ -306,19 +307,19 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   // J2 z0, l0 = J2 z0 - eta2, w = eta2 - J2 b1 ; T1 = J2 A1
   for (int e = lane; e < 2 * N + N * N; e += TEAM) {
     if (e < N) {
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(e2.J()[e * N + l], z0[l], s);
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[e * N + l]), (G)(z0[l]), s);
       J2z[e] = s;
       l0[e] = s - e2.eta()[e];
     } else if (e < 2 * N) {
       const int i = e - N;
-      double s = e2.eta()[i];
-      for (int l = 0; l < N; ++l) s = fma(-e2.J()[i * N + l], e1.b()[l], s);
+      G s = (G)(e2.eta()[i]);
+      for (int l = 0; l < N; ++l) s = fma((G)(-e2.J()[i * N + l]), (G)(e1.b()[l]), s);
       wv[i] = s;
     } else {
       const int t = e - 2 * N, i = t / N, j = t % N;
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(e2.J()[i * N + l], e1.A()[l * N + j], s);
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[i * N + l]), (G)(e1.A()[l * N + j]), s);
       T1[t] = s;
     }
   }
@@ -329,8 +330,8 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   for (int e = lane; e < N + NS + N + N * N + 1; e += TEAM) {
     int t = e;
     if (t < N) {
-      double s = e1.eta()[t];
-      for (int l = 0; l < N; ++l) s = fma(R[l * Q + t], wv[l], s);
+      G s = (G)(e1.eta()[t]);
+      for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + t]), (G)(wv[l]), s);
       out.eta()[t] = s;
       continue;
     }
@@ -338,31 +339,31 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
     if (t < NS) {
       int i, j;
       upper_ij(N, t, i, j);
-      double s = e1.J()[i * N + j];
-      for (int l = 0; l < N; ++l) s = fma(R[l * Q + i], T1[l * N + j], s);
+      G s = (G)(e1.J()[i * N + j]);
+      for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + i]), (G)(T1[l * N + j]), s);
       out.J()[i * N + j] = s;
       out.J()[j * N + i] = s;
       continue;
     }
     t -= NS;
     if (t < N) {
-      double s = e2.b()[t];
-      for (int l = 0; l < N; ++l) s = fma(e2.A()[t * N + l], z0[l], s);
+      G s = (G)(e2.b()[t]);
+      for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[t * N + l]), (G)(z0[l]), s);
       out.b()[t] = s;
       continue;
     }
     t -= N;
     if (t < N * N) {
       const int i = t / N, j = t % N;
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(e2.A()[i * N + l], R[l * Q + j], s);
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[i * N + l]), (G)(R[l * Q + j]), s);
       out.A()[t] = s;
       continue;
     }
     double z = *e1.zeta() + *e2.zeta();
     for (int i = 0; i < N; ++i) {
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(e1.C()[i * N + l], l0[l], s);
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(l0[l]), s);
       z = fma(0.5 * l0[i], s, z);
       z = fma(z0[i], fma(0.5, J2z[i], -e2.eta()[i]), z);
     }
@@ -372,16 +373,16 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   // T1 = A2 MC1 ; then C = T1 A2^T + C2
   for (int e = lane; e < N * N; e += TEAM) {
     const int i = e / N, j = e % N;
-    double s = 0.0;
-    for (int l = 0; l < N; ++l) s = fma(e2.A()[i * N + l], R[l * Q + N + j], s);
+    G s = (G)(0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[i * N + l]), (G)(R[l * Q + N + j]), s);
     T1[e] = s;
   }
   sync<TEAM>();
   for (int t = lane; t < NS; t += TEAM) {
     int i, j;
     upper_ij(N, t, i, j);
-    double s = e2.C()[i * N + j];
-    for (int l = 0; l < N; ++l) s = fma(T1[i * N + l], e2.A()[j * N + l], s);
+    G s = (G)(e2.C()[i * N + j]);
+    for (int l = 0; l < N; ++l) s = fma((G)(T1[i * N + l]), (G)(e2.A()[j * N + l]), s);
     out.C()[i * N + j] = s;
     out.C()[j * N + i] = s;
   }
@@ -400,7 +401,7 @@ __host__ __device__ constexpr int val_doubles() {
   return N * N + N + 1;
 }
 
-template <int N, int TEAM>
+template <int N, int TEAM, typename G = double>
 __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, double* Psi, double* alpha,
                               double* scr, double* fs, int* is) {
   constexpr int Q = N + 1;
@@ -416,16 +417,17 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   for (int t = lane; t < N * N + N * Q; t += TEAM) {
     if (t < N * N) {
       const int i = t / N, j = t % N;
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int l = 0; l < N; ++l) s = fma(e.C()[i * N + l], S2[l * N + j], s);
+      G s = (G)((i == j) ? 1.0 : 0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(S2[l * N + j]), s);
       W[t] = s;
     } else {
       const int u = t - N * N, i = u / Q, j = u % Q;
       double v;
       if (j < N) v = e.A()[i * N + j];
       else {
-        v = e.b()[i];
-        for (int l = 0; l < N; ++l) v = fma(e.C()[i * N + l], v2[l], v);
+        G g = (G)(e.b()[i]);
+        for (int l = 0; l < N; ++l) g = fma((G)(e.C()[i * N + l]), (G)(v2[l]), g);
+        v = (double)g;
       }
       R[u] = v;
     }
@@ -440,19 +442,19 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   // Sz = S2 alpha, l0 = Sz - v2, w = v2 - S2 b ; T1 = S2 A
   for (int t = lane; t < 2 * N + N * N; t += TEAM) {
     if (t < N) {
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(S2[t * N + l], alpha[l], s);
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(S2[t * N + l]), (G)(alpha[l]), s);
       Sz[t] = s;
       l0[t] = s - v2[t];
     } else if (t < 2 * N) {
       const int i = t - N;
-      double s = v2[i];
-      for (int l = 0; l < N; ++l) s = fma(-S2[i * N + l], e.b()[l], s);
+      G s = (G)(v2[i]);
+      for (int l = 0; l < N; ++l) s = fma((G)(-S2[i * N + l]), (G)(e.b()[l]), s);
       wv[i] = s;
     } else {
       const int u = t - 2 * N, i = u / N, j = u % N;
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(S2[i * N + l], e.A()[l * N + j], s);
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(S2[i * N + l]), (G)(e.A()[l * N + j]), s);
       T1[u] = s;
     }
   }
@@ -462,21 +464,21 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   double* vo = out + N * N;
   for (int t = lane; t < N + NS + 1; t += TEAM) {
     if (t < N) {
-      double s = e.eta()[t];
-      for (int l = 0; l < N; ++l) s = fma(Psi[l * N + t], wv[l], s);
+      G s = (G)(e.eta()[t]);
+      for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + t]), (G)(wv[l]), s);
       vo[t] = s;
     } else if (t < N + NS) {
       int i, j;
       upper_ij(N, t - N, i, j);
-      double s = e.J()[i * N + j];
-      for (int l = 0; l < N; ++l) s = fma(Psi[l * N + i], T1[l * N + j], s);
+      G s = (G)(e.J()[i * N + j]);
+      for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + i]), (G)(T1[l * N + j]), s);
       So[i * N + j] = s;
       So[j * N + i] = s;
     } else {
       double z = *e.zeta() + zeta2;
       for (int i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int l = 0; l < N; ++l) s = fma(e.C()[i * N + l], l0[l], s);
+        G s = (G)(0.0);
+        for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(l0[l]), s);
         z = fma(0.5 * l0[i], s, z);
         z = fma(alpha[i], fma(0.5, Sz[i], -v2[i]), z);
       }
