@@ -216,7 +216,8 @@ typedef struct {
 
 /* Tunables of the batched solve, chosen by the caller's autotuner.
  * chunk: sub-intervals per thread (per team for n >= 16) in the first scan
- * level, a power of two in [2, 32]; 0 = built-in choice. */
+ * level, a power of two in [2, 32]; 0 = built-in choice; anything else gives
+ * LQT_EINVAL.  lqt_batch_workspace_size() covers every allowed value. */
 typedef struct {
   int32_t chunk;
   int32_t reserved;

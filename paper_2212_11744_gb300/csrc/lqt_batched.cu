@@ -124,7 +124,13 @@ static lqt_status batch_validate(const lqt_batch* bt, BatchLayout& L) {
   off = bal(off + bal(T1 * n * n * 8) * 3 + bal(T1 * n * 8) * 2 + bal(T1 * 8));
   L.off_team = off; off = bal(off + team_build_scratch_bytes(n));
   L.off_zf = off; off = bal(off + (size_t)L.B * 8);
-  L.off_scan = off; off = bal(off + concat_workspace_bytes(n, total - 1));
+  // The scans may run with any first-level chunk the caller's tuning picks;
+  // the shortest chunk (2) needs the most level storage, so size for it.
+  const int prev = scan_chunk_override();
+  set_scan_chunk(2);
+  const size_t scan_bytes = concat_workspace_bytes(n, total - 1);
+  set_scan_chunk(prev);
+  L.off_scan = off; off = bal(off + scan_bytes);
   L.bytes = off;
   return LQT_OK;
 }
@@ -230,10 +236,12 @@ lqt_status lqt_solve_batched(const lqt_batch* bt, const lqt_tuning* tune, double
   if (s != LQT_OK) return s;
   if (!S || !v || !zeta || !x) return LQT_EINVAL;
   if (!ws || ws_bytes < L.bytes) return LQT_EWORKSPACE;
+  const int chunk = tune ? tune->chunk : 0;
+  if (!(chunk == 0 || chunk == 2 || chunk == 4 || chunk == 8 || chunk == 16 || chunk == 32)) return LQT_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   char* w = (char*)ws;
   const BatchDev bd = batch_dev(L, w);
-  set_scan_chunk(tune ? tune->chunk : 0);
+  set_scan_chunk(chunk);
   cudaError_t e = batch_prepare(bd, st);
   const ElemPtrs el = batch_elements(L, w);
   if (e == cudaSuccess) e = batch_build(bd, el, w + L.off_team, st);

@@ -188,6 +188,7 @@ void launch_boundary_patch(int n, double* maps, const BoundaryPatch& patch, cuda
 // Level-0 chunk length override for the scans (0 = built-in heuristic); set by
 // the batched entry point from its tuning argument.
 void set_scan_chunk(int g);
+int scan_chunk_override();
 // Mixed precision for the scans: matrix products of the combinations in FP32,
 // the LU solves of I + C J in FP64 (set by lqt_solve_mixed for one call).
 void set_mixed_precision(bool on);

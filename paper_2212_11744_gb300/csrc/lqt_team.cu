@@ -439,8 +439,6 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) final_team_kernel(TeamFinalA
 // host side
 // ---------------------------------------------------------------------------
 
-int scan_chunk_override();
-
 template <int N>
 static int team_group0(int64_t T) {
   if (scan_chunk_override() >= 2) return scan_chunk_override();

@@ -70,6 +70,26 @@ def test_batch_chunk_choices_agree_and_graph_replay():
             assert torch.equal(o[k], ref[k]), (bt.n, k)
 
 
+def test_short_chunk_override_on_a_batch_whose_default_is_longer():
+    """A batch large enough that the built-in first-level chunk is > 2, solved
+    with every allowed chunk (the workspace must cover the shortest), checked
+    against the oracle for two of its problems."""
+    from paper_2212_11744_gb300 import _abi
+    from paper_2212_11744_gb300.batch import Batch
+    probs = members(2, [7000] * 10, 40)
+    bt = Batch(probs)
+    for c in (2, 4, 32, 0):
+        out = bt.solve(chunk=c)
+        torch.cuda.synchronize()
+        for b in (0, 9):
+            ref = oracle.solve(probs[b])
+            got = bt.problem_slice(out, b)
+            for k in ("S", "v", "x"):
+                assert rel(got[k].cpu().numpy(), ref[k]) <= TOL, (c, b, k)
+    with pytest.raises(_abi.LQTError):
+        bt.solve(chunk=3)
+
+
 def test_autotuner_picks_a_candidate():
     from paper_2212_11744_gb300.batch import Batch
     bt = Batch(members(4, [500, 800, 300], 3))
