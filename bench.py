@@ -147,26 +147,40 @@ def profiled_traffic():
 
 
 def dist_setup():
+    """torchrun environment -> (world size, rank, local rank).  NCCL when CUDA is
+    present, gloo otherwise (the CPU tests of the multi-rank logic)."""
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(local)
     return ws, rank, local
 
 
+def _dist_device():
+    import torch
+    import torch.distributed as dist
+    return torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
+
+
 def barrier(ws):
+    """All ranks meet here (an all-reduce on the backend's device), then the
+    local GPU, if any, is drained."""
     import torch
     if ws > 1:
         import torch.distributed as dist
-        t = torch.zeros(1, device="cuda")
+        t = torch.zeros(1, device=_dist_device())
         dist.all_reduce(t)
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
 
 def max_over_ranks(x: float, ws: int) -> float:
@@ -174,7 +188,7 @@ def max_over_ranks(x: float, ws: int) -> float:
     if ws == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_dist_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -230,6 +244,126 @@ def workload_config(p):
     return {"workload": f"point_mass_2d n={p.n} m={p.m} T={p.T} K={p.K} t=[0,100] X,r per RK4 half-step",
             "T": p.T, "n": p.n, "m": p.m, "K": p.K,
             "l2": f"inputs larger than L2 ({p.nbytes_inputs() / 1e9:.2f} GB of coefficient samples)"}
+
+
+# ---------------------------------------------------------------------------
+# the other rows of the hot path, measured beside the headline
+# ---------------------------------------------------------------------------
+
+def _events_ms(fn, reps, stream=None):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _relmax(a, b):
+    return float((a - b).abs().max() / b.abs().max().clamp_min(1e-12))
+
+
+def measure_rows(T_headline):
+    """Batched (4096 problems), mixed precision (point mass at T = 2^20 and the
+    n = 64 workload), adjoint (n = 8, T = 2^14) and the short double-integrator
+    solve.  Each entry is timed with CUDA events after a warm-up; failures are
+    recorded, not raised."""
+    import torch
+
+    import paper_2212_11744_gb300 as lqt
+    import workloads as W
+    rows = {}
+
+    def guard(name, fn):
+        try:
+            rows[name] = fn()
+        except Exception as exc:  # keep the headline line even if a row fails
+            rows[name] = {"error": repr(exc)[:300]}
+
+    def batched():
+        from paper_2212_11744_gb300.batch import Batch
+        probs = [W.batched_member(b) for b in range(4096)]
+        byn = {}
+        for p in probs:
+            byn.setdefault(p.n, []).append(p)
+        bts = {n: Batch(v) for n, v in sorted(byn.items())}
+        chunks = {n: bt.autotune(candidates=(0, 8, 32), reps=1) for n, bt in bts.items()}
+        outs = {n: bt.new_outputs() for n, bt in bts.items()}
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for n, bt in bts.items():
+                bt.solve(out=outs[n], stream=s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                for n, bt in bts.items():
+                    bt.solve(out=outs[n], stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        ms = _events_ms(g.replay, 2)
+        per = {str(n): _events_ms(lambda bt=bt, o=outs[n]: bt.solve(out=o), 1) for n, bt in bts.items()}
+        total = int(sum(p.T for p in probs))
+        st = lqt.lqt_get_status()
+        return {"workload": "4096 LQT problems, n in {2,4,8,16} (m = n/2), T in [256, 8192], K = 4, one CUDA graph "
+                            "of four batched solves (one per n)",
+                "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "sub_intervals": total,
+                "per_n_ms": per, "per_n_count": {str(n): bt.B for n, bt in bts.items()},
+                "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": st}
+
+    def mixed():
+        out = {}
+        p = W.point_mass_2d(T=T_headline, K=K_STEPS)
+        dp = lqt.DeviceProblem(p)
+        ws = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_SOLVE), dtype=torch.uint8, device="cuda")
+        a, b = lqt.new_solution(dp), lqt.new_solution(dp)
+        lqt.lqt_solve(dp, out=a, ws=ws)
+        lqt.lqt_solve_mixed(dp, out=b, ws=ws)
+        ms64 = _events_ms(lambda: lqt.lqt_solve(dp, out=a, ws=ws), 3)
+        ms32 = _events_ms(lambda: lqt.lqt_solve_mixed(dp, out=b, ws=ws), 3)
+        out["point_mass_T2^20"] = {"value": p.T / (ms32 * 1e-3), "unit": UNIT, "ms_mixed": ms32, "ms_f64": ms64,
+                                   "rel_err_vs_f64": {k: _relmax(b[k], a[k]) for k in ("S", "v", "zeta", "x", "u")}}
+        del ws, a, b, dp
+        p = W.large_state_n64(T=1 << 16)
+        dp = lqt.DeviceProblem(p)
+        a = lqt.lqt_solve(dp)
+        b = lqt.lqt_solve_mixed(dp)
+        ms64 = _events_ms(lambda: lqt.lqt_solve(dp, out=a), 1)
+        ms32 = _events_ms(lambda: lqt.lqt_solve_mixed(dp, out=b), 1)
+        out["large_state_n64_T2^16"] = {"value": p.T / (ms32 * 1e-3), "unit": UNIT, "ms_mixed": ms32, "ms_f64": ms64,
+                                        "f64_value": p.T / (ms64 * 1e-3),
+                                        "rel_err_vs_f64": {k: _relmax(b[k], a[k]) for k in ("S", "v", "zeta", "x")}}
+        out["note"] = "errors against the FP64 oracle are asserted <= 1e-4 in tests/test_gpu_mixed.py"
+        return out
+
+    def adjoint():
+        p = W.differentiable_n8()
+        dp = lqt.DeviceProblem(p)
+        fwd = lqt.lqt_solve(dp)
+        gx = torch.zeros(p.T + 1, p.n, dtype=torch.float64, device="cuda")
+        gx[-1] = 2.0 * (fwd["x"][-1] - torch.tensor(p.extra["x_target"], device="cuda"))
+        ws = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_BACKWARD), dtype=torch.uint8, device="cuda")
+        lqt.lqt_backward(dp, fwd, gx=gx, g_cost=1.0, ws=ws)
+        fms = _events_ms(lambda: lqt.lqt_solve(dp, out=fwd), 3)
+        bms = _events_ms(lambda: lqt.lqt_backward(dp, fwd, gx=gx, g_cost=1.0, ws=ws), 3)
+        return {"workload": "n=8, m=4, T=2^14, K=4; loss = cost + |x_T - x_target|^2; gradients w.r.t. F, L, X, U, "
+                            "r, Xf, x0", "value": p.T / ((fms + bms) * 1e-3), "unit": UNIT + " (forward + backward)",
+                "ms_forward": fms, "ms_backward": bms}
+
+    def small():
+        p = W.double_integrator()
+        dp = lqt.DeviceProblem(p)
+        o = lqt.lqt_solve(dp)
+        ms = _events_ms(lambda: lqt.lqt_solve(dp, out=o), 20)
+        return {"workload": "double integrator n=2, T=1024, K=10", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms}
+
+    guard("a4_batched", batched)
+    guard("a5_mixed", mixed)
+    guard("a6_adjoint", adjoint)
+    guard("double_integrator_T1024", small)
+    return rows
 
 
 # ---------------------------------------------------------------------------
@@ -326,6 +460,8 @@ def run_ours(args):
 
     err_par, err_seq = err(par), err(seq)
 
+    rows = measure_rows(args.T) if (args.rows and rank == 0) else None
+
     if rank == 0:
         cpu = cpu_baseline_sample(p)
         traffic = profiled_traffic()
@@ -349,6 +485,7 @@ def run_ours(args):
                                "tol_note": "both with K=4 on the same grid, errors vs a K=32 parallel solve"},
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "rows": rows,
         }
         print(json.dumps(line))
     if ws_ > 1:
@@ -363,6 +500,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--rows", type=int, default=1, help="also measure the batched, mixed-precision and adjoint rows")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
