@@ -49,22 +49,45 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(L):
+    P = ct.POINTER(_Problem)
+    L.orc_build_elements.argtypes = [P, ct.c_long, ct.c_long, _dp]
+    L.orc_combine.argtypes = [ct.c_int, _dp, _dp, _dp]
+    L.orc_suffix_values.argtypes = [ct.c_int, ct.c_long, _dp, _dp, _dp, _dp]
+    L.orc_trajectory.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_solve.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_sequential.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_element_size.argtypes = [ct.c_int]
+    L.orc_element_size.restype = ct.c_long
+    for f in ("orc_build_elements", "orc_combine", "orc_suffix_values", "orc_trajectory", "orc_solve",
+              "orc_sequential"):
+        getattr(L, f).restype = ct.c_int
+    return L
+
+
+class swapped_library:
+    """Context manager that makes every oracle call use the shared library at
+    `path` (a copy of lqt_oracle.c with a planted mistake, for the tests that
+    check that the pins catch mistakes)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _configure(ct.CDLL(self.path))
+        return self
+
+    def __exit__(self, *a):
+        global _lib
+        _lib = self.saved
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ct.CDLL(build())
-        P = ct.POINTER(_Problem)
-        _lib.orc_build_elements.argtypes = [P, ct.c_long, ct.c_long, _dp]
-        _lib.orc_combine.argtypes = [ct.c_int, _dp, _dp, _dp]
-        _lib.orc_suffix_values.argtypes = [ct.c_int, ct.c_long, _dp, _dp, _dp, _dp]
-        _lib.orc_trajectory.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp]
-        _lib.orc_solve.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-        _lib.orc_sequential.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-        _lib.orc_element_size.argtypes = [ct.c_int]
-        _lib.orc_element_size.restype = ct.c_long
-        for f in ("orc_build_elements", "orc_combine", "orc_suffix_values", "orc_trajectory", "orc_solve",
-                  "orc_sequential"):
-            getattr(_lib, f).restype = ct.c_int
+        _lib = _configure(ct.CDLL(build()))
     return _lib
 
 

@@ -146,7 +146,13 @@ def riccati_reference(p, rtol=1e-12, atol=1e-13):
     S = Sv[:, :n * n].reshape(-1, n, n)
     v = Sv[:, n * n:n * n + n]
     zeta = Sv[:, -1]
-    return {"S": S, "v": v, "zeta": zeta, "x": np.stack(xs), "cost": total_cost}
+    x = np.stack(xs)
+    # control law eq. LQT_optimal_control at every boundary
+    u = []
+    for j in range(p.T + 1):
+        F, L, X, U, c, H, r = coefs(tpts[j])
+        u.append(-np.linalg.solve(U, L.T @ (S[j] @ x[j] - v[j])))
+    return {"S": S, "v": v, "zeta": zeta, "x": x, "u": np.stack(u), "cost": total_cost}
 
 
 # ---------------------------------------------------------------------------
@@ -375,7 +381,7 @@ def test_semigroup_of_elements():
 @pytest.mark.parametrize("modes", [None, {"r": W.PER_INTERVAL, "X": W.CONST, "F": W.PER_INTERVAL}])
 def test_time_varying_against_adaptive_reference(modes):
     """Every term active (non-symmetric F, output matrix H with nr != n, drift c,
-    time-varying L, U, X, r).  S, v, zeta, x at every t_i from the scan route (O1)
+    time-varying L, U, X, r).  S, v, zeta, x, u at every t_i from the scan route (O1)
     and the sequential sweep (O2) against an adaptive DOP853 solution of the
     paper's sequential equations; the optimal cost V(x0,t0) against direct
     quadrature of the cost along the reference trajectory."""
@@ -383,20 +389,25 @@ def test_time_varying_against_adaptive_reference(modes):
     ref = riccati_reference(base)
     assert abs(ref["cost"] - (ref["zeta"][0] + 0.5 * base.x0 @ ref["S"][0] @ base.x0 - ref["v"][0] @ base.x0)) \
         < 1e-8 * abs(ref["cost"])
-    e1, e2 = [], []
+    e1, e2, eu2 = [], [], []
     for K in (8, 16, 32, 64):
         p = W.resample(base, K)
         o1, o2 = oracle.solve(p), oracle.sequential(p)
-        e1.append(max(rel(o1[k], ref[k]) for k in ("S", "v", "zeta", "x")))
+        e1.append(max(rel(o1[k], ref[k]) for k in ("S", "v", "zeta", "x", "u")))
         e2.append(max(rel(o2[k], ref[k]) for k in ("S", "v", "zeta", "x")))
+        eu2.append(rel(o2["u"], ref["u"]))
         c1 = abs(o1["cost"] - ref["cost"]) / abs(ref["cost"])
+        c2 = abs(o2["cost"] - ref["cost"]) / abs(ref["cost"])
         if K == 64:
-            assert c1 < 1e-10
+            assert c1 < 1e-10 and c2 < 1e-8, (c1, c2)
     assert e1[-1] < 1e-10, e1
     assert e2[-1] < 1e-8, e2
     for e in (e1, e2):
         # order 4 while the error is above the reference solver's own ~1e-11 floor
         assert all(10 < e[i] / e[i + 1] < 22 for i in range(len(e) - 1) if e[i + 1] > 1e-10), e
+    # O2's controls at the coarsest grid are still pre-asymptotic (ratio ~30)
+    assert eu2[-1] < 2e-8, eu2
+    assert all(10 < eu2[i] / eu2[i + 1] < 40 for i in range(len(eu2) - 1)), eu2
 
 
 def test_scan_and_sequential_agree_at_every_boundary():
