@@ -57,10 +57,11 @@ def _configure(L):
     L.orc_trajectory.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_solve.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_sequential.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_densify.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_element_size.argtypes = [ct.c_int]
     L.orc_element_size.restype = ct.c_long
     for f in ("orc_build_elements", "orc_combine", "orc_suffix_values", "orc_trajectory", "orc_solve",
-              "orc_sequential"):
+              "orc_sequential", "orc_densify"):
         getattr(L, f).restype = ct.c_int
     return L
 
@@ -226,3 +227,28 @@ def sequential(p, x0=None) -> dict:
     if rc:
         raise FloatingPointError("oracle: singular matrix in sequential sweep")
     return {"S": S, "v": v, "zeta": z, "x": x, "u": u, "cost": float(cost[0])}
+
+
+def densify(p, sol: dict) -> dict:
+    """Values, states and controls at every RK4 sub-step t_j + i h_j (i = 0..K-1)
+    and t_T, from a boundary solution sol = {S, v, zeta, x} (e.g. solve(p)):
+    per block, K RK4 steps of the Riccati ODEs backward from the block's right
+    boundary and K RK4 steps of the closed loop forward from its left boundary."""
+    n, m, T, K = p.n, p.m, p.T, p.K
+    G = T * K + 1
+    Sd = np.zeros((G, n, n)); vd = np.zeros((G, n)); zd = np.zeros(G); xd = np.zeros((G, n)); ud = np.zeros((G, m))
+    mr = _Marshalled(p)
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    rc = lib().orc_densify(mr.ref(), _ptr(c(sol["S"])), _ptr(c(sol["v"])), _ptr(c(sol["zeta"])), _ptr(c(sol["x"])),
+                           _ptr(Sd), _ptr(vd), _ptr(zd), _ptr(xd), _ptr(ud))
+    if rc:
+        raise FloatingPointError("oracle: singular U sample in densify")
+    return {"S": Sd, "v": vd, "zeta": zd, "x": xd, "u": ud}
+
+
+def fine_times(p) -> np.ndarray:
+    """The RK4 sub-step times t_j + i h_j, i = 0..K-1, and t_T."""
+    K = p.K
+    t = np.asarray(p.t, dtype=np.float64)
+    out = (t[:-1, None] + (t[1:] - t[:-1])[:, None] * (np.arange(K)[None, :] / K)).ravel()
+    return np.concatenate([out, t[-1:]])

@@ -692,5 +692,112 @@ int orc_sequential(const orc_problem *P, const double *x0, double *S, double *v,
   return bad;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Densification: values, states and controls at every RK4 sub-step          */
+/* ------------------------------------------------------------------------ */
+
+/* Within-block densification (Sec. IV-E: the optimal trajectory inside a
+ * sub-interval; Sec. VI-A: the fine grid of K steps per sub-interval).
+ * Input: the solution at the block boundaries (S, v, zeta at t_0..t_T, x at
+ * t_0..t_T).  For every block j independently:
+ *   backward: K RK4 steps of the Riccati ODEs (eq. LQT_differential_S_v plus
+ *     the zeta equation) from (S, v, zeta)_{j+1} at t_{j+1} down to t_j, with
+ *     the same half-step samples as the element build, giving y_i at
+ *     t_j + i h, i = K..0;
+ *   forward: K RK4 steps of the closed-loop ODE (eq.
+ *     optimal_trajectory_ODE_LQT) from x_j at t_j, with S, v at step midpoints
+ *     from the cubic Hermite interpolant of the y_i (slopes = the Riccati
+ *     right-hand side at each y_i with the block's sample there), as in O2.
+ * Output at fine index g = j K + i (i = 0..K-1) and g = T K: at block
+ * boundaries (i = 0, and g = T K) the given boundary solution; inside a block
+ * y_i and the forward RK4 state.  Controls by eq. LQT_optimal_control with the
+ * sample at each point (block j's sample 2i; block T-1's last sample at t_T).
+ * Sd [TK+1][n][n], vd [TK+1][n], zd [TK+1], xd [TK+1][n], ud [TK+1][m]. */
+int orc_densify(const orc_problem *P, const double *S, const double *v, const double *zeta, const double *x,
+                double *Sd, double *vd, double *zd, double *xd, double *ud) {
+  int n = P->n, m = P->m, K = P->K;
+  long T = P->T;
+  size_t ys = (size_t)n * n + n + 1, nn = (size_t)n * n;
+  double *buf = (double *)malloc(sizeof(double) * (2 * (size_t)(K + 1) * ys + 6 * ys + 3 * nn + 8 * (size_t)n +
+                                                   (size_t)m + coefs_size(n, m, P->nr)));
+  double *Y = buf;                        /* y_i, i = 0..K */
+  double *D = Y + (size_t)(K + 1) * ys;   /* slopes d_i, i = 0..K */
+  double *yt = D + (size_t)(K + 1) * ys, *k = yt + ys, *acc = k + ys, *ym = acc + ys;
+  double *tmp = ym + ys + 2 * ys;
+  double *xv = tmp + 3 * nn, *xt = xv + n, *kx = xt + n, *ax = kx + n, *t2 = ax + n;
+  double *cur = t2 + 4 * (size_t)n + m;
+  coefs cf;
+  coefs_alloc(&cf, n, m, P->nr, &cur);
+  int bad = 0;
+  for (long j = 0; j < T; ++j) {
+    double h = (P->t[j + 1] - P->t[j]) / K;
+    double *yK = Y + (size_t)K * ys;
+    memcpy(yK, S + (size_t)(j + 1) * nn, sizeof(double) * nn);
+    memcpy(yK + nn, v + (size_t)(j + 1) * n, sizeof(double) * n);
+    yK[nn + n] = zeta[j + 1];
+    for (int i = K - 1; i >= 0; --i) {
+      const double *y = Y + (size_t)(i + 1) * ys;
+      double *yn = Y + (size_t)i * ys;
+      bad |= coefs_eval(P, j, 2 * i + 2, &cf);
+      riccati_rhs(n, &cf, y, k, tmp);
+      memcpy(D + (size_t)(i + 1) * ys, k, sizeof(double) * ys);
+      for (size_t q = 0; q < ys; ++q) { acc[q] = k[q]; yt[q] = y[q] - 0.5 * h * k[q]; }
+      bad |= coefs_eval(P, j, 2 * i + 1, &cf);
+      riccati_rhs(n, &cf, yt, k, tmp);
+      for (size_t q = 0; q < ys; ++q) { acc[q] += 2.0 * k[q]; yt[q] = y[q] - 0.5 * h * k[q]; }
+      riccati_rhs(n, &cf, yt, k, tmp);
+      for (size_t q = 0; q < ys; ++q) { acc[q] += 2.0 * k[q]; yt[q] = y[q] - h * k[q]; }
+      bad |= coefs_eval(P, j, 2 * i, &cf);
+      riccati_rhs(n, &cf, yt, k, tmp);
+      for (size_t q = 0; q < ys; ++q) { acc[q] += k[q]; yn[q] = y[q] - (h / 6.0) * acc[q]; }
+    }
+    bad |= coefs_eval(P, j, 0, &cf);
+    riccati_rhs(n, &cf, Y, D, tmp);
+    /* forward */
+    memcpy(xv, x + (size_t)j * n, sizeof(double) * n);
+    for (int i = 0; i < K; ++i) {
+      size_t g = (size_t)j * K + i;
+      if (i == 0) {
+        memcpy(Sd + g * nn, S + (size_t)j * nn, sizeof(double) * nn);
+        memcpy(vd + g * n, v + (size_t)j * n, sizeof(double) * n);
+        zd[g] = zeta[j];
+        memcpy(xd + g * n, x + (size_t)j * n, sizeof(double) * n);
+      } else {
+        const double *y = Y + (size_t)i * ys;
+        memcpy(Sd + g * nn, y, sizeof(double) * nn);
+        memcpy(vd + g * n, y + nn, sizeof(double) * n);
+        zd[g] = y[nn + n];
+        memcpy(xd + g * n, xv, sizeof(double) * n);
+      }
+      bad |= coefs_eval(P, j, 2 * i, &cf);
+      mm(n, n, 1, Sd + g * nn, xd + g * n, t2);
+      for (int q = 0; q < n; ++q) t2[q] = vd[g * n + q] - t2[q];
+      mm(m, n, 1, cf.G, t2, ud + g * m);
+      if (i == K - 1) break; /* the state at t_{j+1} is the boundary solution */
+      const double *y0 = Y + (size_t)i * ys, *y1 = Y + (size_t)(i + 1) * ys;
+      const double *d0 = D + (size_t)i * ys, *d1 = D + (size_t)(i + 1) * ys;
+      for (size_t q = 0; q < ys; ++q) ym[q] = 0.5 * (y0[q] + y1[q]) + h * (d0[q] - d1[q]) / 8.0;
+      closed_loop_rhs(n, m, &cf, y0, y0 + nn, xv, kx, t2);
+      for (int q = 0; q < n; ++q) { ax[q] = kx[q]; xt[q] = xv[q] + 0.5 * h * kx[q]; }
+      bad |= coefs_eval(P, j, 2 * i + 1, &cf);
+      closed_loop_rhs(n, m, &cf, ym, ym + nn, xt, kx, t2);
+      for (int q = 0; q < n; ++q) { ax[q] += 2.0 * kx[q]; xt[q] = xv[q] + 0.5 * h * kx[q]; }
+      closed_loop_rhs(n, m, &cf, ym, ym + nn, xt, kx, t2);
+      for (int q = 0; q < n; ++q) { ax[q] += 2.0 * kx[q]; xt[q] = xv[q] + h * kx[q]; }
+      bad |= coefs_eval(P, j, 2 * i + 2, &cf);
+      closed_loop_rhs(n, m, &cf, y1, y1 + nn, xt, kx, t2);
+      for (int q = 0; q < n; ++q) { ax[q] += kx[q]; xv[q] = xv[q] + (h / 6.0) * ax[q]; }
+    }
+  }
+  size_t g = (size_t)T * K;
+  memcpy(Sd + g * nn, S + (size_t)T * nn, sizeof(double) * nn);
+  memcpy(vd + g * n, v + (size_t)T * n, sizeof(double) * n);
+  zd[g] = zeta[T];
+  memcpy(xd + g * n, x + (size_t)T * n, sizeof(double) * n);
+  bad |= control_at(P, T, S + (size_t)T * nn, v + (size_t)T * n, x + (size_t)T * n, ud + g * m, t2, &cf);
+  free(buf);
+  return bad;
+}
+
 /* Size in doubles of one packed element, for callers. */
 long orc_element_size(int n) { return (long)elem_size(n); }

@@ -2,7 +2,8 @@
 
 Each case below plants one mistake in a copy of oracle/lqt_oracle.c (a dropped
 term, a flipped sign, a transposed operand, a wrong index or weight), compiles
-the copy, and runs every pin of test_oracle_pins.py against it.  At least one
+the copy, and runs every pin of test_oracle_pins.py and test_oracle_densify.py
+against it.  At least one
 pin has to fail for every mutant; otherwise the pins would also have let that
 mistake through in the real oracle.  Nothing here touches the GPU.
 """
@@ -14,6 +15,7 @@ import subprocess
 import pytest
 
 import oracle
+from tests import test_oracle_densify as densify_pins
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lqt_oracle.c")
@@ -73,6 +75,13 @@ MUTATIONS = [
     ("O2 Hermite midpoint: slope term sign", "h * (d0[q] - d1[q]) / 8.0", "h * (d1[q] - d0[q]) / 8.0", 0),
     ("O2 forward: midpoint stage from the end point", "closed_loop_rhs(n, m, &cf, ym, ym + nn, xt, kx, t2);\n      for (int q = 0; q < n; ++q) { ax[q] += 2.0 * kx[q]; xt[q] = xv[q] + h * kx[q]; }",
      "closed_loop_rhs(n, m, &cf, y1, y1 + nn, xt, kx, t2);\n      for (int q = 0; q < n; ++q) { ax[q] += 2.0 * kx[q]; xt[q] = xv[q] + h * kx[q]; }", 0),
+    # within-block densification
+    ("densify: Hermite slope sign", "h * (d0[q] - d1[q]) / 8.0", "h * (d1[q] - d0[q]) / 8.0", 1),
+    ("densify: k3 weight", "acc[q] += 2.0 * k[q]; yt[q] = y[q] - h * k[q];", "acc[q] += k[q]; yt[q] = y[q] - h * k[q];", 2),
+    ("densify: block-start slope sample", "bad |= coefs_eval(P, j, 0, &cf);\n    riccati_rhs(n, &cf, Y, D, tmp);",
+     "bad |= coefs_eval(P, j, 1, &cf);\n    riccati_rhs(n, &cf, Y, D, tmp);", 0),
+    ("densify: control sample", "bad |= coefs_eval(P, j, 2 * i, &cf);\n      mm(n, n, 1, Sd",
+     "bad |= coefs_eval(P, j, 0, &cf);\n      mm(n, n, 1, Sd", 0),
     # shared small linear algebra
     ("mtm: operand not transposed", "for (int l = 0; l < k; ++l) s += a[l * p + i] * b[l * q + j];",
      "for (int l = 0; l < k; ++l) s += a[i * k + l] * b[l * q + j];", 0),
@@ -90,8 +99,9 @@ def _replace_nth(text, old, new, nth):
 def _pin_calls():
     """Every (name, zero-argument callable) for the pins, parametrisations expanded."""
     calls = []
-    for name, fn in inspect.getmembers(pins, inspect.isfunction):
-        if not name.startswith("test_") or fn.__module__ != pins.__name__:
+    members = inspect.getmembers(pins, inspect.isfunction) + inspect.getmembers(densify_pins, inspect.isfunction)
+    for name, fn in members:
+        if not name.startswith("test_") or fn.__module__ not in (pins.__name__, densify_pins.__name__):
             continue
         marks = getattr(fn, "pytestmark", [])
         params = [m for m in marks if m.name == "parametrize"]
