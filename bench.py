@@ -359,10 +359,25 @@ def measure_rows(T_headline):
         ms = _events_ms(lambda: lqt.lqt_solve(dp, out=o), 20)
         return {"workload": "double integrator n=2, T=1024, K=10", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms}
 
+    def densify():
+        p = W.point_mass_2d(T=T_headline, K=K_STEPS)
+        dp = lqt.DeviceProblem(p)
+        ws = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_SOLVE), dtype=torch.uint8, device="cuda")
+        sol = lqt.lqt_solve(dp, ws=ws)
+        d = lqt.lqt_densify(dp, sol)
+        wsd = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_DENSIFY), dtype=torch.uint8, device="cuda")
+        dms = _events_ms(lambda: lqt.lqt_densify(dp, sol, out=d, ws=wsd), 3)
+        sms = _events_ms(lambda: lqt.lqt_solve(dp, out=sol, ws=ws), 3)
+        fine = p.T * p.K
+        return {"workload": "point mass T=2^20, K=4: solution at all 4 194 305 RK4 sub-steps from the boundary "
+                            "solution", "value": fine / ((sms + dms) * 1e-3), "unit": "sub-steps/s (solve + densify)",
+                "ms_densify": dms, "ms_solve": sms, "status": lqt.lqt_get_status()}
+
     guard("a4_batched", batched)
     guard("a5_mixed", mixed)
     guard("a6_adjoint", adjoint)
     guard("double_integrator_T1024", small)
+    guard("next1_densify", densify)
     return rows
 
 

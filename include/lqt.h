@@ -108,7 +108,8 @@ enum {
   LQT_WS_TRAJ = 2,
   LQT_WS_SOLVE = 3,
   LQT_WS_SEQUENTIAL = 4,
-  LQT_WS_BACKWARD = 5
+  LQT_WS_BACKWARD = 5,
+  LQT_WS_DENSIFY = 6
 };
 
 /* Bytes of device workspace the call `which` needs for problem p (host call,
@@ -169,6 +170,28 @@ lqt_status lqt_solve_mixed(const lqt_problem *p, const double *x0, double *S, do
  * interpolant of the backward solution.  Same outputs as lqt_solve. */
 lqt_status lqt_solve_sequential(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta,
                                 double *x, double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* Within-block densification: the optimal solution at every RK4 sub-step
+ * t_j + i h_j (h_j = (t_{j+1} - t_j)/K, i = 0..K-1) of every sub-interval and at
+ * t_T, from the solution at the sub-interval boundaries (Sec. IV-E: the optimal
+ * trajectory inside a sub-interval; Sec. VI-A: the K-step fine grid).
+ * Inputs (device): S [T+1][n][n], v [T+1][n], zeta [T+1], x [T+1][n], e.g. the
+ * outputs of lqt_solve.  Per sub-interval j, independently: K classical RK4
+ * steps of the Riccati ODEs (Sec. II-B, eq. LQT_differential_S_v, plus the zeta
+ * equation) backward from (S, v, zeta) at t_{j+1} with the element build's
+ * half-step samples, then RK4 of the closed-loop ODE (eq.
+ * optimal_trajectory_ODE_LQT) forward from x_j with S, v at step midpoints from
+ * the cubic Hermite interpolant of the backward values; controls by eq.
+ * LQT_optimal_control with the L, U sample at each sub-step.  At the
+ * boundaries (i = 0 and t_T) the outputs are the inputs themselves.
+ * Outputs (device, fine index g = j K + i, last g = T K): Sd [TK+1][n][n],
+ * vd [TK+1][n], zd [TK+1], xd [TK+1][n], ud [TK+1][m] (ud may be NULL).
+ * Workspace: lqt_workspace_size(p, LQT_WS_DENSIFY) (derived coefficients).
+ * Supported: n <= 8, K <= 16 (otherwise LQT_EUNSUPPORTED).  Asynchronous,
+ * allocation-free. */
+lqt_status lqt_densify(const lqt_problem *p, const double *S, const double *v, const double *zeta, const double *x,
+                       double *Sd, double *vd, double *zd, double *xd, double *ud, void *ws, size_t ws_bytes,
+                       void *stream);
 
 /* Reverse mode of lqt_solve: gradients of a scalar loss with respect to the
  * coefficients, given the forward outputs S, v, x of lqt_solve (device) and the

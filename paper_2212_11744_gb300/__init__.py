@@ -18,12 +18,14 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, LQT_WS_BUILD, LQT_WS_SEQUENTIAL,
-                   LQT_WS_SOLVE, LQT_WS_TRAJ, LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
+from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, LQT_WS_BUILD, LQT_WS_DENSIFY,
+                   LQT_WS_SEQUENTIAL, LQT_WS_SOLVE, LQT_WS_TRAJ, LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements,
+                   lqt_problem)
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
-    "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_solve", "lqt_solve_mixed", "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
+    "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_densify", "lqt_solve", "lqt_solve_mixed",
+    "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
 ]
 
@@ -214,6 +216,24 @@ def lqt_solve_sequential(dp: DeviceProblem, x0=None, out: Optional[dict] = None,
                                                _ptr(out.get("zeta")), _ptr(out["x"]), _ptr(out.get("u")),
                                                _ptr(out.get("cost")), ws.data_ptr(), ws.numel(),
                                                _stream_handle(stream)), "lqt_solve_sequential")
+    return out
+
+
+def new_dense(dp: DeviceProblem) -> dict:
+    n, m, G = dp.n, dp.m, dp.T * dp.K + 1
+    return {"S": _empty(dp, G, n, n), "v": _empty(dp, G, n), "zeta": _empty(dp, G), "x": _empty(dp, G, n),
+            "u": _empty(dp, G, m)}
+
+
+def lqt_densify(dp: DeviceProblem, sol: dict, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    """Solution at every RK4 sub-step from the boundary solution `sol` (the
+    S, v, zeta, x of lqt_solve): arrays of T K + 1 points."""
+    out = new_dense(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_DENSIFY, ws)
+    _abi.check(_abi.lib().lqt_densify(dp.ref(), _ptr(sol["S"]), _ptr(sol["v"]), _ptr(sol["zeta"]), _ptr(sol["x"]),
+                                      _ptr(out["S"]), _ptr(out["v"]), _ptr(out["zeta"]), _ptr(out["x"]),
+                                      _ptr(out.get("u")), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+               "lqt_densify")
     return out
 
 

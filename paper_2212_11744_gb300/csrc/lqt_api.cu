@@ -118,6 +118,7 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
              scan_workspace_bytes(p->n, p->T, true);
     case LQT_WS_SEQUENTIAL: return L.coef_bytes + align_up(sequential_workspace_bytes(p->n, p->T, p->K));
     case LQT_WS_BACKWARD: return backward_workspace_bytes(*p, L, element_bytes(*p)) + 4096;
+    case LQT_WS_DENSIFY: return L.coef_bytes;
     default: return 0;
   }
 }
@@ -217,6 +218,23 @@ lqt_status lqt_solve_sequential(const lqt_problem* p, const double* x0, double* 
   Coefs cf;
   if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
   return from_cuda(launch_sequential(*p, L, cf, x0, S, v, zeta, x, u, cost, (char*)ws + L.coef_bytes, st));
+}
+
+lqt_status lqt_densify(const lqt_problem* p, const double* S, const double* v, const double* zeta, const double* x,
+                       double* Sd, double* vd, double* zd, double* xd, double* ud, void* ws, size_t ws_bytes,
+                       void* stream) {
+  t_launches = 0;
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (!densify_supported(*p)) return LQT_EUNSUPPORTED;
+  if (!S || !v || !zeta || !x || !Sd || !vd || !zd || !xd) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_DENSIFY);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  Coefs cf;
+  if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
+  return from_cuda(launch_densify(*p, L, cf, S, v, zeta, x, Sd, vd, zd, xd, ud, st));
 }
 
 static lqt_status validate_backward(const lqt_problem* p) {

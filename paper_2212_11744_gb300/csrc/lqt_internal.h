@@ -123,6 +123,10 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
                          const double* v, const double* x, const double* gS, const double* gv, const double* gz,
                          const double* gx, double g_cost, double* gF, double* gL, double* gX, double* gU, double* gr,
                          double* gXf, double* grf, double* gx0, char* ws, cudaStream_t st);
+bool densify_supported(const lqt_problem& p);
+cudaError_t launch_densify(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* S, const double* v,
+                           const double* zeta, const double* x, double* Sd, double* vd, double* zd, double* xd,
+                           double* ud, cudaStream_t st);
 size_t sequential_workspace_bytes(int32_t n, int64_t T, int32_t K);
 cudaError_t launch_sequential(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* x0,
                               double* S, double* v, double* zeta, double* x, double* u, double* cost, char* ws,

@@ -99,3 +99,18 @@ def test_strerror_names_every_status(lib):
     import paper_2212_11744_gb300 as m
     names = {m.lqt_strerror(c) for c in range(8)}
     assert len(names) == 8 and "unknown status" not in names
+
+
+def test_densify_validation_on_host(lib):
+    import paper_2212_11744_gb300 as m
+    from paper_2212_11744_gb300 import _abi
+    L = _abi.lib()
+    hp = _problem()
+    d = ct.c_void_p(256)
+    ws = m.lqt_workspace_size(hp, m.LQT_WS_DENSIFY)
+    assert ws > 0
+    # missing zeta input, too small a workspace, K above 16, n above 8
+    assert L.lqt_densify(hp.ref(), d, d, None, d, d, d, d, d, None, d, ws, None) == _abi.LQT_EINVAL
+    assert L.lqt_densify(hp.ref(), d, d, d, d, d, d, d, d, None, d, ws - 1, None) == _abi.LQT_EWORKSPACE
+    hp.struct.K = 17
+    assert L.lqt_densify(hp.ref(), d, d, d, d, d, d, d, d, None, d, 1 << 40, None) == _abi.LQT_EUNSUPPORTED

@@ -386,3 +386,23 @@ def truncate(p: Problem, Ts: int) -> Problem:
             co[k] = c
     return Problem(name=p.name + f"_first{Ts}", n=p.n, m=p.m, nr=p.nr, T=Ts, K=K, t=p.t[: Ts + 1].copy(), Hf=p.Hf,
                    Xf=p.Xf, rf=p.rf, x0=p.x0, extra=p.extra, funcs=p.funcs, **co)
+
+
+def window(p: Problem, j0: int, count: int) -> Problem:
+    """Sub-intervals j0 .. j0+count-1 of p as a problem of its own (same grid
+    points and coefficient samples; the terminal cost of p placed at the
+    window's end).  Used to check single sub-intervals of a large problem."""
+    K = p.K
+    co = {}
+    for k, c in p.coefs().items():
+        if c is None:
+            co[k] = None
+        elif c.mode == PER_STAGE:
+            co[k] = Coef(c.values[2 * K * j0: 2 * K * (j0 + count) + 1], PER_STAGE)
+        elif c.mode == PER_INTERVAL:
+            co[k] = Coef(c.values[j0:j0 + count], PER_INTERVAL)
+        else:
+            co[k] = c
+    return Problem(name=p.name + f"_w{j0}+{count}", n=p.n, m=p.m, nr=p.nr, T=count, K=K,
+                   t=p.t[j0:j0 + count + 1].copy(), Hf=p.Hf, Xf=p.Xf, rf=p.rf, x0=p.x0, extra=p.extra,
+                   funcs=p.funcs, **co)
