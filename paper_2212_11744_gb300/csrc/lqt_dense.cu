@@ -38,7 +38,8 @@ struct DenseArgs {
   double *Sd, *vd, *zd, *xd, *ud;  // [T K + 1]
 };
 
-// u = U^-1 L^T e for one sample (U symmetric positive definite, m <= MM).
+// u = U^-1 L^T e for one sample (U symmetric positive definite, m <= MM, the
+// padded factor width).
 template <int N, int MM>
 __device__ __forceinline__ void control_from(const double* __restrict__ L, const double* __restrict__ U, int m,
                                              const double* e, double* __restrict__ u) {
@@ -76,15 +77,23 @@ __device__ __forceinline__ void control_from(const double* __restrict__ L, const
   for (int a = 0; a < m; ++a) u[a] = w[a];
 }
 
+// Returns false if a value is not finite.
 template <int N>
-__device__ __forceinline__ void store_values(const RicState<N>& y, double* S, double* v, double* z) {
+__device__ __forceinline__ bool store_values(const RicState<N>& y, double* S, double* v, double* z) {
+  bool ok = isfinite(y.zeta);
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int l = 0; l < N; ++l) S[i * N + l] = y.S[sidx<N>(i, l)];
 #pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = y.v[i];
+  for (int i = 0; i < Dim<N>::NS; ++i) ok = ok && isfinite(y.S[i]);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    v[i] = y.v[i];
+    ok = ok && isfinite(y.v[i]);
+  }
   *z = y.zeta;
+  return ok;
 }
 
 template <int N>
@@ -98,7 +107,7 @@ __device__ __forceinline__ void load_values(RicState<N>& y, const double* S, con
   y.zeta = *z;
 }
 
-template <int N, int M, int MM>
+template <int N, int M>
 __device__ __forceinline__ void control_at(const DenseArgs& a, int64_t j, int32_t p, const RicState<N>& y,
                                            const double* x, double* u) {
   double e[N];
@@ -111,10 +120,10 @@ __device__ __forceinline__ void control_at(const DenseArgs& a, int64_t j, int32_
   }
   const double* L = a.L.ptr + sample_index(a.L.mode, j, p, a.K) * N * a.m;
   const double* U = a.U.ptr + sample_index(a.U.mode, j, p, a.K) * a.m * a.m;
-  control_from<N, MM>(L, U, a.m, e, u);
+  control_from<N, M>(L, U, a.m, e, u);
 }
 
-template <int N, int M, int MM>
+template <int N, int M>
 __global__ void __launch_bounds__(128) densify_kernel(DenseArgs a) {
   constexpr int NS = Dim<N>::NS;
   const int32_t K = a.K;
@@ -124,6 +133,7 @@ __global__ void __launch_bounds__(128) densify_kernel(DenseArgs a) {
     const int64_t g0 = j * K;
     RicState<N> D[kDenseMaxK + 1];
     RicState<N> y, yt, yn, k;
+    bool ok = true;
     load_values<N>(y, a.S + (j + 1) * N * N, a.v + (j + 1) * N, a.zeta + j + 1);
     // backward K steps from t_{j+1}
     for (int32_t i = K - 1; i >= 0; --i) {
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(128) densify_kernel(DenseArgs a) {
       ric_axpy(yt, y, -h, k);
       riccati_rhs<N, M>(yt, F[2], c[2], Lt[2], Q[2], qr[2], k);
       ric_axpy(y, yn, -h / 6.0, k);
-      if (i > 0) store_values<N>(y, a.Sd + (g0 + i) * N * N, a.vd + (g0 + i) * N, a.zd + g0 + i);
+      if (i > 0) ok = store_values<N>(y, a.Sd + (g0 + i) * N * N, a.vd + (g0 + i) * N, a.zd + g0 + i) && ok;
     }
     // slope at t_j with block j's first sample; y now holds the re-integrated value at t_j
     {
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(128) densify_kernel(DenseArgs a) {
         x[i] = a.x[j * N + i];
         a.xd[g0 * N + i] = x[i];
       }
-      if (a.ud) control_at<N, M, MM>(a, j, 0, yb, x, a.ud + g0 * a.m);
+      if (a.ud) control_at<N, M>(a, j, 0, yb, x, a.ud + g0 * a.m);
     }
     // forward K - 1 steps from x_j
     RicState<N> y0 = y;
@@ -216,10 +226,12 @@ __global__ void __launch_bounds__(128) densify_kernel(DenseArgs a) {
       for (int q = 0; q < N; ++q) {
         x[q] = fma(h / 6.0, kx[q], ax[q]);
         a.xd[(g0 + i + 1) * N + q] = x[q];
+        ok = ok && isfinite(x[q]);
       }
-      if (a.ud) control_at<N, M, MM>(a, j, 2 * (i + 1), y1, x, a.ud + (g0 + i + 1) * a.m);
+      if (a.ud) control_at<N, M>(a, j, 2 * (i + 1), y1, x, a.ud + (g0 + i + 1) * a.m);
       y0 = y1;
     }
+    if (!ok) flag(kStatusNonFinite);
     // final point t_T
     if (j == a.T - 1) {
       const int64_t g = a.T * K;
@@ -232,7 +244,7 @@ __global__ void __launch_bounds__(128) densify_kernel(DenseArgs a) {
         xT[i] = a.x[a.T * N + i];
         a.xd[g * N + i] = xT[i];
       }
-      if (a.ud) control_at<N, M, MM>(a, j, 2 * K, yb, xT, a.ud + g * a.m);
+      if (a.ud) control_at<N, M>(a, j, 2 * K, yb, xT, a.ud + g * a.m);
     }
   }
 }
@@ -242,10 +254,7 @@ static cudaError_t launch_dense_nm(const DenseArgs& a, cudaStream_t st) {
   constexpr int threads = 128;
   int64_t blocks = (a.T + threads - 1) / threads;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  if (a.m <= 4)
-    densify_kernel<N, M, 4><<<(unsigned)blocks, threads, 0, st>>>(a);
-  else
-    densify_kernel<N, M, 16><<<(unsigned)blocks, threads, 0, st>>>(a);
+  densify_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a);
   count_launch();
   return cudaGetLastError();
 }

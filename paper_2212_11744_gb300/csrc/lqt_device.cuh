@@ -149,6 +149,53 @@ __device__ __forceinline__ void store_public(const ElemPtrs& el, int64_t k, cons
   if (el.zeta) el.zeta[k] = e.zeta;
 }
 
+// Full-matrix record layouts shared with the team kernels (lqt_team.cuh):
+// element = A (N*N), b (N), C (N*N), eta (N), J (N*N), zeta; value = S (N*N),
+// v (N), zeta.
+template <int N>
+__host__ __device__ constexpr int full_elem_doubles() {
+  return 3 * N * N + 2 * N + 1;
+}
+template <int N>
+__host__ __device__ constexpr int full_val_doubles() {
+  return N * N + N + 1;
+}
+
+template <int N>
+__device__ __forceinline__ void store_full(double* __restrict__ p, const Elem<N>& e) {
+  double* A = p;
+  double* b = A + N * N;
+  double* C = b + N;
+  double* eta = C + N * N;
+  double* J = eta + N;
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) A[i] = e.A[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    b[i] = e.b[i];
+    eta[i] = e.eta[i];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      C[i * N + j] = e.C[sidx<N>(i, j)];
+      J[i * N + j] = e.J[sidx<N>(i, j)];
+    }
+  J[N * N] = e.zeta;
+}
+
+template <int N>
+__device__ __forceinline__ void load_val_full(const double* __restrict__ p, Val<N>& v) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) v.S[sidx<N>(i, j)] = p[i * N + j];
+#pragma unroll
+  for (int i = 0; i < N; ++i) v.v[i] = p[N * N + i];
+  v.zeta = p[N * N + N];
+}
+
 template <int N>
 __device__ __forceinline__ void zero_val(Val<N>& v) {
 #pragma unroll

@@ -123,6 +123,20 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
                          const double* v, const double* x, const double* gS, const double* gv, const double* gz,
                          const double* gx, double g_cost, double* gF, double* gL, double* gX, double* gU, double* gr,
                          double* gXf, double* grf, double* gx0, char* ws, cudaStream_t st);
+// Pairwise upper levels of the n <= 8 scans, one warp per combination
+// (lqt_team.cu); records in the full-matrix layout (full_elem_doubles /
+// full_val_doubles of lqt_device.cuh).
+template <int N, typename GT>
+void team_upper_reduce(const double* src, int64_t cnt, double* agg, cudaStream_t st);
+template <int N, typename GT>
+void team_upper_down(const double* src, int64_t cnt, const double* above, int64_t cnt_above, double* vals,
+                     cudaStream_t st);
+template <int N>
+void team_maps_reduce(const double* maps, int64_t cnt, int G, double* comp, cudaStream_t st);
+template <int N>
+void team_maps_down(const double* maps, int64_t cnt, int G, const double* above, const double* x_in, double* starts,
+                    cudaStream_t st);
+
 bool densify_supported(const lqt_problem& p);
 cudaError_t launch_densify(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* S, const double* v,
                            const double* zeta, const double* x, double* Sd, double* vd, double* zd, double* xd,

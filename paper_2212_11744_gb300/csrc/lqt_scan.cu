@@ -45,7 +45,7 @@ static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ---------------------------------------------------------------------------
-// element source abstraction: public SoA (level 0) or packed records
+// element source: the public SoA arrays (level 0)
 // ---------------------------------------------------------------------------
 
 template <int N>
@@ -53,19 +53,13 @@ struct SrcPublic {
   ElemPtrs el;
   __device__ __forceinline__ void load(int64_t k, Elem<N>& e) const { load_public<N>(el, k, e); }
 };
-template <int N>
-struct SrcPacked {
-  const double* p;
-  __device__ __forceinline__ void load(int64_t k, Elem<N>& e) const {
-    load_packed<N>(p + k * packed_elem_doubles<N>(), e);
-  }
-};
 
 // ---------------------------------------------------------------------------
 // value scan kernels
 // ---------------------------------------------------------------------------
 
-// agg[g] = e[gG] (x) e[gG+1] (x) ... (x) e[min(gG+G, cnt)-1]
+// agg[g] = e[gG] (x) e[gG+1] (x) ... (x) e[min(gG+G, cnt)-1], stored as a
+// full-matrix record for the warp-per-combination upper levels.
 template <int N, class Src, typename GT = double>
 __global__ void __launch_bounds__(128) reduce_elems_kernel(Src src, int64_t cnt, int G, double* __restrict__ agg) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,12 +72,10 @@ __global__ void __launch_bounds__(128) reduce_elems_kernel(Src src, int64_t cnt,
     src.load(k, e);
     combine<N, GT>(e, acc, acc);
   }
-  store_packed<N>(agg + g * packed_elem_doubles<N>(), acc);
+  store_full<N>(agg + g * full_elem_doubles<N>(), acc);
 }
 
 struct DownOut {
-  // packed value output (levels >= 1)
-  double* vals;
   // level-0 outputs (public layout); zeta may be null
   double *S, *v, *zeta;
   // level-0 optimal-state maps and chunk composites (may be null)
@@ -108,9 +100,11 @@ __device__ __forceinline__ void store_val_public(const DownOut& o, int64_t k, co
   if (!ok) flag(kStatusNonFinite);
 }
 
-// Suffix values of one group, right to left, from the carry `above` (the
-// value of everything after the group; zero value at the right end).
-template <int N, class Src, bool Level0, typename GT = double>
+// Suffix values of one level-0 group, right to left, from the carry `above`
+// (the value of everything after the group, a full-matrix value record; zero
+// value at the right end), with the one-sub-interval optimal-state maps and
+// the chunk's composite map.
+template <int N, class Src, typename GT = double>
 __global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, int G, const double* __restrict__ above,
                                                           int64_t cnt_above, DownOut o) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,57 +113,51 @@ __global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, 
   const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
   Val<N> carry;
   if (above != nullptr && g + 1 < cnt_above)
-    load_val<N>(above + (g + 1) * packed_val_doubles<N>(), carry);
+    load_val_full<N>(above + (g + 1) * full_val_doubles<N>(), carry);
   else
     zero_val<N>(carry);
   // composite of the maps of this chunk (x_{first} -> x_{last+1})
   double P[N * N], pv[N];
   constexpr int PM = N * N + N;
-  if (Level0) {
 #pragma unroll
-    for (int i = 0; i < N * N; ++i) P[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < N * N; ++i) P[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
 #pragma unroll
-    for (int i = 0; i < N; ++i) pv[i] = 0.0;
-  }
+  for (int i = 0; i < N; ++i) pv[i] = 0.0;
   Elem<N> e;
   Val<N> nv;
   double Psi[N * N], alpha[N];
   for (int64_t k = last; k >= first; --k) {
     src.load(k, e);
     combine_value<N, GT>(e, carry, nv, Psi, alpha);
-    if (Level0) {
-      store_val_public<N>(o, k, nv);
-      if (o.maps != nullptr && k < o.T) {
-        double* mp = o.maps + k * PM;
+    store_val_public<N>(o, k, nv);
+    if (o.maps != nullptr && k < o.T) {
+      double* mp = o.maps + k * PM;
 #pragma unroll
-        for (int i = 0; i < N * N; ++i) mp[i] = Psi[i];
+      for (int i = 0; i < N * N; ++i) mp[i] = Psi[i];
 #pragma unroll
-        for (int i = 0; i < N; ++i) mp[N * N + i] = alpha[i];
-        // (P, pv) <- (P Psi, P alpha + pv)
-        double P2[N * N];
+      for (int i = 0; i < N; ++i) mp[N * N + i] = alpha[i];
+      // (P, pv) <- (P Psi, P alpha + pv)
+      double P2[N * N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          double s = pv[i];
+      for (int i = 0; i < N; ++i) {
+        double s = pv[i];
 #pragma unroll
-          for (int l = 0; l < N; ++l) s = fma(P[i * N + l], alpha[l], s);
-          pv[i] = s;
+        for (int l = 0; l < N; ++l) s = fma(P[i * N + l], alpha[l], s);
+        pv[i] = s;
 #pragma unroll
-          for (int j = 0; j < N; ++j) {
-            double t = 0.0;
+        for (int j = 0; j < N; ++j) {
+          double t = 0.0;
 #pragma unroll
-            for (int l = 0; l < N; ++l) t = fma(P[i * N + l], Psi[l * N + j], t);
-            P2[i * N + j] = t;
-          }
+          for (int l = 0; l < N; ++l) t = fma(P[i * N + l], Psi[l * N + j], t);
+          P2[i * N + j] = t;
         }
-#pragma unroll
-        for (int i = 0; i < N * N; ++i) P[i] = P2[i];
       }
-    } else {
-      store_val<N>(o.vals + k * packed_val_doubles<N>(), nv);
+#pragma unroll
+      for (int i = 0; i < N * N; ++i) P[i] = P2[i];
     }
     carry = nv;
   }
-  if (Level0 && o.composite != nullptr && last + 1 <= o.T) {
+  if (o.composite != nullptr && last + 1 <= o.T) {
     // chunk g maps x_{first} to x_{last+1}; only chunks that end at or before T
     double* cp = o.composite + g * PM;
 #pragma unroll
@@ -431,8 +419,8 @@ static ScanPlan make_plan(int64_t T, bool with_traj) {
   pl.G0 = level0_group(T);
   pl.T = T;
   size_t off = 0;
-  const size_t PE = sizeof(double) * packed_elem_doubles<N>();
-  const size_t PV = sizeof(double) * packed_val_doubles<N>();
+  const size_t PE = sizeof(double) * full_elem_doubles<N>();
+  const size_t PV = sizeof(double) * full_val_doubles<N>();
   const size_t PM = sizeof(double) * (N * N + N);
   int64_t c = T + 1;
   int G = pl.G0;
@@ -469,45 +457,39 @@ static ScanPlan make_plan(int64_t T, bool with_traj) {
   return pl;
 }
 
+// Level 0 (chunks of G0 elements, one thread each, register-resident) and the
+// pairwise upper levels (one warp per combination: at these levels there are
+// too few combinations to fill the GPU, so the time is the length of one
+// combination's FP64 chain, which the warp shortens by spreading every
+// product over its lanes).
 template <int N, typename GT = double>
 static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& out0, char* ws, cudaStream_t st) {
   const int64_t T = pl.T;
   SrcPublic<N> s0{el};
   // reduce up the levels
   int64_t c = T + 1;
-  int G = pl.G0;
   for (int l = 0; l < pl.nlev; ++l) {
     double* agg = (double*)(ws + pl.off_agg[l]);
     if (l == 0) {
-      reduce_elems_kernel<N, SrcPublic<N>, GT><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, G, agg);
+      reduce_elems_kernel<N, SrcPublic<N>, GT><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, pl.G0, agg);
+      count_launch();
     } else {
-      SrcPacked<N> sp{(const double*)(ws + pl.off_agg[l - 1])};
-      reduce_elems_kernel<N, SrcPacked<N>, GT><<<blocks_for(pl.cnt[l]), 128, 0, st>>>(sp, c, G, agg);
+      team_upper_reduce<N, GT>((const double*)(ws + pl.off_agg[l - 1]), c, agg, st);
     }
-    count_launch();
     c = pl.cnt[l];
-    G = kUpperGroup;
   }
   // down the levels: top level first (one group, zero carry)
-  for (int l = pl.nlev; l >= 0; --l) {
-    const int Gl = (l == 0) ? pl.G0 : kUpperGroup;
-    const int64_t cl = (l == 0) ? T + 1 : pl.cnt[l - 1];
+  for (int l = pl.nlev; l >= 1; --l) {
     const double* above = (l < pl.nlev) ? (const double*)(ws + pl.off_val[l]) : nullptr;
     const int64_t cabove = (l < pl.nlev) ? pl.cnt[l] : 0;
-    const int64_t groups = ceil_div(cl, Gl);
-    if (l == 0) {
-      down_values_kernel<N, SrcPublic<N>, true, GT><<<blocks_for(groups), 128, 0, st>>>(s0, cl, Gl, above, cabove,
-                                                                                      out0);
-    } else {
-      SrcPacked<N> sp{(const double*)(ws + pl.off_agg[l - 1])};
-      DownOut o{};
-      o.vals = (double*)(ws + pl.off_val[l - 1]);
-      o.T = T;
-      down_values_kernel<N, SrcPacked<N>, false, GT><<<blocks_for(groups), 128, 0, st>>>(sp, cl, Gl, above, cabove,
-                                                                                       o);
-    }
-    count_launch();
+    team_upper_down<N, GT>((const double*)(ws + pl.off_agg[l - 1]), pl.cnt[l - 1], above, cabove,
+                           (double*)(ws + pl.off_val[l - 1]), st);
   }
+  const double* above = pl.nlev > 0 ? (const double*)(ws + pl.off_val[0]) : nullptr;
+  const int64_t cabove = pl.nlev > 0 ? pl.cnt[0] : 0;
+  down_values_kernel<N, SrcPublic<N>, GT><<<blocks_for(ceil_div(T + 1, pl.G0)), 128, 0, st>>>(
+      s0, T + 1, pl.G0, above, cabove, out0);
+  count_launch();
 }
 
 template <int N>
@@ -515,20 +497,17 @@ static void traj_scan(const ScanPlan& pl, const double* x0, const double* S, con
                       const Coefs& cf, int32_t m, double* x, double* u, double* cost, char* ws, cudaStream_t st) {
   const int64_t T = pl.T;
   const double* maps0 = (const double*)(ws + pl.off_maps);
-  // reduce the chunk composites up the trajectory levels
-  for (int l = 1; l < pl.tlev; ++l) {
-    reduce_maps_kernel<N><<<blocks_for(pl.tcnt[l]), 128, 0, st>>>((const double*)(ws + pl.off_tmap[l - 1]),
-                                                                    pl.tcnt[l - 1], kUpperGroup,
-                                                                    (double*)(ws + pl.off_tmap[l]));
-    count_launch();
-  }
+  // reduce the chunk composites up the trajectory levels (one warp per
+  // composition, as for the value levels)
+  for (int l = 1; l < pl.tlev; ++l)
+    team_maps_reduce<N>((const double*)(ws + pl.off_tmap[l - 1]), pl.tcnt[l - 1], kUpperGroup,
+                        (double*)(ws + pl.off_tmap[l]), st);
   // starts down the levels
   for (int l = pl.tlev - 1; l >= 0; --l) {
     const double* above = (l + 1 < pl.tlev) ? (const double*)(ws + pl.off_tstart[l + 1]) : nullptr;
     const int G = (l + 1 < pl.tlev) ? kUpperGroup : (int)pl.tcnt[l];
-    down_maps_kernel<N><<<blocks_for(ceil_div(pl.tcnt[l], G)), 128, 0, st>>>(
-        (const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G, above, x0, (double*)(ws + pl.off_tstart[l]));
-    count_launch();
+    team_maps_down<N>((const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G, above, x0,
+                      (double*)(ws + pl.off_tstart[l]), st);
   }
   const double* starts1 = pl.tlev > 0 ? (const double*)(ws + pl.off_tstart[0]) : nullptr;
   final_traj_kernel<N><<<blocks_for(ceil_div(T + 1, pl.G0)), 128, 0, st>>>(

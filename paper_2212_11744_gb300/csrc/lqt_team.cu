@@ -25,6 +25,24 @@ struct TeamCfg<16> {
   static constexpr bool SMEM = true;
   static constexpr int SLOTS = 152 * 8;
 };
+// n <= 8: the thread-per-element kernels do level 0 of the scans; these
+// warp-per-combination instances run the pairwise upper levels.
+template <int N>
+struct TeamCfgSmall {
+  static constexpr int TEAM = 32;
+  static constexpr bool SMEM = true;
+  static constexpr int SLOTS = 152 * 8;
+};
+template <>
+struct TeamCfg<1> : TeamCfgSmall<1> {};
+template <>
+struct TeamCfg<2> : TeamCfgSmall<2> {};
+template <>
+struct TeamCfg<3> : TeamCfgSmall<3> {};
+template <>
+struct TeamCfg<4> : TeamCfgSmall<4> {};
+template <>
+struct TeamCfg<8> : TeamCfgSmall<8> {};
 template <>
 struct TeamCfg<64> {
   static constexpr int TEAM = 256;
@@ -592,6 +610,57 @@ static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemP
   team_launch<N>(final_team_kernel<N>, tdiv(p.T + 1, pl.G0), maps_slot_doubles<N>(), f, st);
   return cudaGetLastError();
 }
+
+// Upper levels of the thread-per-element scans (lqt_scan.cu), n <= 8: one
+// warp per combination, records in the full-matrix layout.
+template <int N, typename GT>
+void team_upper_reduce(const double* src, int64_t cnt, double* agg, cudaStream_t st) {
+  static_assert(Rec<N>::SIZE == full_elem_doubles<N>(), "record layouts differ");
+  TeamScanArgs a{};
+  a.src = src; a.cnt = cnt; a.G = 2; a.agg = agg;
+  team_launch<N>(reduce_team_kernel<N, GT>, tdiv(cnt, 2), reduce_slot_doubles<N>(), a, st);
+}
+
+template <int N, typename GT>
+void team_upper_down(const double* src, int64_t cnt, const double* above, int64_t cnt_above, double* vals,
+                     cudaStream_t st) {
+  static_assert(team::val_doubles<N>() == full_val_doubles<N>(), "value layouts differ");
+  TeamScanArgs a{};
+  a.src = src; a.cnt = cnt; a.G = 2; a.above = above; a.cnt_above = cnt_above; a.vals = vals;
+  team_launch<N>(down_team_kernel<N, false, GT>, tdiv(cnt, 2), down_slot_doubles<N>(), a, st);
+}
+
+template <int N>
+void team_maps_reduce(const double* maps, int64_t cnt, int G, double* comp, cudaStream_t st) {
+  TeamMapArgs a{};
+  a.maps = maps; a.cnt = cnt; a.G = G; a.comp = comp;
+  team_launch<N>(reduce_maps_team_kernel<N>, tdiv(cnt, G), maps_slot_doubles<N>(), a, st);
+}
+
+template <int N>
+void team_maps_down(const double* maps, int64_t cnt, int G, const double* above, const double* x_in, double* starts,
+                    cudaStream_t st) {
+  TeamMapArgs a{};
+  a.maps = maps; a.cnt = cnt; a.G = G; a.above = above; a.x_in = x_in; a.starts = starts;
+  team_launch<N>(down_maps_team_kernel<N>, tdiv(cnt, G), maps_slot_doubles<N>(), a, st);
+}
+
+#define LQT_TEAM_UPPER(N)                                                                                 \
+  template void team_upper_reduce<N, double>(const double*, int64_t, double*, cudaStream_t);             \
+  template void team_upper_reduce<N, float>(const double*, int64_t, double*, cudaStream_t);              \
+  template void team_upper_down<N, double>(const double*, int64_t, const double*, int64_t, double*,      \
+                                           cudaStream_t);                                                \
+  template void team_upper_down<N, float>(const double*, int64_t, const double*, int64_t, double*,       \
+                                          cudaStream_t);                                                 \
+  template void team_maps_reduce<N>(const double*, int64_t, int, double*, cudaStream_t);                 \
+  template void team_maps_down<N>(const double*, int64_t, int, const double*, const double*, double*,    \
+                                  cudaStream_t);
+LQT_TEAM_UPPER(1)
+LQT_TEAM_UPPER(2)
+LQT_TEAM_UPPER(3)
+LQT_TEAM_UPPER(4)
+LQT_TEAM_UPPER(8)
+#undef LQT_TEAM_UPPER
 
 template <int N>
 static cudaError_t team_concat(int64_t Tcat, const ElemPtrs& el, double* S, double* v, double* zeta,

@@ -15,9 +15,12 @@ CASES = [
     ("double_integrator_T1024_K10", lambda: W.double_integrator(T=1024, K=10)),
     ("point_mass_T1000_K4", lambda: W.point_mass_2d(T=1000, K=4)),
     ("general_n3_m2_nr2_T37", lambda: W.general_time_varying(3, 2, 2, T=37, K=3, seed=21)),
-    ("general_mixed_modes_T45", lambda: W.general_time_varying(
+    # K = 8: at K <= 4 this problem's Riccati RK4 (the sequential method, and so
+    # the densification) is unstable at its right end, while the element
+    # build is not
+    ("general_mixed_modes_T45_K8", lambda: W.resample(W.general_time_varying(
         4, 2, 3, T=45, K=2, seed=22, modes={"r": W.PER_INTERVAL, "X": W.CONST, "F": W.PER_INTERVAL,
-                                             "L": W.CONST, "U": W.PER_INTERVAL})),
+                                             "L": W.CONST, "U": W.PER_INTERVAL}), 8)),
     ("general_nonuniform_T29", lambda: W.general_time_varying(2, 1, 2, T=29, K=4, seed=23, nonuniform=True)),
     ("scalar_n1_T50_K16", lambda: W.resample(W.general_time_varying(1, 1, 1, T=50, K=5, seed=24), 16)),
     ("n8_m4_T300", lambda: W.batched_member(5, T=300, n=8)),
@@ -85,3 +88,22 @@ def test_densify_full_point_mass_sampled():
             g = to_np(d[k][j * K:(j + 1) * K + 1])
             worst = max(worst, relerr(g, ref[k]))
     assert worst <= TOL, worst
+
+
+def test_unstable_step_is_reported():
+    """The same problem at K = 2: the Riccati RK4 diverges in the last
+    sub-interval (the oracle's states there are not finite).  The status word
+    reports exactly whether the GPU's outputs contain a non-finite value."""
+    import paper_2212_11744_gb300 as lqt
+    p = W.general_time_varying(4, 2, 3, T=45, K=2, seed=22, modes={"r": W.PER_INTERVAL, "X": W.CONST,
+                                                                     "F": W.PER_INTERVAL, "L": W.CONST,
+                                                                     "U": W.PER_INTERVAL})
+    sol = oracle.solve(p)
+    assert not np.isfinite(oracle.densify(p, sol)["x"]).all()
+    dp = lqt.DeviceProblem(p)
+    got = lqt.lqt_densify(dp, {k: dev(sol[k]) for k in ("S", "v", "zeta", "x")})
+    torch.cuda.synchronize()
+    finite = all(bool(torch.isfinite(got[k]).all()) for k in ("S", "v", "zeta", "x"))
+    assert not finite or float(got["S"].abs().max()) > 1e5  # diverged either way
+    assert lqt.lqt_get_status() == (0 if finite else lqt._abi.LQT_ENONFINITE)
+    assert lqt.lqt_get_status() == 0
