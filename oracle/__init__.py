@@ -58,10 +58,14 @@ def _configure(L):
     L.orc_solve.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_sequential.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_densify.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_build_elements_forward.argtypes = [P, ct.c_long, ct.c_long, _dp]
+    L.orc_prefix.argtypes = [ct.c_int, ct.c_long, _dp, _dp]
+    L.orc_trajectory_method2.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
     L.orc_element_size.argtypes = [ct.c_int]
     L.orc_element_size.restype = ct.c_long
     for f in ("orc_build_elements", "orc_combine", "orc_suffix_values", "orc_trajectory", "orc_solve",
-              "orc_sequential", "orc_densify"):
+              "orc_sequential", "orc_densify", "orc_build_elements_forward", "orc_prefix",
+              "orc_trajectory_method2"):
         getattr(L, f).restype = ct.c_int
     return L
 
@@ -252,3 +256,36 @@ def fine_times(p) -> np.ndarray:
     t = np.asarray(p.t, dtype=np.float64)
     out = (t[:-1, None] + (t[1:] - t[:-1])[:, None] * (np.arange(K)[None, :] / K)).ravel()
     return np.concatenate([out, t[-1:]])
+
+
+def build_elements_forward(p, j0: int = 0, j1: int | None = None) -> dict:
+    """Elements j0..j1-1 (j < T) from K RK4 steps of the forward conditional
+    HJB ODEs (Sec. IV-C), unpacked."""
+    j1 = p.T if j1 is None else j1
+    out = np.zeros((j1 - j0, element_size(p.n)))
+    m = _Marshalled(p)
+    if lib().orc_build_elements_forward(m.ref(), j0, j1, _ptr(out)):
+        raise FloatingPointError("oracle: singular U sample")
+    return unpack(p.n, out)
+
+
+def prefix(n: int, elems: dict) -> dict:
+    """The T+1 prefixes p_k = a_0 (x) ... (x) a_{k-1} (p_0 = identity) of T elements."""
+    packed = pack(n, elems)
+    T = packed.shape[0]
+    out = np.zeros((T + 1, element_size(n)))
+    if lib().orc_prefix(n, T, _ptr(packed), _ptr(out)):
+        raise FloatingPointError("oracle: singular combination")
+    return unpack(n, out)
+
+
+def trajectory_method2(p, S, v, x0=None) -> dict:
+    """Optimal states and controls at the boundaries by Method 2 with
+    forward-ODE elements, given the values S, v."""
+    x0 = np.ascontiguousarray(p.x0 if x0 is None else x0, dtype=np.float64)
+    x = np.zeros((p.T + 1, p.n)); u = np.zeros((p.T + 1, p.m))
+    m = _Marshalled(p)
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    if lib().orc_trajectory_method2(m.ref(), _ptr(c(S)), _ptr(c(v)), _ptr(x0), _ptr(x), _ptr(u)):
+        raise FloatingPointError("oracle: singular matrix in Method 2")
+    return {"x": x, "u": u}

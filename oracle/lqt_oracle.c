@@ -693,6 +693,153 @@ int orc_sequential(const orc_problem *P, const double *x0, double *S, double *v,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Method 2: forward-HJB elements, prefix fold, optimal states                 */
+/* ------------------------------------------------------------------------ */
+
+/* Right-hand side of the forward conditional HJB ODEs in tau (Sec. IV-C,
+ * Theorem "Forward_HJB_LQT"), with Q = H^T X H, q = H^T X r, B = L U^{-1} L^T:
+ *   dA/dtau    = -C Q A + F A
+ *   db/dtau    =  C q + F b - C Q b + c
+ *   dC/dtau    = -C Q C + B + F C + C F^T
+ *   deta/dtau  =  A^T q - A^T Q b
+ *   dJ/dtau    =  A^T Q A
+ *   dzeta/dtau =  1/2 r^T X r - b^T q + 1/2 b^T Q b
+ * The zeta equation is the state-free part of the forward conditional HJB
+ * (eq. forward_conditional_HJB) at x = 0, z = b, where the multiplier vanishes:
+ * the running cost of the target state b.  tmp needs 4 n^2 doubles. */
+static void forward_rhs(int n, const coefs *cf, const double *y, double *dy, double *tmp) {
+  elem_view s = view(n, (double *)y), d = view(n, dy);
+  double *QA = tmp, *CQ = tmp + n * n, *M1 = tmp + 2 * n * n, *M2 = tmp + 3 * n * n;
+  mm(n, n, n, cf->Q, s.A, QA);
+  mm(n, n, n, s.C, cf->Q, CQ);
+  /* dA = -C (Q A) + F A */
+  mm(n, n, n, s.C, QA, M1);
+  mm(n, n, n, cf->F, s.A, M2);
+  for (int i = 0; i < n * n; ++i) d.A[i] = M2[i] - M1[i];
+  /* db = C q + F b - C Q b + c */
+  for (int i = 0; i < n; ++i) {
+    double acc = cf->c[i];
+    for (int k = 0; k < n; ++k) acc += s.C[i * n + k] * cf->q[k] + cf->F[i * n + k] * s.b[k];
+    for (int k = 0; k < n; ++k) acc -= CQ[i * n + k] * s.b[k];
+    d.b[i] = acc;
+  }
+  /* dC = -C Q C + B + F C + C F^T */
+  mm(n, n, n, CQ, s.C, M1);
+  mm(n, n, n, cf->F, s.C, M2);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      d.C[i * n + j] = -M1[i * n + j] + cf->B[i * n + j] + M2[i * n + j] + M2[j * n + i];
+  symmetrise(n, d.C);
+  /* deta = A^T (q - Q b);  dJ = A^T Q A */
+  double *w = M1; /* n */
+  for (int i = 0; i < n; ++i) {
+    double acc = cf->q[i];
+    for (int k = 0; k < n; ++k) acc -= cf->Q[i * n + k] * s.b[k];
+    w[i] = acc;
+  }
+  mtm(n, n, 1, s.A, w, d.eta);
+  mtm(n, n, n, s.A, QA, d.J);
+  symmetrise(n, d.J);
+  /* dzeta */
+  double z = 0.5 * cf->rho;
+  for (int i = 0; i < n; ++i) {
+    double Qb = 0.0;
+    for (int k = 0; k < n; ++k) Qb += cf->Q[i * n + k] * s.b[k];
+    z += -s.b[i] * cf->q[i] + 0.5 * s.b[i] * Qb;
+  }
+  *d.zeta = z;
+}
+
+/* Element a_j = V(., t_j; ., t_{j+1}) by K classical RK4 steps of the forward
+ * conditional ODEs in tau, from A = I and the rest 0 at tau = t_j (eq.
+ * abcej_boundary) up to tau = t_{j+1}; step i uses the samples at half-steps
+ * p = 2i, 2i+1, 2i+2. */
+static int build_block_forward(const orc_problem *P, long j, double *e) {
+  int n = P->n, K = P->K;
+  size_t es = elem_size(n);
+  double h = (P->t[j + 1] - P->t[j]) / K;
+  double *buf = (double *)malloc(sizeof(double) * (5 * es + 4 * (size_t)n * n + coefs_size(n, P->m, P->nr)));
+  double *y = buf, *yt = y + es, *k = yt + es, *acc = k + es, *tmp = acc + es;
+  double *cur = tmp + 4 * (size_t)n * n + es;
+  coefs cf;
+  coefs_alloc(&cf, n, P->m, P->nr, &cur);
+  memset(y, 0, sizeof(double) * es);
+  eye(n, view(n, y).A);
+  int bad = 0;
+  for (int i = 0; i < K; ++i) {
+    bad |= coefs_eval(P, j, 2 * i, &cf);
+    forward_rhs(n, &cf, y, k, tmp);
+    for (size_t q = 0; q < es; ++q) { acc[q] = k[q]; yt[q] = y[q] + 0.5 * h * k[q]; }
+    bad |= coefs_eval(P, j, 2 * i + 1, &cf);
+    forward_rhs(n, &cf, yt, k, tmp);
+    for (size_t q = 0; q < es; ++q) { acc[q] += 2.0 * k[q]; yt[q] = y[q] + 0.5 * h * k[q]; }
+    forward_rhs(n, &cf, yt, k, tmp);
+    for (size_t q = 0; q < es; ++q) { acc[q] += 2.0 * k[q]; yt[q] = y[q] + h * k[q]; }
+    bad |= coefs_eval(P, j, 2 * i + 2, &cf);
+    forward_rhs(n, &cf, yt, k, tmp);
+    for (size_t q = 0; q < es; ++q) { acc[q] += k[q]; y[q] = y[q] + (h / 6.0) * acc[q]; }
+  }
+  memcpy(e, y, sizeof(double) * es);
+  free(buf);
+  return bad;
+}
+
+/* Forward-ODE elements j in [j0, j1), 0 <= j0 <= j1 <= T (no terminal element). */
+int orc_build_elements_forward(const orc_problem *P, long j0, long j1, double *elems) {
+  size_t es = elem_size(P->n);
+  int bad = 0;
+  for (long j = j0; j < j1; ++j) bad |= build_block_forward(P, j, elems + (size_t)(j - j0) * es);
+  return bad;
+}
+
+/* Prefixes of T elements by the sequential left-to-right fold (Theorem
+ * "parallel_HJB", eq. parallel_cond_B_HJB): p_0 = identity element,
+ * p_{k+1} = p_k (x) a_k = V(., t_0; ., t_{k+1}).  Writes the T+1 prefixes. */
+int orc_prefix(int n, long T, const double *elems, double *prefixes) {
+  size_t es = elem_size(n);
+  memset(prefixes, 0, sizeof(double) * es);
+  eye(n, view(n, prefixes).A);
+  int bad = 0;
+  for (long k = 0; k < T; ++k)
+    bad |= orc_combine(n, prefixes + (size_t)k * es, elems + (size_t)k * es, prefixes + (size_t)(k + 1) * es);
+  return bad;
+}
+
+/* Method 2 (Sec. IV-E, eq. Opt_trajectory_method2 in the LQT form):
+ *   x_k = (I + C(t_0,t_k) S_k)^{-1} (A(t_0,t_k) x0 + b(t_0,t_k) + C(t_0,t_k) v_k)
+ * with (A, b, C)(t_0, t_k) from the prefixes of the forward-ODE elements, then
+ * the controls of eq. LQT_optimal_control.  x[(T+1) n], u[(T+1) m]. */
+int orc_trajectory_method2(const orc_problem *P, const double *S, const double *v, const double *x0, double *x,
+                           double *u) {
+  int n = P->n;
+  long T = P->T;
+  size_t es = elem_size(n), nn = (size_t)n * n;
+  double *el = (double *)malloc(sizeof(double) * es * (size_t)(2 * T + 1));
+  double *pre = el + es * (size_t)T;
+  int bad = orc_build_elements_forward(P, 0, T, el);
+  bad |= orc_prefix(n, T, el, pre);
+  double *W = (double *)malloc(sizeof(double) * (nn + 4 * (size_t)n + coefs_size(n, P->m, P->nr)));
+  double *rhs = W + nn, *tv = rhs + n, *cur = tv + 3 * (size_t)n;
+  coefs cf;
+  coefs_alloc(&cf, n, P->m, P->nr, &cur);
+  for (long k = 0; k <= T; ++k) {
+    elem_view pk = view(n, pre + (size_t)k * es);
+    const double *Sk = S + (size_t)k * nn, *vk = v + (size_t)k * n;
+    mm(n, n, n, pk.C, Sk, W);
+    for (int i = 0; i < n; ++i) W[i * n + i] += 1.0;
+    mm(n, n, 1, pk.A, x0, rhs);
+    mm(n, n, 1, pk.C, vk, tv);
+    for (int i = 0; i < n; ++i) rhs[i] += pk.b[i] + tv[i];
+    bad |= solve(n, 1, W, rhs);
+    memcpy(x + (size_t)k * n, rhs, sizeof(double) * n);
+    bad |= control_at(P, k, Sk, vk, x + (size_t)k * n, u + (size_t)k * P->m, tv, &cf);
+  }
+  free(W);
+  free(el);
+  return bad;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Densification: values, states and controls at every RK4 sub-step          */
 /* ------------------------------------------------------------------------ */
 

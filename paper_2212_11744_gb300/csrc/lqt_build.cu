@@ -185,11 +185,49 @@ __global__ void __launch_bounds__(256) qr_identity_kernel(const double* __restri
   out[N] = rho;
 }
 
+// The same with N consecutive threads per sample (N a power of two <= 32),
+// thread i forming row i of X r: a warp reads 32 consecutive rows, so the
+// stream of X samples (the largest input when X is sampled per half-step) is
+// read in full 128-byte lines; rho is reduced over the N lanes.
+template <int N>
+__global__ void __launch_bounds__(256) qr_rows_kernel(const double* __restrict__ X, int32_t X_mode,
+                                                      const double* __restrict__ r, int32_t r_mode, int32_t dmode,
+                                                      int64_t cnt, int32_t K, int64_t T, double* __restrict__ qr) {
+  static_assert(N >= 2 && N <= 32 && (N & (N - 1)) == 0, "rows kernel needs a power-of-two N <= 32");
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = tid / N;
+  const int i = (int)(tid % N);
+  const bool live = s < cnt;
+  double q = 0.0, ri = 0.0;
+  if (live) {
+    const double* row = X + input_index(X_mode, dmode, s, K, T) * N * N + i * N;
+    if (r) {
+      const double* rs = r + input_index(r_mode, dmode, s, K, T) * N;
+#pragma unroll
+      for (int l = 0; l < N; ++l) q = fma(row[l], rs[l], q);
+      ri = rs[i];
+    }
+  }
+  double rho = ri * q;
+#pragma unroll
+  for (int o = N / 2; o > 0; o >>= 1) rho += __shfl_xor_sync(0xffffffffu, rho, o);
+  if (live) {
+    qr[s * (N + 1) + i] = q;
+    if (i == 0) qr[s * (N + 1) + N] = rho;
+  }
+}
+
 template <int N>
 static void launch_qr_identity(const PrepArgs& a, cudaStream_t st) {
   const int threads = 256;
-  qr_identity_kernel<N><<<(unsigned)((a.cnt_qr + threads - 1) / threads), threads, 0, st>>>(
-      a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr, a.K, a.T, a.qr);
+  if constexpr (N >= 2 && N <= 32 && (N & (N - 1)) == 0) {
+    const int64_t total = a.cnt_qr * N;
+    qr_rows_kernel<N><<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
+        a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr, a.K, a.T, a.qr);
+  } else {
+    qr_identity_kernel<N><<<(unsigned)((a.cnt_qr + threads - 1) / threads), threads, 0, st>>>(
+        a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr, a.K, a.T, a.qr);
+  }
   count_launch();
 }
 

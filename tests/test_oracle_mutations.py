@@ -2,8 +2,8 @@
 
 Each case below plants one mistake in a copy of oracle/lqt_oracle.c (a dropped
 term, a flipped sign, a transposed operand, a wrong index or weight), compiles
-the copy, and runs every pin of test_oracle_pins.py and test_oracle_densify.py
-against it.  At least one
+the copy, and runs every pin of test_oracle_pins.py, test_oracle_densify.py
+and test_oracle_method2.py against it.  At least one
 pin has to fail for every mutant; otherwise the pins would also have let that
 mistake through in the real oracle.  Nothing here touches the GPU.
 """
@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_densify as densify_pins
+from tests import test_oracle_method2 as method2_pins
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lqt_oracle.c")
@@ -82,6 +83,21 @@ MUTATIONS = [
      "bad |= coefs_eval(P, j, 1, &cf);\n    riccati_rhs(n, &cf, Y, D, tmp);", 0),
     ("densify: control sample", "bad |= coefs_eval(P, j, 2 * i, &cf);\n      mm(n, n, 1, Sd",
      "bad |= coefs_eval(P, j, 0, &cf);\n      mm(n, n, 1, Sd", 0),
+    # Method 2: forward-HJB elements, prefix fold, states
+    ("forward dA: sign of F A", "for (int i = 0; i < n * n; ++i) d.A[i] = M2[i] - M1[i];",
+     "for (int i = 0; i < n * n; ++i) d.A[i] = -M2[i] - M1[i];", 0),
+    ("forward db: dropped c", "double acc = cf->c[i];\n    for (int k = 0; k < n; ++k) acc += s.C[i * n + k] * cf->q[k]",
+     "double acc = 0.0;\n    for (int k = 0; k < n; ++k) acc += s.C[i * n + k] * cf->q[k]", 0),
+    ("forward dC: dropped B", "-M1[i * n + j] + cf->B[i * n + j] + M2[i * n + j]", "-M1[i * n + j] + M2[i * n + j]", 0),
+    ("forward deta: sign of Q b", "for (int k = 0; k < n; ++k) acc -= cf->Q[i * n + k] * s.b[k];\n    w[i] = acc;",
+     "for (int k = 0; k < n; ++k) acc += cf->Q[i * n + k] * s.b[k];\n    w[i] = acc;", 0),
+    ("forward dzeta: factor of b Q b", "z += -s.b[i] * cf->q[i] + 0.5 * s.b[i] * Qb;", "z += -s.b[i] * cf->q[i] + s.b[i] * Qb;", 0),
+    ("forward RK4: k4 sample", "bad |= coefs_eval(P, j, 2 * i + 2, &cf);\n    forward_rhs",
+     "bad |= coefs_eval(P, j, 2 * i + 1, &cf);\n    forward_rhs", 0),
+    ("prefix: operands swapped", "orc_combine(n, prefixes + (size_t)k * es, elems + (size_t)k * es,",
+     "orc_combine(n, elems + (size_t)k * es, prefixes + (size_t)k * es,", 0),
+    ("method 2: dropped C v", "for (int i = 0; i < n; ++i) rhs[i] += pk.b[i] + tv[i];",
+     "for (int i = 0; i < n; ++i) rhs[i] += pk.b[i];", 0),
     # shared small linear algebra
     ("mtm: operand not transposed", "for (int l = 0; l < k; ++l) s += a[l * p + i] * b[l * q + j];",
      "for (int l = 0; l < k; ++l) s += a[i * k + l] * b[l * q + j];", 0),
@@ -99,9 +115,10 @@ def _replace_nth(text, old, new, nth):
 def _pin_calls():
     """Every (name, zero-argument callable) for the pins, parametrisations expanded."""
     calls = []
-    members = inspect.getmembers(pins, inspect.isfunction) + inspect.getmembers(densify_pins, inspect.isfunction)
+    mods = (pins, densify_pins, method2_pins)
+    members = [m for mod in mods for m in inspect.getmembers(mod, inspect.isfunction)]
     for name, fn in members:
-        if not name.startswith("test_") or fn.__module__ not in (pins.__name__, densify_pins.__name__):
+        if not name.startswith("test_") or fn.__module__ not in tuple(mod.__name__ for mod in mods):
             continue
         marks = getattr(fn, "pytestmark", [])
         params = [m for m in marks if m.name == "parametrize"]
