@@ -127,9 +127,22 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def source_hash() -> str:
+    """sha256 (first 16 hex digits) of the element-build kernel's own source:
+    the right-hand side, RK4 driver and kernel in lqt_build.cu and the element
+    types and stores of lqt_device.cuh that it uses."""
+    csrc = os.path.join(ROOT, "paper_2212_11744_gb300", "csrc")
+    build = open(os.path.join(csrc, "lqt_build.cu")).read()
+    dev = open(os.path.join(csrc, "lqt_device.cuh")).read()
+    parts = [
+        build[build.index("// Right-hand side of the backward conditional HJB ODEs in s:"):
+              build.index("// Terminal element a_T")],
+        dev[:dev.index("// Packed element size")],
+    ]
+    i0 = dev.index("template <int N>\n__device__ __forceinline__ void store_public")
+    parts.append(dev[i0:dev.index("template <int N>", i0 + 10)])
     h = hashlib.sha256()
-    for f in ("lqt_build.cu", "lqt_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2212_11744_gb300", "csrc", f), "rb").read())
+    for part in parts:
+        h.update(part.encode())
     return h.hexdigest()[:16]
 
 

@@ -109,7 +109,9 @@ enum {
   LQT_WS_SOLVE = 3,
   LQT_WS_SEQUENTIAL = 4,
   LQT_WS_BACKWARD = 5,
-  LQT_WS_DENSIFY = 6
+  LQT_WS_DENSIFY = 6,
+  LQT_WS_METHOD2 = 7,
+  LQT_WS_SOLVE_METHOD2 = 8
 };
 
 /* Bytes of device workspace the call `which` needs for problem p (host call,
@@ -170,6 +172,40 @@ lqt_status lqt_solve_mixed(const lqt_problem *p, const double *x0, double *S, do
  * interpolant of the backward solution.  Same outputs as lqt_solve. */
 lqt_status lqt_solve_sequential(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta,
                                 double *x, double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* Method 2 of the optimal-trajectory recovery (Sec. IV-E, eq.
+ * Opt_trajectory_method2) with elements from the forward conditional HJB ODEs
+ * (Sec. IV-C, Theorem Forward_HJB_LQT).  Supported: n <= 8 (otherwise
+ * LQT_EUNSUPPORTED).  All three are asynchronous and allocation-free.
+ *
+ * lqt_build_elements_forward: the T elements a_j = V(., t_j; ., t_{j+1}),
+ * j = 0..T-1 (no terminal element), each by K classical RK4 steps of the
+ * forward conditional ODEs in tau from A = I, b = C = eta = J = 0, zeta = 0 at
+ * tau = t_j (eq. abcej_boundary) to t_{j+1}, stage samples at half-steps 2i,
+ * 2i+1, 2i+2 of step i.  zeta (not given in the paper) follows
+ * dzeta/dtau = r'Xr/2 - b'H'Xr + b'H'XHb/2, the state-free part of the forward
+ * conditional HJB at x = 0, z = b.  Output layout as lqt_build_elements, T
+ * entries; workspace lqt_workspace_size(p, LQT_WS_BUILD).
+ *
+ * lqt_trajectory_method2: from those T elements and the values S, v (device,
+ * [T+1], e.g. from lqt_solve), the prefixes V(., t_0; ., t_k) =
+ * a_0 (x) ... (x) a_{k-1} by a parallel prefix scan with the combination of
+ * Sec. IV-A (eq. lqt_comb), and then
+ *   x_k = (I + C_k S_k)^-1 (A_k x0 + b_k + C_k v_k),  k = 0..T,
+ * with (A_k, b_k, C_k) the prefix's parameters, and u_k by eq.
+ * LQT_optimal_control.  x [T+1][n], u [T+1][m] (u may be NULL).  Workspace
+ * lqt_workspace_size(p, LQT_WS_METHOD2).
+ *
+ * lqt_solve_method2: the whole path of the paper's Method 2 variant: values by
+ * the backward-ODE elements and the suffix scan (as lqt_solve), states by the
+ * forward-ODE elements, the prefix scan and the formula above; outputs and
+ * cost as lqt_solve.  Workspace lqt_workspace_size(p, LQT_WS_SOLVE_METHOD2). */
+lqt_status lqt_build_elements_forward(const lqt_problem *p, const lqt_elements *out, void *ws, size_t ws_bytes,
+                                      void *stream);
+lqt_status lqt_trajectory_method2(const lqt_problem *p, const lqt_elements *fwd, const double *S, const double *v,
+                                  const double *x0, double *x, double *u, void *ws, size_t ws_bytes, void *stream);
+lqt_status lqt_solve_method2(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
+                             double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
 
 /* Within-block densification: the optimal solution at every RK4 sub-step
  * t_j + i h_j (h_j = (t_{j+1} - t_j)/K, i = 0..K-1) of every sub-interval and at

@@ -19,13 +19,14 @@ import torch
 
 from . import _abi
 from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, LQT_WS_BUILD, LQT_WS_DENSIFY,
-                   LQT_WS_SEQUENTIAL, LQT_WS_SOLVE, LQT_WS_TRAJ, LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements,
-                   lqt_problem)
+                   LQT_WS_METHOD2, LQT_WS_SEQUENTIAL, LQT_WS_SOLVE, LQT_WS_SOLVE_METHOD2, LQT_WS_TRAJ,
+                   LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
     "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_densify", "lqt_solve", "lqt_solve_mixed",
-    "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size",
+    "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size", "lqt_build_elements_forward",
+    "lqt_trajectory_method2", "lqt_solve_method2",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
 ]
 
@@ -141,6 +142,44 @@ def lqt_build_elements(dp: DeviceProblem, out: Optional[dict] = None, ws=None, s
     es = _elements_struct(out)
     _abi.check(_abi.lib().lqt_build_elements(dp.ref(), ct.byref(es), ws.data_ptr(), ws.numel(),
                                              _stream_handle(stream)), "lqt_build_elements")
+    return out
+
+
+def lqt_build_elements_forward(dp: DeviceProblem, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    """The T forward-ODE elements (Sec. IV-C), arrays of T entries."""
+    n, T = dp.n, dp.T
+    out = out or {"A": _empty(dp, T, n, n), "b": _empty(dp, T, n), "C": _empty(dp, T, n, n),
+                  "eta": _empty(dp, T, n), "J": _empty(dp, T, n, n), "zeta": _empty(dp, T)}
+    ws = _workspace(dp, LQT_WS_BUILD, ws)
+    es = _elements_struct(out)
+    _abi.check(_abi.lib().lqt_build_elements_forward(dp.ref(), ct.byref(es), ws.data_ptr(), ws.numel(),
+                                                     _stream_handle(stream)), "lqt_build_elements_forward")
+    return out
+
+
+def lqt_trajectory_method2(dp: DeviceProblem, fwd: dict, sol: dict, x0=None, out: Optional[dict] = None, ws=None,
+                           stream=None) -> dict:
+    """States and controls by Method 2 from forward-ODE elements `fwd` and the
+    values sol["S"], sol["v"]."""
+    x0 = dp.x0 if x0 is None else x0
+    n, m, T1 = dp.n, dp.m, dp.T + 1
+    out = out or {"x": _empty(dp, T1, n), "u": _empty(dp, T1, m)}
+    ws = _workspace(dp, LQT_WS_METHOD2, ws)
+    es = _elements_struct(fwd)
+    _abi.check(_abi.lib().lqt_trajectory_method2(dp.ref(), ct.byref(es), _ptr(sol["S"]), _ptr(sol["v"]), _ptr(x0),
+                                                 _ptr(out["x"]), _ptr(out.get("u")), ws.data_ptr(), ws.numel(),
+                                                 _stream_handle(stream)), "lqt_trajectory_method2")
+    return out
+
+
+def lqt_solve_method2(dp: DeviceProblem, x0=None, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    """lqt_solve with the states by Method 2 (forward-ODE elements, prefix scan)."""
+    x0 = dp.x0 if x0 is None else x0
+    out = new_solution(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_SOLVE_METHOD2, ws)
+    _abi.check(_abi.lib().lqt_solve_method2(dp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]), _ptr(out.get("zeta")),
+                                            _ptr(out["x"]), _ptr(out.get("u")), _ptr(out.get("cost")), ws.data_ptr(),
+                                            ws.numel(), _stream_handle(stream)), "lqt_solve_method2")
     return out
 
 

@@ -186,6 +186,41 @@ __device__ __forceinline__ void store_full(double* __restrict__ p, const Elem<N>
 }
 
 template <int N>
+__device__ __forceinline__ void load_full(const double* __restrict__ p, Elem<N>& e) {
+  const double* A = p;
+  const double* b = A + N * N;
+  const double* C = b + N;
+  const double* eta = C + N * N;
+  const double* J = eta + N;
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) e.A[i] = A[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    e.b[i] = b[i];
+    e.eta[i] = eta[i];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      e.C[sidx<N>(i, j)] = C[i * N + j];
+      e.J[sidx<N>(i, j)] = J[i * N + j];
+    }
+  e.zeta = J[N * N];
+}
+
+template <int N>
+__device__ __forceinline__ void store_val_full(double* __restrict__ p, const Val<N>& v) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) p[i * N + j] = v.S[sidx<N>(i, j)];
+#pragma unroll
+  for (int i = 0; i < N; ++i) p[N * N + i] = v.v[i];
+  p[N * N + N] = v.zeta;
+}
+
+template <int N>
 __device__ __forceinline__ void load_val_full(const double* __restrict__ p, Val<N>& v) {
 #pragma unroll
   for (int i = 0; i < N; ++i)
@@ -528,6 +563,106 @@ __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V,
       out.S[sidx<N>(i, j)] = (double)s;
     }
   out.zeta = (double)zeta;
+}
+
+// ---------------------------------------------------------------------------
+// prefix form of the combination (Method 2, Sec. IV-E)
+// ---------------------------------------------------------------------------
+
+// The (A, b, C) part of a prefix V(., t_0; ., t_k): only these enter the
+// Method 2 states, and only these of a left operand enter the (A, b, C) of a
+// combination.
+template <int N>
+struct Prefix {
+  double A[N * N];
+  double b[N];
+  double C[Dim<N>::NS];
+};
+
+template <int N>
+__device__ __forceinline__ void identity_prefix(Prefix<N>& P) {
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) P.A[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) P.b[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < Dim<N>::NS; ++i) P.C[i] = 0.0;
+}
+
+// The (A, b, C) part of a full-matrix record (full_elem_doubles layout).
+template <int N>
+__device__ __forceinline__ void load_prefix_full(const double* __restrict__ p, Prefix<N>& P) {
+  const double* A = p;
+  const double* b = A + N * N;
+  const double* C = b + N;
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) P.A[i] = A[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) P.b[i] = b[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) P.C[sidx<N>(i, j)] = C[i * N + j];
+}
+
+// P <- P (x) e, (A, b, C) part only (Lemma LQT_combination with the prefix as
+// the left operand): W = I + C_P J_e, [K | MC | z0] = W^-1 [A_P | C_P |
+// b_P + C_P eta_e]; A = A_e K, b = A_e z0 + b_e, C = A_e MC A_e^T + C_e.
+template <int N>
+__device__ __forceinline__ void combine_prefix(Prefix<N>& P, const Elem<N>& e) {
+  constexpr int Q = 2 * N + 1;
+  double W[N * N];
+  double R[N * Q];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(P.C[sidx<N>(i, l)], e.J[sidx<N>(l, j)], s);
+      W[i * N + j] = s;
+      R[i * Q + j] = P.A[i * N + j];
+      R[i * Q + N + j] = P.C[sidx<N>(i, j)];
+    }
+    double s = P.b[i];
+#pragma unroll
+    for (int l = 0; l < N; ++l) s = fma(P.C[sidx<N>(i, l)], e.eta[l], s);
+    R[i * Q + 2 * N] = s;
+  }
+  lu_solve<N, Q>(W, R);
+  double T1[N * N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = e.b[i];
+#pragma unroll
+    for (int l = 0; l < N; ++l) s = fma(e.A[i * N + l], R[l * Q + 2 * N], s);
+    P.b[i] = s;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double t = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) t = fma(e.A[i * N + l], R[l * Q + N + j], t);
+      T1[i * N + j] = t;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      double s = e.C[sidx<N>(i, j)];
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(T1[i * N + l], e.A[j * N + l], s);
+      P.C[sidx<N>(i, j)] = s;
+    }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(e.A[i * N + l], R[l * Q + j], s);
+      P.A[i * N + j] = s;
+    }
 }
 
 }  // namespace lqt

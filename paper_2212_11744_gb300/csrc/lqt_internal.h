@@ -137,6 +137,18 @@ template <int N>
 void team_maps_down(const double* maps, int64_t cnt, int G, const double* above, const double* x_in, double* starts,
                     cudaStream_t st);
 
+template <int N>
+void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, double* pre, cudaStream_t st);
+
+// Method 2 (lqt_forward.cu, lqt_scan.cu): forward-ODE elements, prefix scan
+// and the optimal states from the prefixes and the values.
+cudaError_t launch_build_forward(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                                 cudaStream_t st);
+size_t prefix_workspace_bytes(int n, int64_t T);
+cudaError_t run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
+                        const double* v, const double* zeta, const double* x0, double* x, double* u, double* cost,
+                        char* ws, cudaStream_t st);
+
 bool densify_supported(const lqt_problem& p);
 cudaError_t launch_densify(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* S, const double* v,
                            const double* zeta, const double* x, double* Sd, double* vd, double* zd, double* xd,

@@ -53,6 +53,12 @@ struct SrcPublic {
   ElemPtrs el;
   __device__ __forceinline__ void load(int64_t k, Elem<N>& e) const { load_public<N>(el, k, e); }
 };
+// full-matrix records of the upper levels (full_elem_doubles layout)
+template <int N>
+struct SrcFull {
+  const double* p;
+  __device__ __forceinline__ void load(int64_t k, Elem<N>& e) const { load_full<N>(p + k * full_elem_doubles<N>(), e); }
+};
 
 // ---------------------------------------------------------------------------
 // value scan kernels
@@ -164,6 +170,32 @@ __global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, 
     for (int i = 0; i < N * N; ++i) cp[i] = P[i];
 #pragma unroll
     for (int i = 0; i < N; ++i) cp[N * N + i] = pv[i];
+  }
+}
+
+// Upper-level down-sweep, one thread per group: suffix values of the group's
+// records (full layout) from the carry of the level above, written in the
+// full value layout.
+template <int N, typename GT = double>
+__global__ void __launch_bounds__(128) down_vals_upper_kernel(SrcFull<N> src, int64_t cnt, int G,
+                                                              const double* __restrict__ above, int64_t cnt_above,
+                                                              double* __restrict__ vals) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * G;
+  if (first >= cnt) return;
+  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+  Val<N> carry, nv;
+  if (above != nullptr && g + 1 < cnt_above)
+    load_val_full<N>(above + (g + 1) * full_val_doubles<N>(), carry);
+  else
+    zero_val<N>(carry);
+  Elem<N> e;
+  double Psi[N * N], alpha[N];
+  for (int64_t k = last; k >= first; --k) {
+    src.load(k, e);
+    combine_value<N, GT>(e, carry, nv, Psi, alpha);
+    store_val_full<N>(vals + k * full_val_doubles<N>(), nv);
+    carry = nv;
   }
 }
 
@@ -457,11 +489,15 @@ static ScanPlan make_plan(int64_t T, bool with_traj) {
   return pl;
 }
 
+// Upper levels with fewer pairs than this run one warp per combination (the
+// level is then latency-bound: a warp spreads one combination's products
+// over its lanes, shortening the dependent FP64 chain); larger levels run one
+// thread per pair (throughput-bound: a thread-per-pair warp instruction
+// serves 32 combinations).  Both read and write the same full-matrix records.
+constexpr int64_t kTeamLevelBelow = 2048;
+
 // Level 0 (chunks of G0 elements, one thread each, register-resident) and the
-// pairwise upper levels (one warp per combination: at these levels there are
-// too few combinations to fill the GPU, so the time is the length of one
-// combination's FP64 chain, which the warp shortens by spreading every
-// product over its lanes).
+// pairwise upper levels.
 template <int N, typename GT = double>
 static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& out0, char* ws, cudaStream_t st) {
   const int64_t T = pl.T;
@@ -473,8 +509,12 @@ static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& ou
     if (l == 0) {
       reduce_elems_kernel<N, SrcPublic<N>, GT><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, pl.G0, agg);
       count_launch();
-    } else {
+    } else if (pl.cnt[l] < kTeamLevelBelow) {
       team_upper_reduce<N, GT>((const double*)(ws + pl.off_agg[l - 1]), c, agg, st);
+    } else {
+      SrcFull<N> sf{(const double*)(ws + pl.off_agg[l - 1])};
+      reduce_elems_kernel<N, SrcFull<N>, GT><<<blocks_for(pl.cnt[l]), 128, 0, st>>>(sf, c, kUpperGroup, agg);
+      count_launch();
     }
     c = pl.cnt[l];
   }
@@ -482,8 +522,16 @@ static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& ou
   for (int l = pl.nlev; l >= 1; --l) {
     const double* above = (l < pl.nlev) ? (const double*)(ws + pl.off_val[l]) : nullptr;
     const int64_t cabove = (l < pl.nlev) ? pl.cnt[l] : 0;
-    team_upper_down<N, GT>((const double*)(ws + pl.off_agg[l - 1]), pl.cnt[l - 1], above, cabove,
-                           (double*)(ws + pl.off_val[l - 1]), st);
+    const int64_t cl = pl.cnt[l - 1];
+    const int64_t groups = ceil_div(cl, kUpperGroup);
+    double* vals = (double*)(ws + pl.off_val[l - 1]);
+    if (groups < kTeamLevelBelow) {
+      team_upper_down<N, GT>((const double*)(ws + pl.off_agg[l - 1]), cl, above, cabove, vals, st);
+    } else {
+      SrcFull<N> sf{(const double*)(ws + pl.off_agg[l - 1])};
+      down_vals_upper_kernel<N, GT><<<blocks_for(groups), 128, 0, st>>>(sf, cl, kUpperGroup, above, cabove, vals);
+      count_launch();
+    }
   }
   const double* above = pl.nlev > 0 ? (const double*)(ws + pl.off_val[0]) : nullptr;
   const int64_t cabove = pl.nlev > 0 ? pl.cnt[0] : 0;
@@ -497,17 +545,32 @@ static void traj_scan(const ScanPlan& pl, const double* x0, const double* S, con
                       const Coefs& cf, int32_t m, double* x, double* u, double* cost, char* ws, cudaStream_t st) {
   const int64_t T = pl.T;
   const double* maps0 = (const double*)(ws + pl.off_maps);
-  // reduce the chunk composites up the trajectory levels (one warp per
-  // composition, as for the value levels)
-  for (int l = 1; l < pl.tlev; ++l)
-    team_maps_reduce<N>((const double*)(ws + pl.off_tmap[l - 1]), pl.tcnt[l - 1], kUpperGroup,
-                        (double*)(ws + pl.off_tmap[l]), st);
+  // reduce the chunk composites up the trajectory levels (thread or warp per
+  // composition by level size, as for the value levels)
+  for (int l = 1; l < pl.tlev; ++l) {
+    if (pl.tcnt[l] < kTeamLevelBelow) {
+      team_maps_reduce<N>((const double*)(ws + pl.off_tmap[l - 1]), pl.tcnt[l - 1], kUpperGroup,
+                          (double*)(ws + pl.off_tmap[l]), st);
+    } else {
+      reduce_maps_kernel<N><<<blocks_for(pl.tcnt[l]), 128, 0, st>>>((const double*)(ws + pl.off_tmap[l - 1]),
+                                                                      pl.tcnt[l - 1], kUpperGroup,
+                                                                      (double*)(ws + pl.off_tmap[l]));
+      count_launch();
+    }
+  }
   // starts down the levels
   for (int l = pl.tlev - 1; l >= 0; --l) {
     const double* above = (l + 1 < pl.tlev) ? (const double*)(ws + pl.off_tstart[l + 1]) : nullptr;
     const int G = (l + 1 < pl.tlev) ? kUpperGroup : (int)pl.tcnt[l];
-    team_maps_down<N>((const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G, above, x0,
-                      (double*)(ws + pl.off_tstart[l]), st);
+    const int64_t groups = ceil_div(pl.tcnt[l], G);
+    if (groups < kTeamLevelBelow) {
+      team_maps_down<N>((const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G, above, x0,
+                        (double*)(ws + pl.off_tstart[l]), st);
+    } else {
+      down_maps_kernel<N><<<blocks_for(groups), 128, 0, st>>>((const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G,
+                                                             above, x0, (double*)(ws + pl.off_tstart[l]));
+      count_launch();
+    }
   }
   const double* starts1 = pl.tlev > 0 ? (const double*)(ws + pl.off_tstart[0]) : nullptr;
   final_traj_kernel<N><<<blocks_for(ceil_div(T + 1, pl.G0)), 128, 0, st>>>(
@@ -691,6 +754,248 @@ cudaError_t launch_maps_from_values(const lqt_problem& p, const ElemPtrs& el, co
   }
   count_launch();
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Method 2 (Sec. IV-E, eq. Opt_trajectory_method2): prefix scan of the
+// forward-ODE elements and the optimal states from the prefixes
+// ---------------------------------------------------------------------------
+
+// Levels of the prefix scan over T elements: chunk aggregates at level 0,
+// pairs above; per level the aggregates and their exclusive prefixes (full
+// records).
+struct PrefixPlan {
+  int G0;
+  int64_t T;
+  int nlev;
+  int64_t cnt[64];
+  size_t off_agg[64], off_pre[64];
+  size_t bytes;
+};
+
+template <int N>
+static PrefixPlan make_prefix_plan(int64_t T) {
+  PrefixPlan pl{};
+  pl.G0 = level0_group(T);
+  pl.T = T;
+  const size_t PE = sizeof(double) * full_elem_doubles<N>();
+  size_t off = 0;
+  int64_t c = T;
+  int G = pl.G0;
+  while (c > G) {
+    const int64_t nc = ceil_div(c, G);
+    pl.cnt[pl.nlev] = nc;
+    pl.off_agg[pl.nlev] = off;
+    off = align_up(off + nc * PE);
+    pl.off_pre[pl.nlev] = off;
+    off = align_up(off + nc * PE);
+    ++pl.nlev;
+    c = nc;
+    G = kUpperGroup;
+  }
+  pl.bytes = align_up(off);
+  return pl;
+}
+
+// Exclusive prefixes of the level-l aggregates, one thread per pair (the
+// large levels; the small ones run one warp per pair in lqt_team.cu):
+// pre[2g] = pre_up[g], pre[2g+1] = pre_up[g] (x) agg[2g].
+template <int N>
+__global__ void __launch_bounds__(128) prefix_down_kernel(const double* __restrict__ agg, int64_t cnt,
+                                                          const double* __restrict__ pre_up,
+                                                          double* __restrict__ pre) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * g >= cnt) return;
+  constexpr int FE = full_elem_doubles<N>();
+  Elem<N> left, e;
+  if (pre_up) {
+    load_full<N>(pre_up + g * FE, left);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) left.A[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      left.b[i] = 0.0;
+      left.eta[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < Dim<N>::NS; ++i) {
+      left.C[i] = 0.0;
+      left.J[i] = 0.0;
+    }
+    left.zeta = 0.0;
+  }
+  store_full<N>(pre + 2 * g * FE, left);
+  if (2 * g + 1 < cnt) {
+    load_full<N>(agg + 2 * g * FE, e);
+    combine<N>(left, e, e);
+    store_full<N>(pre + (2 * g + 1) * FE, e);
+  }
+}
+
+struct Method2Args {
+  ElemPtrs el;  // forward-ODE elements, T of them
+  int64_t T;
+  int G;
+  const double* pre0;  // exclusive prefixes of the level-0 chunks (full records), or null (one chunk)
+  const double *S, *v, *zeta, *x0;
+  const double* Ku;
+  int32_t Ku_per_boundary, m;
+  double *x, *u, *cost;
+};
+
+// x_k = (I + C S_k)^-1 (A x0 + b + C v_k) for the prefix (A, b, C) = V(., t_0;
+// ., t_k), then u_k = U^-1 L^T (v_k - S_k x_k).  Returns false if x_k is not finite.
+template <int N>
+__device__ __forceinline__ bool method2_state(const Method2Args& a, int64_t k, const Prefix<N>& P) {
+  const double* Sk = a.S + k * N * N;
+  const double* vk = a.v + k * N;
+  double W[N * N], r[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = P.b[i];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      s = fma(P.A[i * N + l], a.x0[l], s);
+      s = fma(P.C[sidx<N>(i, l)], vk[l], s);
+    }
+    r[i] = s;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double w = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) w = fma(P.C[sidx<N>(i, l)], Sk[l * N + j], w);
+      W[i * N + j] = w;
+    }
+  }
+  lu_solve<N, 1>(W, r);
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    a.x[k * N + i] = r[i];
+    ok = ok && isfinite(r[i]);
+  }
+  if (a.u) {
+    double e[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = vk[i];
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(-Sk[i * N + l], r[l], s);
+      e[i] = s;
+    }
+    const double* Kk = a.Ku + (a.Ku_per_boundary ? k * a.m * N : 0);
+    for (int q = 0; q < a.m; ++q) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(Kk[q * N + l], e[l], s);
+      a.u[k * a.m + q] = s;
+    }
+  }
+  return ok;
+}
+
+// One thread per level-0 chunk: fold the chunk's elements left to right onto
+// the prefix before the chunk, emitting the state at every boundary.
+template <int N>
+__global__ void __launch_bounds__(128) method2_kernel(Method2Args a) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = g * a.G;
+  if (first >= a.T) return;
+  const int64_t last = (first + a.G < a.T ? first + a.G : a.T) - 1;
+  Prefix<N> P;
+  if (a.pre0)
+    load_prefix_full<N>(a.pre0 + g * full_elem_doubles<N>(), P);
+  else
+    identity_prefix<N>(P);
+  SrcPublic<N> src{a.el};
+  Elem<N> e;
+  bool ok = true;
+  for (int64_t k = first; k <= last; ++k) {
+    ok = method2_state<N>(a, k, P) && ok;
+    src.load(k, e);
+    combine_prefix<N>(P, e);
+  }
+  if (last == a.T - 1) ok = method2_state<N>(a, a.T, P) && ok;
+  if (!ok) flag(kStatusNonFinite);
+  if (g == 0 && a.cost != nullptr) {
+    double c = a.zeta ? a.zeta[0] : 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(a.S[i * N + l], a.x0[l], s);
+      c = fma(a.x0[i], fma(0.5, s, -a.v[i]), c);
+    }
+    *a.cost = c;
+  }
+}
+
+template <int N>
+static cudaError_t method2_n(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
+                             const double* v, const double* zeta, const double* x0, double* x, double* u,
+                             double* cost, char* ws, cudaStream_t st) {
+  const PrefixPlan pl = make_prefix_plan<N>(p.T);
+  SrcPublic<N> s0{fwd};
+  int64_t c = p.T;
+  for (int l = 0; l < pl.nlev; ++l) {
+    double* agg = (double*)(ws + pl.off_agg[l]);
+    if (l == 0) {
+      reduce_elems_kernel<N, SrcPublic<N>, double><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, pl.G0, agg);
+      count_launch();
+    } else if (pl.cnt[l] < kTeamLevelBelow) {
+      team_upper_reduce<N, double>((const double*)(ws + pl.off_agg[l - 1]), c, agg, st);
+    } else {
+      SrcFull<N> sf{(const double*)(ws + pl.off_agg[l - 1])};
+      reduce_elems_kernel<N, SrcFull<N>, double><<<blocks_for(pl.cnt[l]), 128, 0, st>>>(sf, c, kUpperGroup, agg);
+      count_launch();
+    }
+    c = pl.cnt[l];
+  }
+  for (int l = pl.nlev - 1; l >= 0; --l) {
+    const double* up = l + 1 < pl.nlev ? (const double*)(ws + pl.off_pre[l + 1]) : nullptr;
+    const int64_t pairs = ceil_div(pl.cnt[l], 2);
+    if (pairs < kTeamLevelBelow) {
+      team_prefix_down<N>((const double*)(ws + pl.off_agg[l]), pl.cnt[l], up, (double*)(ws + pl.off_pre[l]), st);
+    } else {
+      prefix_down_kernel<N><<<blocks_for(pairs), 128, 0, st>>>((const double*)(ws + pl.off_agg[l]), pl.cnt[l], up,
+                                                               (double*)(ws + pl.off_pre[l]));
+      count_launch();
+    }
+  }
+  Method2Args a{};
+  a.el = fwd; a.T = p.T; a.G = pl.G0;
+  a.pre0 = pl.nlev > 0 ? (const double*)(ws + pl.off_pre[0]) : nullptr;
+  a.S = S; a.v = v; a.zeta = zeta; a.x0 = x0;
+  a.Ku = cf.Ku; a.Ku_per_boundary = cf.Ku_per_boundary; a.m = p.m;
+  a.x = x; a.u = u; a.cost = cost;
+  method2_kernel<N><<<blocks_for(ceil_div(p.T, pl.G0)), 128, 0, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+size_t prefix_workspace_bytes(int n, int64_t T) {
+  switch (n) {
+    case 1: return make_prefix_plan<1>(T).bytes;
+    case 2: return make_prefix_plan<2>(T).bytes;
+    case 3: return make_prefix_plan<3>(T).bytes;
+    case 4: return make_prefix_plan<4>(T).bytes;
+    case 8: return make_prefix_plan<8>(T).bytes;
+    default: return 0;
+  }
+}
+
+cudaError_t run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
+                        const double* v, const double* zeta, const double* x0, double* x, double* u, double* cost,
+                        char* ws, cudaStream_t st) {
+  switch (p.n) {
+    case 1: return method2_n<1>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    case 2: return method2_n<2>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    case 3: return method2_n<3>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    case 4: return method2_n<4>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    case 8: return method2_n<8>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 size_t scan_workspace_bytes(int32_t n, int64_t T, bool with_traj) {

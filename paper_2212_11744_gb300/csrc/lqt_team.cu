@@ -645,6 +645,48 @@ void team_maps_down(const double* maps, int64_t cnt, int G, const double* above,
   team_launch<N>(down_maps_team_kernel<N>, tdiv(cnt, G), maps_slot_doubles<N>(), a, st);
 }
 
+// Exclusive prefixes of the level-l aggregates of the Method 2 prefix scan:
+// pre[2g] = pre_up[g], pre[2g+1] = pre_up[g] (x) agg[2g] (pre_up = the level
+// above; at the top level, the identity element).  One warp per pair.
+struct TeamPrefixArgs {
+  const double* agg;     // level-l aggregates, full records
+  int64_t cnt;           // entries at level l
+  const double* pre_up;  // prefixes of level l+1 (full records), or null at the top
+  double* pre;           // out: prefixes of level l
+};
+
+template <int N>
+constexpr int prefix_slot_doubles() { return Rec<N>::SIZE + team::combine_scratch_doubles<N>() + 8; }
+
+template <int N>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) prefix_down_team_kernel(TeamPrefixArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  __shared__ double fs[TEAM];
+  __shared__ int is[TEAM];
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(nullptr, prefix_slot_doubles<N>());
+  double* ident = base;
+  double* scr = ident + Rec<N>::SIZE;
+  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) ident[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
+  team::sync<TEAM>();
+  const int64_t groups = tdiv(a.cnt, 2);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const Rec<N> left = a.pre_up ? Rec<N>::packed(const_cast<double*>(a.pre_up) + g * Rec<N>::SIZE)
+                                 : Rec<N>::packed(ident);
+    team::copy_rec<N, TEAM>(lane, Rec<N>::packed(a.pre + 2 * g * Rec<N>::SIZE), left);
+    if (2 * g + 1 < a.cnt)
+      team::combine<N, TEAM>(lane, left, Rec<N>::packed(const_cast<double*>(a.agg) + 2 * g * Rec<N>::SIZE),
+                             Rec<N>::packed(a.pre + (2 * g + 1) * Rec<N>::SIZE), scr, fs, is);
+    team::sync<TEAM>();
+  }
+}
+
+template <int N>
+void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, double* pre, cudaStream_t st) {
+  TeamPrefixArgs a{agg, cnt, pre_up, pre};
+  team_launch<N>(prefix_down_team_kernel<N>, tdiv(cnt, 2), prefix_slot_doubles<N>(), a, st);
+}
+
 #define LQT_TEAM_UPPER(N)                                                                                 \
   template void team_upper_reduce<N, double>(const double*, int64_t, double*, cudaStream_t);             \
   template void team_upper_reduce<N, float>(const double*, int64_t, double*, cudaStream_t);              \
@@ -654,7 +696,8 @@ void team_maps_down(const double* maps, int64_t cnt, int G, const double* above,
                                           cudaStream_t);                                                 \
   template void team_maps_reduce<N>(const double*, int64_t, int, double*, cudaStream_t);                 \
   template void team_maps_down<N>(const double*, int64_t, int, const double*, const double*, double*,    \
-                                  cudaStream_t);
+                                  cudaStream_t);                                                         \
+  template void team_prefix_down<N>(const double*, int64_t, const double*, double*, cudaStream_t);
 LQT_TEAM_UPPER(1)
 LQT_TEAM_UPPER(2)
 LQT_TEAM_UPPER(3)
