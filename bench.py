@@ -386,11 +386,24 @@ def measure_rows(T_headline):
                             "solution", "value": fine / ((sms + dms) * 1e-3), "unit": "sub-steps/s (solve + densify)",
                 "ms_densify": dms, "ms_solve": sms, "status": lqt.lqt_get_status()}
 
+    def method2():
+        p = W.point_mass_2d(T=T_headline, K=K_STEPS)
+        dp = lqt.DeviceProblem(p)
+        ws = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_SOLVE_METHOD2), dtype=torch.uint8, device="cuda")
+        m2 = lqt.lqt_solve_method2(dp, ws=ws)
+        m1 = lqt.lqt_solve(dp)
+        ms = _events_ms(lambda: lqt.lqt_solve_method2(dp, out=m2, ws=ws), 3)
+        return {"workload": "point mass T=2^20, K=4: values by the suffix scan, states by Method 2 (forward-ODE "
+                            "elements, prefix scan)", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                "rel_diff_vs_method1": {k: _relmax(m2[k], m1[k]) for k in ("x", "u")},
+                "status": lqt.lqt_get_status()}
+
     guard("a4_batched", batched)
     guard("a5_mixed", mixed)
     guard("a6_adjoint", adjoint)
     guard("double_integrator_T1024", small)
     guard("next1_densify", densify)
+    guard("next2_method2", method2)
     return rows
 
 

@@ -494,7 +494,12 @@ static ScanPlan make_plan(int64_t T, bool with_traj) {
 // over its lanes, shortening the dependent FP64 chain); larger levels run one
 // thread per pair (throughput-bound: a thread-per-pair warp instruction
 // serves 32 combinations).  Both read and write the same full-matrix records.
-constexpr int64_t kTeamLevelBelow = 2048;
+// For n <= 3 a thread's combination is already short, and the warp version
+// is not faster at any level size.
+template <int N>
+constexpr int64_t team_level_below() {
+  return N >= 4 ? 2048 : 0;
+}
 
 // Level 0 (chunks of G0 elements, one thread each, register-resident) and the
 // pairwise upper levels.
@@ -509,7 +514,7 @@ static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& ou
     if (l == 0) {
       reduce_elems_kernel<N, SrcPublic<N>, GT><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, pl.G0, agg);
       count_launch();
-    } else if (pl.cnt[l] < kTeamLevelBelow) {
+    } else if (pl.cnt[l] < team_level_below<N>()) {
       team_upper_reduce<N, GT>((const double*)(ws + pl.off_agg[l - 1]), c, agg, st);
     } else {
       SrcFull<N> sf{(const double*)(ws + pl.off_agg[l - 1])};
@@ -525,7 +530,7 @@ static void value_scan(const ScanPlan& pl, const ElemPtrs& el, const DownOut& ou
     const int64_t cl = pl.cnt[l - 1];
     const int64_t groups = ceil_div(cl, kUpperGroup);
     double* vals = (double*)(ws + pl.off_val[l - 1]);
-    if (groups < kTeamLevelBelow) {
+    if (groups < team_level_below<N>()) {
       team_upper_down<N, GT>((const double*)(ws + pl.off_agg[l - 1]), cl, above, cabove, vals, st);
     } else {
       SrcFull<N> sf{(const double*)(ws + pl.off_agg[l - 1])};
@@ -548,7 +553,7 @@ static void traj_scan(const ScanPlan& pl, const double* x0, const double* S, con
   // reduce the chunk composites up the trajectory levels (thread or warp per
   // composition by level size, as for the value levels)
   for (int l = 1; l < pl.tlev; ++l) {
-    if (pl.tcnt[l] < kTeamLevelBelow) {
+    if (pl.tcnt[l] < team_level_below<N>()) {
       team_maps_reduce<N>((const double*)(ws + pl.off_tmap[l - 1]), pl.tcnt[l - 1], kUpperGroup,
                           (double*)(ws + pl.off_tmap[l]), st);
     } else {
@@ -563,7 +568,7 @@ static void traj_scan(const ScanPlan& pl, const double* x0, const double* S, con
     const double* above = (l + 1 < pl.tlev) ? (const double*)(ws + pl.off_tstart[l + 1]) : nullptr;
     const int G = (l + 1 < pl.tlev) ? kUpperGroup : (int)pl.tcnt[l];
     const int64_t groups = ceil_div(pl.tcnt[l], G);
-    if (groups < kTeamLevelBelow) {
+    if (groups < team_level_below<N>()) {
       team_maps_down<N>((const double*)(ws + pl.off_tmap[l]), pl.tcnt[l], G, above, x0,
                         (double*)(ws + pl.off_tstart[l]), st);
     } else {
@@ -943,7 +948,7 @@ static cudaError_t method2_n(const lqt_problem& p, const Coefs& cf, const ElemPt
     if (l == 0) {
       reduce_elems_kernel<N, SrcPublic<N>, double><<<blocks_for(pl.cnt[0]), 128, 0, st>>>(s0, c, pl.G0, agg);
       count_launch();
-    } else if (pl.cnt[l] < kTeamLevelBelow) {
+    } else if (pl.cnt[l] < team_level_below<N>()) {
       team_upper_reduce<N, double>((const double*)(ws + pl.off_agg[l - 1]), c, agg, st);
     } else {
       SrcFull<N> sf{(const double*)(ws + pl.off_agg[l - 1])};
@@ -955,7 +960,7 @@ static cudaError_t method2_n(const lqt_problem& p, const Coefs& cf, const ElemPt
   for (int l = pl.nlev - 1; l >= 0; --l) {
     const double* up = l + 1 < pl.nlev ? (const double*)(ws + pl.off_pre[l + 1]) : nullptr;
     const int64_t pairs = ceil_div(pl.cnt[l], 2);
-    if (pairs < kTeamLevelBelow) {
+    if (pairs < team_level_below<N>()) {
       team_prefix_down<N>((const double*)(ws + pl.off_agg[l]), pl.cnt[l], up, (double*)(ws + pl.off_pre[l]), st);
     } else {
       prefix_down_kernel<N><<<blocks_for(pairs), 128, 0, st>>>((const double*)(ws + pl.off_agg[l]), pl.cnt[l], up,
