@@ -398,12 +398,55 @@ def measure_rows(T_headline):
                 "rel_diff_vs_method1": {k: _relmax(m2[k], m1[k]) for k in ("x", "u")},
                 "status": lqt.lqt_get_status()}
 
+    def invariant():
+        """The 4096-problem batch and the n = 64 problem with the time-invariant
+        element build (every problem there has constant F, L, U, X and a uniform
+        grid)."""
+        from paper_2212_11744_gb300.batch import Batch
+        probs = [W.batched_member(b) for b in range(4096)]
+        byn = {}
+        for p in probs:
+            byn.setdefault(p.n, []).append(p)
+        bts = {n: Batch(v) for n, v in sorted(byn.items())}
+        for bt in bts.values():
+            bt.set_invariant_build(True)
+        chunks = {n: bt.autotune(candidates=(0, 8, 32), reps=1) for n, bt in bts.items()}
+        outs = {n: bt.new_outputs() for n, bt in bts.items()}
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for n, bt in bts.items():
+                bt.solve(out=outs[n], stream=s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                for n, bt in bts.items():
+                    bt.solve(out=outs[n], stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        ms = _events_ms(g.replay, 2)
+        per = {str(n): _events_ms(lambda bt=bt, o=outs[n]: bt.solve(out=o), 1) for n, bt in bts.items()}
+        total = int(sum(p.T for p in probs))
+        res = {"workload": "the 4096-problem batch (as a4) with the time-invariant element build",
+               "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "per_n_ms": per,
+               "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": lqt.lqt_get_status()}
+        del bts, outs, g
+        p = W.large_state_n64(T=1 << 16)
+        dp = lqt.DeviceProblem(p)
+        try:
+            o = lqt.lqt_solve_invariant(dp)
+            res["large_state_n64_T2^16_ms"] = _events_ms(lambda: lqt.lqt_solve_invariant(dp, out=o), 1)
+        except lqt.LQTError as exc:
+            res["large_state_n64_T2^16"] = str(exc)
+        return res
+
     guard("a4_batched", batched)
     guard("a5_mixed", mixed)
     guard("a6_adjoint", adjoint)
     guard("double_integrator_T1024", small)
     guard("next1_densify", densify)
     guard("next2_method2", method2)
+    guard("next3_invariant", invariant)
     return rows
 
 

@@ -111,7 +111,9 @@ enum {
   LQT_WS_BACKWARD = 5,
   LQT_WS_DENSIFY = 6,
   LQT_WS_METHOD2 = 7,
-  LQT_WS_SOLVE_METHOD2 = 8
+  LQT_WS_SOLVE_METHOD2 = 8,
+  LQT_WS_INVARIANT = 9,
+  LQT_WS_SOLVE_INVARIANT = 10
 };
 
 /* Bytes of device workspace the call `which` needs for problem p (host call,
@@ -172,6 +174,28 @@ lqt_status lqt_solve_mixed(const lqt_problem *p, const double *x0, double *S, do
  * interpolant of the backward solution.  Same outputs as lqt_solve. */
 lqt_status lqt_solve_sequential(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta,
                                 double *x, double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
+
+/* Time-invariant specialisation of the element build (row a1 for problems
+ * with F, L, U, X constant and H constant or NULL; c and r may vary; n <= 8,
+ * or n = 16 with 5 <= m <= 8).
+ * With such coefficients and sub-intervals of one length h K, every
+ * sub-interval's RK4 of Theorem Backward_HJB_LQT (Sec. IV-B) gives the same
+ * A, C, J and passes through the same A, J at every RK4 stage (the paper's
+ * observation in Sec. VI-B that a time-invariant model has one conditional
+ * value function per block): one thread integrates A, C, J once and records the
+ * stage matrices; one thread per sub-interval then integrates only b, eta,
+ * zeta.  The elements equal lqt_build_elements' up to rounding.  The grid must
+ * be uniform: a sub-interval whose length differs from the first one's by
+ * more than 1e-12 relative sets the status word (lqt_get_status gives
+ * LQT_EINVAL).  Coefficients not constant, or other n, m: LQT_EUNSUPPORTED.
+ * lqt_build_elements_invariant: as lqt_build_elements (T+1 elements incl. the
+ * terminal one); workspace lqt_workspace_size(p, LQT_WS_INVARIANT).
+ * lqt_solve_invariant: as lqt_solve with this build; workspace
+ * lqt_workspace_size(p, LQT_WS_SOLVE_INVARIANT).  Asynchronous, allocation-free. */
+lqt_status lqt_build_elements_invariant(const lqt_problem *p, const lqt_elements *out, void *ws, size_t ws_bytes,
+                                        void *stream);
+lqt_status lqt_solve_invariant(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
+                               double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
 
 /* Method 2 of the optimal-trajectory recovery (Sec. IV-E, eq.
  * Opt_trajectory_method2) with elements from the forward conditional HJB ODEs
@@ -276,10 +300,16 @@ typedef struct {
 /* Tunables of the batched solve, chosen by the caller's autotuner.
  * chunk: sub-intervals per thread (per team for n >= 16) in the first scan
  * level, a power of two in [2, 32]; 0 = built-in choice; anything else gives
- * LQT_EINVAL.  lqt_batch_workspace_size() covers every allowed value. */
+ * LQT_EINVAL.  lqt_batch_workspace_size() covers every allowed value.
+ * flags: LQT_TUNE_INVARIANT_BUILD selects the time-invariant element build
+ * (see lqt_build_elements_invariant): every problem of a batch already has
+ * constant F, L, U, X; each must also have sub-intervals of one length (else
+ * the status word reports LQT_EINVAL); n <= 8, or n = 16 with 5 <= m <= 8
+ * (else LQT_EUNSUPPORTED).  Other bits: LQT_EINVAL. */
+enum { LQT_TUNE_INVARIANT_BUILD = 1 };
 typedef struct {
   int32_t chunk;
-  int32_t reserved;
+  int32_t flags;
 } lqt_tuning;
 
 size_t lqt_batch_workspace_size(const lqt_batch *b);

@@ -19,14 +19,15 @@ import torch
 
 from . import _abi
 from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, LQT_WS_BUILD, LQT_WS_DENSIFY,
-                   LQT_WS_METHOD2, LQT_WS_SEQUENTIAL, LQT_WS_SOLVE, LQT_WS_SOLVE_METHOD2, LQT_WS_TRAJ,
+                   LQT_WS_INVARIANT, LQT_WS_METHOD2, LQT_WS_SEQUENTIAL, LQT_WS_SOLVE, LQT_WS_SOLVE_INVARIANT,
+                   LQT_WS_SOLVE_METHOD2, LQT_WS_TRAJ,
                    LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
     "lqt_scan_trajectory", "lqt_scan_value_noalloc", "lqt_densify", "lqt_solve", "lqt_solve_mixed",
     "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size", "lqt_build_elements_forward",
-    "lqt_trajectory_method2", "lqt_solve_method2",
+    "lqt_trajectory_method2", "lqt_solve_method2", "lqt_build_elements_invariant", "lqt_solve_invariant",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
 ]
 
@@ -154,6 +155,29 @@ def lqt_build_elements_forward(dp: DeviceProblem, out: Optional[dict] = None, ws
     es = _elements_struct(out)
     _abi.check(_abi.lib().lqt_build_elements_forward(dp.ref(), ct.byref(es), ws.data_ptr(), ws.numel(),
                                                      _stream_handle(stream)), "lqt_build_elements_forward")
+    return out
+
+
+def lqt_build_elements_invariant(dp: DeviceProblem, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    """The T+1 elements by the time-invariant build (constant F, L, U, X, H;
+    uniform grid)."""
+    out = new_elements(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_INVARIANT, ws)
+    es = _elements_struct(out)
+    _abi.check(_abi.lib().lqt_build_elements_invariant(dp.ref(), ct.byref(es), ws.data_ptr(), ws.numel(),
+                                                       _stream_handle(stream)), "lqt_build_elements_invariant")
+    return out
+
+
+def lqt_solve_invariant(dp: DeviceProblem, x0=None, out: Optional[dict] = None, ws=None, stream=None) -> dict:
+    """lqt_solve with the time-invariant element build."""
+    x0 = dp.x0 if x0 is None else x0
+    out = new_solution(dp) if out is None else out
+    ws = _workspace(dp, LQT_WS_SOLVE_INVARIANT, ws)
+    _abi.check(_abi.lib().lqt_solve_invariant(dp.ref(), _ptr(x0), _ptr(out["S"]), _ptr(out["v"]),
+                                              _ptr(out.get("zeta")), _ptr(out["x"]), _ptr(out.get("u")),
+                                              _ptr(out.get("cost")), ws.data_ptr(), ws.numel(),
+                                              _stream_handle(stream)), "lqt_solve_invariant")
     return out
 
 

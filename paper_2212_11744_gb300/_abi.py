@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblqt_gb300.so")
 LQT_OK, LQT_EINVAL, LQT_EWORKSPACE, LQT_ENONFINITE, LQT_ESINGULAR, LQT_ETIMEOUT, LQT_ECUDA, LQT_EUNSUPPORTED = range(8)
 LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE = 0, 1, 2
 (LQT_WS_BUILD, LQT_WS_VALUE, LQT_WS_TRAJ, LQT_WS_SOLVE, LQT_WS_SEQUENTIAL, LQT_WS_BACKWARD, LQT_WS_DENSIFY,
- LQT_WS_METHOD2, LQT_WS_SOLVE_METHOD2) = range(9)
+ LQT_WS_METHOD2, LQT_WS_SOLVE_METHOD2, LQT_WS_INVARIANT, LQT_WS_SOLVE_INVARIANT) = range(11)
+LQT_TUNE_INVARIANT_BUILD = 1
 LQT_STATIC_SCRATCH_BYTES = 16 << 20
 
 EXPORTED = (
@@ -23,7 +24,8 @@ EXPORTED = (
     "lqt_solve_sequential", "lqt_host_staging_size", "lqt_solve_host", "lqt_get_status", "lqt_strerror",
     "lqt_last_launch_count", "lqt_scan_value_noalloc", "lqt_backward", "lqt_batch_workspace_size",
     "lqt_batch_boundaries", "lqt_batch_plan", "lqt_solve_batched", "lqt_solve_mixed", "lqt_densify",
-    "lqt_build_elements_forward", "lqt_trajectory_method2", "lqt_solve_method2",
+    "lqt_build_elements_forward", "lqt_trajectory_method2", "lqt_solve_method2", "lqt_build_elements_invariant",
+    "lqt_solve_invariant",
 )
 
 _dp = ct.POINTER(ct.c_double)
@@ -54,7 +56,7 @@ class lqt_batch(ct.Structure):
 
 
 class lqt_tuning(ct.Structure):
-    _fields_ = [("chunk", ct.c_int32), ("reserved", ct.c_int32)]
+    _fields_ = [("chunk", ct.c_int32), ("flags", ct.c_int32)]
 
 
 class LQTError(RuntimeError):
@@ -88,6 +90,8 @@ def lib():
     L.lqt_build_elements_forward.argtypes = [P, ct.POINTER(lqt_elements), v, ct.c_size_t, v]
     L.lqt_trajectory_method2.argtypes = [P, ct.POINTER(lqt_elements), v, v, v, v, v, v, ct.c_size_t, v]
     L.lqt_solve_method2.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]
+    L.lqt_build_elements_invariant.argtypes = [P, ct.POINTER(lqt_elements), v, ct.c_size_t, v]
+    L.lqt_solve_invariant.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]
     L.lqt_solve_mixed.argtypes = [P, v, v, v, v, v, v, v, v, ct.c_size_t, v]
     L.lqt_solve_mixed.restype = ct.c_int
     L.lqt_host_staging_size.argtypes = [P]
@@ -113,6 +117,7 @@ def lib():
     L.lqt_last_launch_count.restype = ct.c_int32
     for f in ("lqt_build_elements", "lqt_scan_value", "lqt_scan_trajectory", "lqt_solve", "lqt_solve_sequential",
               "lqt_densify", "lqt_build_elements_forward", "lqt_trajectory_method2", "lqt_solve_method2",
+              "lqt_build_elements_invariant", "lqt_solve_invariant",
               "lqt_solve_host", "lqt_get_status"):
         getattr(L, f).restype = ct.c_int
     _lib = L

@@ -87,6 +87,12 @@ class Batch:
         _abi.check(L.lqt_batch_plan(ct.byref(self.struct), self.ws.data_ptr(), self.ws.numel(),
                                     torch.cuda.current_stream(self.device).cuda_stream), "lqt_batch_plan")
         self.chunk = 0
+        self.flags = 0
+
+    def set_invariant_build(self, on: bool = True):
+        """Use the time-invariant element build (every problem of a batch has
+        constant F, L, U, X; each needs sub-intervals of one length)."""
+        self.flags = _abi.LQT_TUNE_INVARIANT_BUILD if on else 0
 
     def new_outputs(self):
         n, m, N = self.n, self.m, self.total
@@ -95,7 +101,7 @@ class Batch:
 
     def solve(self, out=None, chunk=None, stream=None) -> dict:
         out = self.new_outputs() if out is None else out
-        tune = lqt_tuning(self.chunk if chunk is None else chunk, 0)
+        tune = lqt_tuning(self.chunk if chunk is None else chunk, self.flags)
         st = torch.cuda.current_stream(self.device) if stream is None else stream
         _abi.check(_abi.lib().lqt_solve_batched(
             ct.byref(self.struct), ct.byref(tune), out["S"].data_ptr(), out["v"].data_ptr(), out["zeta"].data_ptr(),
@@ -111,7 +117,7 @@ class Batch:
         """Times the batched solve for each first-level chunk length and keeps
         the fastest (cached per state dimension, problem count and total
         boundaries)."""
-        key = (self.n, self.B, self.total)
+        key = (self.n, self.B, self.total, self.flags)
         if key in _TUNED:
             self.chunk = _TUNED[key][0]
             return self.chunk

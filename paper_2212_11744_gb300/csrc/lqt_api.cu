@@ -120,6 +120,13 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
     case LQT_WS_BACKWARD: return backward_workspace_bytes(*p, L, element_bytes(*p)) + 4096;
     case LQT_WS_DENSIFY: return L.coef_bytes;
     case LQT_WS_METHOD2: return p->n > 8 ? 0 : L.coef_bytes + prefix_workspace_bytes(p->n, p->T);
+    case LQT_WS_INVARIANT:
+      return invariant_supported(p->n, L.M) ? L.coef_bytes + align_up(invariant_table_bytes(p->n, L.M, p->K)) : 0;
+    case LQT_WS_SOLVE_INVARIANT:
+      return invariant_supported(p->n, L.M)
+                 ? L.coef_bytes + element_bytes(*p) + align_up(T1 * 8) + team_build_scratch_bytes(p->n) +
+                       scan_workspace_bytes(p->n, p->T, true) + align_up(invariant_table_bytes(p->n, L.M, p->K))
+                 : 0;
     case LQT_WS_SOLVE_METHOD2:
       return p->n > 8 ? 0
                       : L.coef_bytes + 2 * element_bytes(*p) + align_up(T1 * 8) +
@@ -223,6 +230,57 @@ lqt_status lqt_solve_sequential(const lqt_problem* p, const double* x0, double* 
   Coefs cf;
   if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
   return from_cuda(launch_sequential(*p, L, cf, x0, S, v, zeta, x, u, cost, (char*)ws + L.coef_bytes, st));
+}
+
+static lqt_status validate_invariant(const lqt_problem* p) {
+  lqt_status s = validate(p);
+  if (s != LQT_OK) return s;
+  if (p->F.mode != LQT_CONST || p->L.mode != LQT_CONST || p->U.mode != LQT_CONST || p->X.mode != LQT_CONST ||
+      (p->H.ptr && p->H.mode != LQT_CONST))
+    return LQT_EUNSUPPORTED;
+  if (!invariant_supported(p->n, make_layout(*p).M)) return LQT_EUNSUPPORTED;
+  return LQT_OK;
+}
+
+lqt_status lqt_build_elements_invariant(const lqt_problem* p, const lqt_elements* out, void* ws, size_t ws_bytes,
+                                        void* stream) {
+  t_launches = 0;
+  lqt_status s = validate_invariant(p);
+  if (s != LQT_OK) return s;
+  if (!out || !out->A || !out->b || !out->C || !out->eta || !out->J) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_INVARIANT);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  Coefs cf;
+  if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
+  ElemPtrs el{out->A, out->b, out->C, out->eta, out->J, out->zeta};
+  return from_cuda(launch_build_invariant(*p, L, cf, el, (double*)((char*)ws + L.coef_bytes), st));
+}
+
+lqt_status lqt_solve_invariant(const lqt_problem* p, const double* x0, double* S, double* v, double* zeta, double* x,
+                               double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate_invariant(p);
+  if (s != LQT_OK) return s;
+  if (!x0 || !S || !v || !x) return LQT_EINVAL;
+  const size_t need = lqt_workspace_size(p, LQT_WS_SOLVE_INVARIANT);
+  if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(*p);
+  char* base = (char*)ws;
+  Coefs cf;
+  if (launch_prepare_coefs(*p, L, base, cf, st) != cudaSuccess) return LQT_ECUDA;
+  ElemPtrs el = carve_elements(*p, base + L.coef_bytes);
+  char* cur = base + L.coef_bytes + element_bytes(*p);
+  double* zbuf = (double*)cur;
+  double* zout = zeta ? zeta : zbuf;
+  cur += align_up(((size_t)p->T + 1) * 8) + team_build_scratch_bytes(p->n);
+  const size_t scan_bytes = scan_workspace_bytes(p->n, p->T, true);
+  double* table = (double*)(cur + scan_bytes);
+  if (launch_build_invariant(*p, L, cf, el, table, st) != cudaSuccess) return LQT_ECUDA;
+  return from_cuda(run_value_and_traj(*p, L, cf, el, S, v, zout, x0, x, u, cost, true, true, nullptr, nullptr, cur,
+                                      scan_bytes, st));
 }
 
 lqt_status lqt_build_elements_forward(const lqt_problem* p, const lqt_elements* out, void* ws, size_t ws_bytes,
@@ -440,6 +498,7 @@ lqt_status lqt_get_status(void* stream, int32_t timeout_ms) {
   if (cudaMemcpyToSymbol(g_status_word, &zero, sizeof(zero)) != cudaSuccess) return LQT_ECUDA;
   if (word & kStatusNonFinite) return LQT_ENONFINITE;
   if (word & kStatusSingular) return LQT_ESINGULAR;
+  if (word & kStatusNonUniform) return LQT_EINVAL;
   return LQT_OK;
 }
 

@@ -74,7 +74,7 @@ __global__ void controls_cost_kernel(BatchDev bd, const double* S, const double*
 struct BatchLayout {
   int32_t B, n, m, K, M;
   int64_t total, total_qr;
-  size_t off_probs, off_off, off_offqr, off_Lt, off_Ku, off_qr, off_el, off_team, off_zf, off_scan, bytes;
+  size_t off_probs, off_off, off_offqr, off_Lt, off_Ku, off_qr, off_el, off_team, off_zf, off_inv, off_scan, bytes;
 };
 
 static int32_t batch_factor_width(int n, int m) {
@@ -124,6 +124,9 @@ static lqt_status batch_validate(const lqt_batch* bt, BatchLayout& L) {
   off = bal(off + bal(T1 * n * n * 8) * 3 + bal(T1 * n * 8) * 2 + bal(T1 * 8));
   L.off_team = off; off = bal(off + team_build_scratch_bytes(n));
   L.off_zf = off; off = bal(off + (size_t)L.B * 8);
+  // per-problem tables of the time-invariant build (when it supports n)
+  L.off_inv = off;
+  if (invariant_supported(n, L.M)) off = bal(off + (size_t)L.B * invariant_table_bytes(n, L.M, L.K));
   // The scans may run with any first-level chunk the caller's tuning picks;
   // the shortest chunk (2) needs the most level storage, so size for it.
   const int prev = scan_chunk_override();
@@ -238,13 +241,19 @@ lqt_status lqt_solve_batched(const lqt_batch* bt, const lqt_tuning* tune, double
   if (!ws || ws_bytes < L.bytes) return LQT_EWORKSPACE;
   const int chunk = tune ? tune->chunk : 0;
   if (!(chunk == 0 || chunk == 2 || chunk == 4 || chunk == 8 || chunk == 16 || chunk == 32)) return LQT_EINVAL;
+  const int flags = tune ? tune->flags : 0;
+  if (flags & ~LQT_TUNE_INVARIANT_BUILD) return LQT_EINVAL;
+  const bool invariant = (flags & LQT_TUNE_INVARIANT_BUILD) != 0;
+  if (invariant && !invariant_supported(L.n, L.M)) return LQT_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   char* w = (char*)ws;
   const BatchDev bd = batch_dev(L, w);
   set_scan_chunk(chunk);
   cudaError_t e = batch_prepare(bd, st);
   const ElemPtrs el = batch_elements(L, w);
-  if (e == cudaSuccess) e = batch_build(bd, el, w + L.off_team, st);
+  if (e == cudaSuccess)
+    e = invariant ? batch_build_invariant(bd, el, (double*)(w + L.off_inv), st)
+                  : batch_build(bd, el, w + L.off_team, st);
   BoundaryPatch patch{L.B, bd.off, bd.probs};
   if (e == cudaSuccess)
     e = concat_scan(L.n, L.total - 1, el, S, v, zeta, bt->x0[0], x, patch, w + L.off_scan, st);

@@ -734,6 +734,11 @@ cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& c
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  return launch_terminal_element(p, out, st);
+}
+
+// Terminal element a_T into index T of the public arrays.
+cudaError_t launch_terminal_element(const lqt_problem& p, const ElemPtrs& out, cudaStream_t st) {
   const int64_t T = p.T;
   const int n = p.n;
   TermArgs t{p.n, p.nr, p.Hf, p.Xf, p.rf, out.A + T * n * n, out.b + T * n, out.C + T * n * n,

@@ -13,6 +13,7 @@ namespace lqt {
 // Device status word bits (read and cleared by lqt_get_status).
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusSingular = 2u;
+constexpr unsigned kStatusNonUniform = 4u;  // a time-invariant build met sub-intervals of different lengths
 
 extern __device__ unsigned g_status_word;
 
@@ -149,6 +150,13 @@ cudaError_t run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& f
                         const double* v, const double* zeta, const double* x0, double* x, double* u, double* cost,
                         char* ws, cudaStream_t st);
 
+// Time-invariant specialisation of the element build (lqt_invariant.cu).
+bool invariant_supported(int n, int M);
+size_t invariant_table_bytes(int n, int M, int K);
+cudaError_t launch_build_invariant(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                                   double* table, cudaStream_t st);
+cudaError_t launch_terminal_element(const lqt_problem& p, const ElemPtrs& out, cudaStream_t st);
+
 bool densify_supported(const lqt_problem& p);
 cudaError_t launch_densify(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* S, const double* v,
                            const double* zeta, const double* x, double* Sd, double* vd, double* zd, double* xd,
@@ -197,6 +205,9 @@ __host__ __device__ __forceinline__ int32_t batch_find(const int64_t* off, int32
 cudaError_t batch_prepare(const BatchDev& bd, cudaStream_t st);
 cudaError_t batch_build(const BatchDev& bd, const ElemPtrs& el, char* team_scratch, cudaStream_t st);
 cudaError_t batch_build_team(const BatchDev& bd, const ElemPtrs& el, double* gscratch, cudaStream_t st);
+cudaError_t batch_build_invariant(const BatchDev& bd, const ElemPtrs& el, double* tables, cudaStream_t st);
+template <int N, int M>
+void launch_inv_batch_build(const BatchDev& bd, const double* tables, const ElemPtrs& out, cudaStream_t st);
 
 // Concatenated scan: value scan over `Tcat + 1` elements, then the boundary maps
 // of every problem but the last replaced by x -> x0 of the next problem, then

@@ -500,3 +500,20 @@ def test_grid_dynamic_programming_1d():
     for i in range(T + 1):
         got = np.array([o["zeta"][i], o["S"][i, 0, 0], o["v"][i, 0]])
         assert np.abs(extrap[i] - got).max() < 2e-4 * max(1.0, np.abs(got).max()), (i, extrap[i], got)
+
+
+def test_time_invariant_blocks_share_A_C_J():
+    """Sec. VI-B (a time-invariant model has one conditional value function per
+    block length): with F, L, H, X, U constant and a uniform grid, the oracle's
+    elements have the same A, C, J in every block (to rounding: the block
+    lengths of a linspace grid differ in their last bits), while b, eta, zeta
+    follow the time-varying r and c.
+    The time-invariant build computes A, C, J once and only b, eta, zeta per
+    block, so its elements must equal the general build's."""
+    p = W.general_time_varying(3, 2, 2, T=9, K=3, seed=41, tf=1.8,
+                               modes={"F": W.CONST, "L": W.CONST, "H": W.CONST, "X": W.CONST, "U": W.CONST})
+    e = oracle.build_elements(p, 0, p.T)
+    for k in ("A", "C", "J"):
+        assert max(rel(e[k][j], e[k][0]) for j in range(p.T)) < 1e-14, k
+    for k in ("b", "eta", "zeta"):
+        assert not np.allclose(e[k][1], e[k][0]), k
