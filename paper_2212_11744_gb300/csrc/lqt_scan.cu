@@ -30,14 +30,20 @@ static thread_local int t_chunk_override = 0;
 void set_scan_chunk(int g) { t_chunk_override = g; }
 int scan_chunk_override() { return t_chunk_override; }
 
-// Level-0 chunk length from T: longest power of two <= 32 that still leaves
-// >= 16384 chunks (so every sub-partition has a warp), at least 2; or the
-// caller's override.
+// Level-0 chunk length from T, or the caller's override.  Level 0 is FP64
+// throughput-bound with one thread per chunk, and a sub-partition runs one
+// FP64 warp instruction per 64 cycles whatever its warp count, so the chunks
+// are sized to give every one of the 152 x 4 sub-partitions exactly one warp
+// (152 * 4 * 32 = 19456 threads): any more warps only leave some
+// sub-partitions with one warp more than others at the end.  At least 2, at
+// most 64 elements per chunk.
+constexpr int64_t kLevel0Threads = 152 * 4 * 32;
 static int level0_group(int64_t T) {
   if (t_chunk_override >= 2) return t_chunk_override;
-  int g = 2;
-  while (g < 32 && (T + 1) / (2 * g) >= 16384) g *= 2;
-  return g;
+  int64_t g = (T + 1 + kLevel0Threads - 1) / kLevel0Threads;
+  if (g < 2) g = 2;
+  if (g > 64) g = 64;
+  return (int)g;
 }
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -95,4 +95,4 @@ def test_autotuner_picks_a_candidate():
     bt = Batch(members(4, [500, 800, 300], 3))
     best = bt.autotune(candidates=(0, 4, 16), reps=2)
     assert best in (0, 4, 16)
-    assert Batch.tuning_table()[(4, 3, bt.total)][0] == best
+    assert Batch.tuning_table()[(4, 3, bt.total, 0)][0] == best
