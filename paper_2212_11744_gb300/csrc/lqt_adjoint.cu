@@ -709,6 +709,382 @@ __global__ void __launch_bounds__(64) rk4_adjoint_kernel(RK4AdjArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// 5'. the same discrete RK4 adjoint with one warp per sub-interval
+// ---------------------------------------------------------------------------
+//
+// One thread per sub-interval leaves the FP64 pipe mostly idle at the adjoint
+// workload's size (2^14 sub-intervals = 512 warps for 608 sub-partitions, each
+// a long dependent chain with its matrices in local memory).  Here a warp owns
+// a sub-interval: every matrix product spreads its n^2 outputs over the 32
+// lanes, all buffers live in shared memory, and there are 32x more warps.  The
+// arithmetic is the thread version's, step for step.
+
+namespace warp {
+
+__device__ __forceinline__ void sync() { __syncwarp(); }
+
+// c = a b, c = a^T b, c = a b^T  (n x n, lanes over the outputs)
+__device__ __forceinline__ void mm(int lane, int n, const double* a, const double* b, double* c) {
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s = fma(a[i * n + l], b[l * n + j], s);
+    c[e] = s;
+  }
+  sync();
+}
+__device__ __forceinline__ void mtm(int lane, int n, const double* a, const double* b, double* c) {
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s = fma(a[l * n + i], b[l * n + j], s);
+    c[e] = s;
+  }
+  sync();
+}
+__device__ __forceinline__ void mmt(int lane, int n, const double* a, const double* b, double* c) {
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s = fma(a[i * n + l], b[j * n + l], s);
+    c[e] = s;
+  }
+  sync();
+}
+__device__ __forceinline__ void mv(int lane, int n, const double* a, const double* x, double* y) {
+  if (lane < n) {
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s = fma(a[lane * n + l], x[l], s);
+    y[lane] = s;
+  }
+  sync();
+}
+__device__ __forceinline__ void mtv(int lane, int n, const double* a, const double* x, double* y) {
+  if (lane < n) {
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s = fma(a[l * n + lane], x[l], s);
+    y[lane] = s;
+  }
+  sync();
+}
+// a <- (a + a^T) / 2  (n <= 8: at most two entries per lane; every lane runs
+// the same iterations so that the warp barrier is reached by all)
+__device__ __forceinline__ void symm(int lane, int n, double* a) {
+  double v[(AN * AN + 31) / 32];
+#pragma unroll
+  for (int it = 0; it < (AN * AN + 31) / 32; ++it) {
+    const int e = lane + 32 * it;
+    const int i = e / n, j = e % n;
+    v[it] = (e < n * n && i < j) ? 0.5 * (a[i * n + j] + a[j * n + i]) : 0.0;
+  }
+  sync();
+#pragma unroll
+  for (int it = 0; it < (AN * AN + 31) / 32; ++it) {
+    const int e = lane + 32 * it;
+    const int i = e / n, j = e % n;
+    if (e < n * n && i < j) {
+      a[i * n + j] = v[it];
+      a[j * n + i] = v[it];
+    }
+  }
+  sync();
+}
+
+// Buffers of one RHS evaluation: t1, t2, t3 (n^2 each), vectors beta, betab,
+// Fe, Jb (n each), JG (n^2).
+struct Tmp {
+  double *t1, *t2, *t3, *JG, *beta, *betab, *v1, *v2;
+};
+
+// k = f(y): the thread version's rhs_full, lanes over entries.
+__device__ void rhs_full(int lane, int n, const double* y, const double* F, const double* B, const double* Q,
+                         const double* q, double rho, double* k, const Tmp& t) {
+  const int nn = n * n;
+  FE Y = fe_view(n, const_cast<double*>(y)), K = fe_view(n, k);
+  mv(lane, n, B, Y.eta, t.beta);
+  mm(lane, n, B, Y.J, t.t1);                                   // G
+  for (int e = lane; e < nn; e += 32) t.t2[e] = t.t1[e] - F[e];  // G - F
+  sync();
+  mm(lane, n, Y.A, t.t2, K.A);
+  if (lane < n) {
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s = fma(Y.A[lane * n + l], t.beta[l], s);
+    K.b[lane] = -s;
+  }
+  mm(lane, n, Y.A, B, t.t2);
+  mmt(lane, n, t.t2, Y.A, K.C);
+  for (int e = lane; e < nn; e += 32) K.C[e] = -K.C[e];
+  sync();
+  symm(lane, n, K.C);
+  mtv(lane, n, F, Y.eta, t.v1);
+  mv(lane, n, Y.J, t.beta, t.v2);
+  if (lane < n) K.eta[lane] = -q[lane] - t.v1[lane] + t.v2[lane];
+  mm(lane, n, Y.J, F, t.t2);  // JF
+  mm(lane, n, Y.J, t.t1, t.JG);
+  for (int e = lane; e < nn; e += 32) {
+    const int i = e / n, c = e % n;
+    K.J[e] = -Q[e] - t.t2[i * n + c] - t.t2[c * n + i] + t.JG[e];
+  }
+  sync();
+  symm(lane, n, K.J);
+  if (lane == 0) {
+    double z = -0.5 * rho;
+    for (int i = 0; i < n; ++i) z += 0.5 * Y.eta[i] * t.beta[i];
+    *K.z = z;
+  }
+  sync();
+}
+
+// The thread version's rhs_vjp, lanes over entries; Fb, Bb, Qb accumulate
+// entry-wise (each lane owns the same entries throughout), qb, rhob by lanes
+// < n and lane 0.
+__device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const double* B, double* kb, double* yb,
+                        double* Fb, double* Bb, double* Qb, double* qb, double* rhob, const Tmp& t) {
+  const int nn = n * n;
+  FE Y = fe_view(n, const_cast<double*>(y)), Kb = fe_view(n, kb), YB = fe_view(n, yb);
+  symm(lane, n, Kb.C);
+  symm(lane, n, Kb.J);
+  mv(lane, n, B, Y.eta, t.beta);
+  if (lane < n) t.betab[lane] = 0.0;
+  mm(lane, n, B, Y.J, t.t1);  // G = B J
+  for (int e = lane; e < nn; e += 32) t.t2[e] = t.t1[e] - F[e];
+  sync();
+  mmt(lane, n, Kb.A, t.t2, t.t3);
+  for (int e = lane; e < nn; e += 32) YB.A[e] += t.t3[e];
+  sync();
+  mtm(lane, n, Y.A, Kb.A, t.t3);  // Gbar
+  for (int e = lane; e < nn; e += 32) Fb[e] -= t.t3[e];
+  sync();
+  mmt(lane, n, t.t3, Y.J, t.t2);
+  for (int e = lane; e < nn; e += 32) Bb[e] += t.t2[e];
+  sync();
+  mtm(lane, n, B, t.t3, t.t2);
+  for (int e = lane; e < nn; e += 32) {
+    const int i = e / n, c = e % n;
+    YB.J[e] += t.t2[e];
+    YB.A[e] -= Kb.b[i] * t.beta[c];
+  }
+  sync();
+  mtv(lane, n, Y.A, Kb.b, t.v1);
+  if (lane < n) t.betab[lane] -= t.v1[lane];
+  mm(lane, n, Kb.C, Y.A, t.t2);
+  mm(lane, n, t.t2, B, t.t3);
+  for (int e = lane; e < nn; e += 32) YB.A[e] -= 2.0 * t.t3[e];
+  sync();
+  mtm(lane, n, Y.A, t.t2, t.t3);
+  for (int e = lane; e < nn; e += 32) {
+    const int i = e / n, c = e % n;
+    Bb[e] -= t.t3[e];
+    Fb[e] -= Y.eta[i] * Kb.eta[c];
+    YB.J[e] += Kb.eta[i] * t.beta[c];
+  }
+  if (lane < n) qb[lane] -= Kb.eta[lane];
+  sync();
+  mv(lane, n, F, Kb.eta, t.v1);
+  mtv(lane, n, Y.J, Kb.eta, t.v2);
+  if (lane < n) {
+    YB.eta[lane] -= t.v1[lane];
+    t.betab[lane] += t.v2[lane];
+  }
+  for (int e = lane; e < nn; e += 32) Qb[e] -= Kb.J[e];
+  sync();
+  mmt(lane, n, Kb.J, F, t.t2);
+  for (int e = lane; e < nn; e += 32) YB.J[e] -= t.t2[e];
+  sync();
+  mm(lane, n, F, Kb.J, t.t2);
+  for (int e = lane; e < nn; e += 32) YB.J[e] -= t.t2[e];
+  sync();
+  mmt(lane, n, Kb.J, t.t1, t.t2);
+  for (int e = lane; e < nn; e += 32) YB.J[e] += t.t2[e];
+  sync();
+  mtm(lane, n, Y.J, Kb.J, t.t3);  // Gbar2
+  for (int e = lane; e < nn; e += 32) Fb[e] -= t.t3[e];
+  sync();
+  mmt(lane, n, Y.J, Kb.J, t.t2);
+  for (int e = lane; e < nn; e += 32) Fb[e] -= t.t2[e];
+  sync();
+  mmt(lane, n, t.t3, Y.J, t.t2);
+  for (int e = lane; e < nn; e += 32) Bb[e] += t.t2[e];
+  sync();
+  mtm(lane, n, B, t.t3, t.t2);
+  for (int e = lane; e < nn; e += 32) YB.J[e] += t.t2[e];
+  const double zb = *Kb.z;
+  if (lane == 0) *rhob -= 0.5 * zb;
+  if (lane < n) {
+    YB.eta[lane] += 0.5 * zb * t.beta[lane];
+    t.betab[lane] += 0.5 * zb * Y.eta[lane];
+  }
+  sync();
+  for (int e = lane; e < nn; e += 32) {
+    const int i = e / n, c = e % n;
+    Bb[e] += t.betab[i] * Y.eta[c];
+  }
+  mtv(lane, n, B, t.betab, t.v1);
+  if (lane < n) YB.eta[lane] += t.v1[lane];
+  sync();
+}
+
+}  // namespace warp
+
+// Shared-memory doubles of one warp of rk4_adjoint_warp_kernel.
+__host__ __device__ constexpr int rk4w_smem_doubles() {
+  return 11 * AS + 8 * AN * AN + 4 * AN + (2 * 8 + 1) * AN + (2 * 8 + 1) + 8;
+}
+
+__global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x;
+  const int n = a.n, nn = n * n, fs = fe_size(n), K = a.K, M = a.M;
+  double* y = sm;
+  double* k1 = y + AS;
+  double* k2 = k1 + AS;
+  double* k3 = k2 + AS;
+  double* y2 = k3 + AS;
+  double* y3 = y2 + AS;
+  double* y4 = y3 + AS;
+  double* yb = y4 + AS;
+  double* kb = yb + AS;   // one stage's output adjoint at a time
+  double* acc = kb + AS;  // a stage's input adjoint
+  double* kbs = acc + AS; // the step's h-weighted output adjoint
+  double* B = kbs + AS;
+  double* Fb = B + AN * AN;
+  double* Bb = Fb + AN * AN;
+  double* Qb = Bb + AN * AN;
+  warp::Tmp tmp;
+  tmp.t1 = Qb + AN * AN;
+  tmp.t2 = tmp.t1 + AN * AN;
+  tmp.t3 = tmp.t2 + AN * AN;
+  tmp.JG = tmp.t3 + AN * AN;
+  tmp.beta = tmp.JG + AN * AN;
+  tmp.betab = tmp.beta + AN;
+  tmp.v1 = tmp.betab + AN;
+  tmp.v2 = tmp.v1 + AN;
+  double* qb = tmp.v2 + AN;          // [(2K+1) n]
+  double* rhob = qb + (2 * 8 + 1) * AN;  // [2K+1]
+  for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
+    const double h = (a.t[j + 1] - a.t[j]) / K;
+    const double* F = a.cf.F.ptr + sample_index(a.cf.F.mode, j, 0, K) * nn;
+    const double* Lt = a.cf.Lt.ptr + sample_index(a.cf.Lt.mode, j, 0, K) * n * M;
+    const double* Q = a.X + sample_index(a.X_mode, j, 0, K) * nn;
+    for (int e = lane; e < nn; e += 32) {
+      const int i = e / n, c = e % n;
+      double s = 0.0;
+      for (int l = 0; l < M; ++l) s = fma(Lt[i * M + l], Lt[c * M + l], s);
+      B[e] = s;
+      Fb[e] = 0.0;
+      Bb[e] = 0.0;
+      Qb[e] = 0.0;
+    }
+    for (int e = lane; e < (2 * K + 1) * n; e += 32) qb[e] = 0.0;
+    for (int e = lane; e <= 2 * K; e += 32) rhob[e] = 0.0;
+    for (int e = lane; e < fs; e += 32) y[e] = (e < nn && e % (n + 1) == 0) ? 1.0 : 0.0;
+    warp::sync();
+    auto qr_at = [&](int p) { return a.cf.qr.ptr + sample_index(a.cf.qr.mode, j, p, K) * (n + 1); };
+    double* ysj = a.ys + j * (int64_t)K * fs;
+    // forward, storing the state before every step
+    for (int i = K - 1; i >= 0; --i) {
+      for (int e = lane; e < fs; e += 32) ysj[i * fs + e] = y[e];
+      const double* q1 = qr_at(2 * i + 2);
+      const double* q2 = qr_at(2 * i + 1);
+      const double* q3 = qr_at(2 * i);
+      warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], k1, tmp);
+      for (int e = lane; e < fs; e += 32) y2[e] = y[e] - 0.5 * h * k1[e];
+      warp::sync();
+      warp::rhs_full(lane, n, y2, F, B, Q, q2, q2[n], k2, tmp);
+      for (int e = lane; e < fs; e += 32) y3[e] = y[e] - 0.5 * h * k2[e];
+      warp::sync();
+      warp::rhs_full(lane, n, y3, F, B, Q, q2, q2[n], k3, tmp);
+      for (int e = lane; e < fs; e += 32) y4[e] = y[e] - h * k3[e];
+      warp::sync();
+      warp::rhs_full(lane, n, y4, F, B, Q, q3, q3[n], y2, tmp);  // k4 into y2
+      for (int e = lane; e < fs; e += 32) y[e] = y[e] - (h / 6.0) * (k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + y2[e]);
+      warp::sync();
+    }
+    // adjoint
+    const double* eb = a.ebar + j * fs;
+    for (int e = lane; e < fs; e += 32) yb[e] = eb[e];
+    warp::sync();
+    for (int i = 0; i < K; ++i) {
+      for (int e = lane; e < fs; e += 32) y[e] = ysj[i * fs + e];
+      warp::sync();
+      const int p1 = 2 * i + 2, p2 = 2 * i + 1, p3 = 2 * i;
+      const double* q1 = qr_at(p1);
+      const double* q2 = qr_at(p2);
+      const double* q3 = qr_at(p3);
+      warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], k1, tmp);
+      for (int e = lane; e < fs; e += 32) y2[e] = y[e] - 0.5 * h * k1[e];
+      warp::sync();
+      warp::rhs_full(lane, n, y2, F, B, Q, q2, q2[n], k2, tmp);
+      for (int e = lane; e < fs; e += 32) y3[e] = y[e] - 0.5 * h * k2[e];
+      warp::sync();
+      warp::rhs_full(lane, n, y3, F, B, Q, q2, q2[n], k3, tmp);
+      for (int e = lane; e < fs; e += 32) y4[e] = y[e] - h * k3[e];
+      warp::sync();
+      // y_new = y - h/6 (k1 + 2 k2 + 2 k3 + k4): stage output adjoints
+      // kb4 = -h/6 yb, kb3 = -h/3 yb (+ -h acc4), kb2 = -h/3 yb (+ -h/2 acc3),
+      // kb1 = -h/6 yb (+ -h/2 acc2)
+      for (int e = lane; e < fs; e += 32) {
+        kbs[e] = yb[e];
+        kb[e] = -(h / 6.0) * yb[e];
+        acc[e] = 0.0;
+      }
+      warp::sync();
+      warp::rhs_vjp(lane, n, y4, F, B, kb, acc, Fb, Bb, Qb, qb + p3 * n, rhob + p3, tmp);
+      for (int e = lane; e < fs; e += 32) {
+        yb[e] += acc[e];
+        kb[e] = -(h / 3.0) * kbs[e] - h * acc[e];
+        acc[e] = 0.0;
+      }
+      warp::sync();
+      warp::rhs_vjp(lane, n, y3, F, B, kb, acc, Fb, Bb, Qb, qb + p2 * n, rhob + p2, tmp);
+      for (int e = lane; e < fs; e += 32) {
+        yb[e] += acc[e];
+        kb[e] = -(h / 3.0) * kbs[e] - 0.5 * h * acc[e];
+        acc[e] = 0.0;
+      }
+      warp::sync();
+      warp::rhs_vjp(lane, n, y2, F, B, kb, acc, Fb, Bb, Qb, qb + p2 * n, rhob + p2, tmp);
+      for (int e = lane; e < fs; e += 32) {
+        yb[e] += acc[e];
+        kb[e] = -(h / 6.0) * kbs[e] - 0.5 * h * acc[e];
+        acc[e] = 0.0;
+      }
+      warp::sync();
+      warp::rhs_vjp(lane, n, y, F, B, kb, acc, Fb, Bb, Qb, qb + p1 * n, rhob + p1, tmp);
+      for (int e = lane; e < fs; e += 32) yb[e] += acc[e];
+      warp::sync();
+    }
+    // coefficient adjoints of this sub-interval (as in the thread version)
+    double* oF = a.pF + j * nn;
+    double* oB = a.pB + j * nn;
+    double* oX = a.pX + j * nn;
+    for (int e = lane; e < nn; e += 32) {
+      const int i = e / n, c = e % n;
+      oF[e] = Fb[e];
+      oB[e] = Bb[e];
+      double x = 0.5 * (Qb[i * n + c] + Qb[c * n + i]);
+      for (int p = 0; p <= 2 * K; ++p) {
+        const double* rp = a.r ? a.r + sample_index(a.r_mode, j, p, K) * n : nullptr;
+        if (rp) x += qb[p * n + i] * rp[c] + rhob[p] * rp[i] * rp[c];
+      }
+      oX[e] = x;
+    }
+    if (a.pr) {
+      for (int e = lane; e < (2 * K + 1) * n; e += 32) {
+        const int p = e / n, i = e % n;
+        const double* rp = a.r ? a.r + sample_index(a.r_mode, j, p, K) * n : nullptr;
+        double s = 0.0;
+        for (int l = 0; l < n; ++l) s = fma(Q[l * n + i], qb[p * n + l], s);
+        if (rp)
+          for (int l = 0; l < n; ++l) s += rhob[p] * (Q[i * n + l] + Q[l * n + i]) * rp[l];
+        a.pr[(j * (2 * K + 1) + p) * n + i] = s;
+      }
+    }
+    warp::sync();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // 6. reductions into the coefficient layouts
 // ---------------------------------------------------------------------------
 
@@ -948,7 +1324,12 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   ra.r = p.r.ptr; ra.r_mode = p.r.mode; ra.ebar = ea.ebar_out; ra.ys = (double*)(ws + b.ys);
   ra.pF = (double*)(ws + b.pF); ra.pB = (double*)(ws + b.pB); ra.pX = (double*)(ws + b.pX);
   ra.pr = (double*)(ws + b.pr);
-  rk4_adjoint_kernel<<<nb(T, 64), 64, 0, st>>>(ra);
+  {
+    const size_t smem = rk4w_smem_doubles() * sizeof(double);
+    cudaFuncSetAttribute(rk4_adjoint_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = T < 152 * 12 ? T : 152 * 12;
+    rk4_adjoint_warp_kernel<<<(unsigned)grid, 32, smem, st>>>(ra);
+  }
   count_launch();
   // 6. reductions
   auto reduce = [&](const double* part, int64_t rows, int size, int32_t mode, double* out) {

@@ -73,83 +73,72 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
   const double* A = y.A();
   const double* J = y.J();
   const double* eta = y.eta();
-  for (int e = lane; e < 2 * N * M + M; e += TEAM) {
-    if (e < 2 * N * M) {
-      const int which = e / (N * M), r = e % (N * M), i = r / M, a = r % M;
-      const double* X = which ? J : A;
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(X[i * N + l], Lt[l * M + a], s);
-      (which ? P : AL)[i * M + a] = s;
-    } else {
-      const int a = e - 2 * N * M;
-      double s = 0.0;
-      for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
-      w[a] = s;
+  // One loop per output kind (a warp's lanes then run the same code).
+  for (int e = lane; e < N * M; e += TEAM) {
+    const int i = e / M, a = e % M;
+    double s1 = 0.0, s2 = 0.0;
+    for (int l = 0; l < N; ++l) {
+      s1 = fma(A[i * N + l], Lt[l * M + a], s1);
+      s2 = fma(J[i * N + l], Lt[l * M + a], s2);
     }
+    AL[e] = s1;
+    P[e] = s2;
+  }
+  for (int a = lane; a < M; a += TEAM) {
+    double s = 0.0;
+    for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
+    w[a] = s;
   }
   sync<TEAM>();
   constexpr int NS = N * (N + 1) / 2;
-  constexpr int ITEMS = N * N + N + NS + N + NS + 1;
-  for (int e = lane; e < ITEMS; e += TEAM) {
-    int t = e;
-    if (t < N * N) {  // dA = AL P^T - A F
-      const int i = t / N, j = t % N;
-      double s = 0.0;
-      for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
-      for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
-      k.A()[t] = s;
-      continue;
+  // dA = AL P^T - A F
+  for (int t = lane; t < N * N; t += TEAM) {
+    const int i = t / N, j = t % N;
+    double s = 0.0;
+    for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
+    for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
+    k.A()[t] = s;
+  }
+  // db = -AL w - A c ; deta = -q - F^T eta + J c + P w
+  for (int t = lane; t < N; t += TEAM) {
+    double s = 0.0, se = -qr[t];
+    for (int a = 0; a < M; ++a) {
+      s = fma(-AL[t * M + a], w[a], s);
+      se = fma(P[t * M + a], w[a], se);
     }
-    t -= N * N;
-    if (t < N) {  // db = -AL w - A c
-      double s = 0.0;
-      for (int a = 0; a < M; ++a) s = fma(-AL[t * M + a], w[a], s);
-      if (c)
-        for (int l = 0; l < N; ++l) s = fma(-A[t * N + l], c[l], s);
-      k.b()[t] = s;
-      continue;
-    }
-    t -= N;
-    if (t < NS) {  // dC = -AL AL^T
-      int i, j;
-      upper_ij(N, t, i, j);
-      double s = 0.0;
-      for (int a = 0; a < M; ++a) s = fma(-AL[i * M + a], AL[j * M + a], s);
-      k.C()[i * N + j] = s;
-      k.C()[j * N + i] = s;
-      continue;
-    }
-    t -= NS;
-    if (t < N) {  // deta = -q - F^T eta + J c + P w
-      double s = -qr[t];
-      for (int l = 0; l < N; ++l) s = fma(-F[l * N + t], eta[l], s);
-      if (c)
-        for (int l = 0; l < N; ++l) s = fma(J[t * N + l], c[l], s);
-      for (int a = 0; a < M; ++a) s = fma(P[t * M + a], w[a], s);
-      k.eta()[t] = s;
-      continue;
-    }
-    t -= N;
-    if (t < NS) {  // dJ = -Q - JF - (JF)^T + P P^T
-      int i, j;
-      upper_ij(N, t, i, j);
-      double s = -Q[i * N + j];
+    for (int l = 0; l < N; ++l) se = fma(-F[l * N + t], eta[l], se);
+    if (c)
       for (int l = 0; l < N; ++l) {
-        s = fma(-J[i * N + l], F[l * N + j], s);
-        s = fma(-J[j * N + l], F[l * N + i], s);
+        s = fma(-A[t * N + l], c[l], s);
+        se = fma(J[t * N + l], c[l], se);
       }
-      for (int a = 0; a < M; ++a) s = fma(P[i * M + a], P[j * M + a], s);
-      k.J()[i * N + j] = s;
-      k.J()[j * N + i] = s;
-      continue;
+    k.b()[t] = s;
+    k.eta()[t] = se;
+  }
+  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored)
+  for (int t = lane; t < NS; t += TEAM) {
+    int i, j;
+    upper_ij(N, t, i, j);
+    double sc = 0.0, sj = -Q[i * N + j];
+    for (int a = 0; a < M; ++a) {
+      sc = fma(-AL[i * M + a], AL[j * M + a], sc);
+      sj = fma(P[i * M + a], P[j * M + a], sj);
     }
-    {  // dzeta
-      double z = -0.5 * qr[N];
-      for (int a = 0; a < M; ++a) z = fma(0.5 * w[a], w[a], z);
-      if (c)
-        for (int l = 0; l < N; ++l) z = fma(eta[l], c[l], z);
-      *k.zeta() = z;
+    for (int l = 0; l < N; ++l) {
+      sj = fma(-J[i * N + l], F[l * N + j], sj);
+      sj = fma(-J[j * N + l], F[l * N + i], sj);
     }
+    k.C()[i * N + j] = sc;
+    k.C()[j * N + i] = sc;
+    k.J()[i * N + j] = sj;
+    k.J()[j * N + i] = sj;
+  }
+  if (lane == 0) {  // dzeta (O(M + N))
+    double z = -0.5 * qr[N];
+    for (int a = 0; a < M; ++a) z = fma(0.5 * w[a], w[a], z);
+    if (c)
+      for (int l = 0; l < N; ++l) z = fma(eta[l], c[l], z);
+    *k.zeta() = z;
   }
   sync<TEAM>();
 }
@@ -257,6 +246,26 @@ __device__ void lu_solve(int lane, double* W, double* R, int Q, double* fscratch
   }
 }
 
+// Sum of one value per thread over the team (every thread gets the sum).
+// scratch: TEAM doubles (teams larger than a warp).
+template <int TEAM>
+__device__ __forceinline__ double team_sum(int lane, double x, double* scratch) {
+  if constexpr (TEAM <= 32) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  } else {
+    scratch[lane] = x;
+    __syncthreads();
+    for (int w = TEAM / 2; w > 0; w >>= 1) {
+      if (lane < w) scratch[lane] += scratch[lane + w];
+      __syncthreads();
+    }
+    const double r = scratch[0];
+    __syncthreads();
+    return r;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // combination rule
 // ---------------------------------------------------------------------------
@@ -280,24 +289,20 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   double* J2z = l0 + N;
   double* wv = J2z + N;
   // W = I + C1 J2 ; R = [A1 | C1 | b1 + C1 eta2]
-  for (int e = lane; e < N * N + N * Q; e += TEAM) {
-    if (e < N * N) {
-      const int i = e / N, j = e % N;
-      G s = (G)((i == j) ? 1.0 : 0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(e2.J()[l * N + j]), s);
-      W[e] = s;
-    } else {
-      const int t = e - N * N, i = t / Q, j = t % Q;
-      double v;
-      if (j < N) v = e1.A()[i * N + j];
-      else if (j < 2 * N) v = e1.C()[i * N + (j - N)];
-      else {
-        G g = (G)(e1.b()[i]);
-        for (int l = 0; l < N; ++l) g = fma((G)(e1.C()[i * N + l]), (G)(e2.eta()[l]), g);
-        v = (double)g;
-      }
-      R[t] = v;
-    }
+  for (int e = lane; e < N * N; e += TEAM) {
+    const int i = e / N, j = e % N;
+    G s = (G)((i == j) ? 1.0 : 0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(e2.J()[l * N + j]), s);
+    W[e] = s;
+  }
+  for (int e = lane; e < 2 * N * N; e += TEAM) {
+    const int i = e / (2 * N), j = e % (2 * N);
+    R[i * Q + j] = j < N ? e1.A()[i * N + j] : e1.C()[i * N + (j - N)];
+  }
+  for (int i = lane; i < N; i += TEAM) {
+    G g = (G)(e1.b()[i]);
+    for (int l = 0; l < N; ++l) g = fma((G)(e1.C()[i * N + l]), (G)(e2.eta()[l]), g);
+    R[i * Q + 2 * N] = (double)g;
   }
   sync<TEAM>();
   lu_solve<N, TEAM>(lane, W, R, Q, fs, is);
@@ -305,69 +310,58 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   for (int i = lane; i < N; i += TEAM) z0[i] = R[i * Q + 2 * N];
   sync<TEAM>();
   // J2 z0, l0 = J2 z0 - eta2, w = eta2 - J2 b1 ; T1 = J2 A1
-  for (int e = lane; e < 2 * N + N * N; e += TEAM) {
-    if (e < N) {
-      G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[e * N + l]), (G)(z0[l]), s);
-      J2z[e] = s;
-      l0[e] = s - e2.eta()[e];
-    } else if (e < 2 * N) {
-      const int i = e - N;
-      G s = (G)(e2.eta()[i]);
-      for (int l = 0; l < N; ++l) s = fma((G)(-e2.J()[i * N + l]), (G)(e1.b()[l]), s);
-      wv[i] = s;
-    } else {
-      const int t = e - 2 * N, i = t / N, j = t % N;
-      G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[i * N + l]), (G)(e1.A()[l * N + j]), s);
-      T1[t] = s;
-    }
+  for (int e = lane; e < N; e += TEAM) {
+    G s = (G)(0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[e * N + l]), (G)(z0[l]), s);
+    J2z[e] = s;
+    l0[e] = s - e2.eta()[e];
+    G w = (G)(e2.eta()[e]);
+    for (int l = 0; l < N; ++l) w = fma((G)(-e2.J()[e * N + l]), (G)(e1.b()[l]), w);
+    wv[e] = w;
+  }
+  for (int t = lane; t < N * N; t += TEAM) {
+    const int i = t / N, j = t % N;
+    G s = (G)(0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[i * N + l]), (G)(e1.A()[l * N + j]), s);
+    T1[t] = s;
   }
   sync<TEAM>();
   // eta = K1^T w + eta1 ; J = K1^T T1 + J1 (upper, mirrored) ; b = A2 z0 + b2 ;
-  // A = A2 K1 ; zeta (lane 0)
+  // A = A2 K1 ; zeta: one term per row i, summed over the team.  Each output
+  // kind has its own loop, so that a warp's lanes run the same code.
   constexpr int NS = N * (N + 1) / 2;
-  for (int e = lane; e < N + NS + N + N * N + 1; e += TEAM) {
-    int t = e;
-    if (t < N) {
-      G s = (G)(e1.eta()[t]);
-      for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + t]), (G)(wv[l]), s);
-      out.eta()[t] = s;
-      continue;
-    }
-    t -= N;
-    if (t < NS) {
-      int i, j;
-      upper_ij(N, t, i, j);
-      G s = (G)(e1.J()[i * N + j]);
-      for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + i]), (G)(T1[l * N + j]), s);
-      out.J()[i * N + j] = s;
-      out.J()[j * N + i] = s;
-      continue;
-    }
-    t -= NS;
-    if (t < N) {
-      G s = (G)(e2.b()[t]);
-      for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[t * N + l]), (G)(z0[l]), s);
-      out.b()[t] = s;
-      continue;
-    }
-    t -= N;
-    if (t < N * N) {
-      const int i = t / N, j = t % N;
-      G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[i * N + l]), (G)(R[l * Q + j]), s);
-      out.A()[t] = s;
-      continue;
-    }
-    double z = *e1.zeta() + *e2.zeta();
-    for (int i = 0; i < N; ++i) {
+  for (int t = lane; t < N; t += TEAM) {
+    G s = (G)(e1.eta()[t]);
+    for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + t]), (G)(wv[l]), s);
+    out.eta()[t] = s;
+    G sb = (G)(e2.b()[t]);
+    for (int l = 0; l < N; ++l) sb = fma((G)(e2.A()[t * N + l]), (G)(z0[l]), sb);
+    out.b()[t] = sb;
+  }
+  for (int t = lane; t < NS; t += TEAM) {
+    int i, j;
+    upper_ij(N, t, i, j);
+    G s = (G)(e1.J()[i * N + j]);
+    for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + i]), (G)(T1[l * N + j]), s);
+    out.J()[i * N + j] = s;
+    out.J()[j * N + i] = s;
+  }
+  for (int t = lane; t < N * N; t += TEAM) {
+    const int i = t / N, j = t % N;
+    G s = (G)(0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[i * N + l]), (G)(R[l * Q + j]), s);
+    out.A()[t] = s;
+  }
+  {
+    double zt = 0.0;
+    for (int i = lane; i < N; i += TEAM) {
       G s = (G)(0.0);
       for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(l0[l]), s);
-      z = fma(0.5 * l0[i], s, z);
-      z = fma(z0[i], fma(0.5, J2z[i], -e2.eta()[i]), z);
+      zt = fma(0.5 * l0[i], s, zt);
+      zt = fma(z0[i], fma(0.5, J2z[i], -e2.eta()[i]), zt);
     }
-    *out.zeta() = z;
+    const double z = team_sum<TEAM>(lane, zt, fs);
+    if (lane == 0) *out.zeta() = *e1.zeta() + *e2.zeta() + z;
   }
   sync<TEAM>();
   // T1 = A2 MC1 ; then C = T1 A2^T + C2
@@ -414,23 +408,17 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   double* Sz = T1 + N * N;
   double* l0 = Sz + N;
   double* wv = l0 + N;
-  for (int t = lane; t < N * N + N * Q; t += TEAM) {
-    if (t < N * N) {
-      const int i = t / N, j = t % N;
-      G s = (G)((i == j) ? 1.0 : 0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(S2[l * N + j]), s);
-      W[t] = s;
-    } else {
-      const int u = t - N * N, i = u / Q, j = u % Q;
-      double v;
-      if (j < N) v = e.A()[i * N + j];
-      else {
-        G g = (G)(e.b()[i]);
-        for (int l = 0; l < N; ++l) g = fma((G)(e.C()[i * N + l]), (G)(v2[l]), g);
-        v = (double)g;
-      }
-      R[u] = v;
-    }
+  for (int t = lane; t < N * N; t += TEAM) {
+    const int i = t / N, j = t % N;
+    G s = (G)((i == j) ? 1.0 : 0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(S2[l * N + j]), s);
+    W[t] = s;
+    R[i * Q + j] = e.A()[t];
+  }
+  for (int i = lane; i < N; i += TEAM) {
+    G g = (G)(e.b()[i]);
+    for (int l = 0; l < N; ++l) g = fma((G)(e.C()[i * N + l]), (G)(v2[l]), g);
+    R[i * Q + N] = (double)g;
   }
   sync<TEAM>();
   lu_solve<N, TEAM>(lane, W, R, Q, fs, is);
@@ -440,50 +428,48 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   }
   sync<TEAM>();
   // Sz = S2 alpha, l0 = Sz - v2, w = v2 - S2 b ; T1 = S2 A
-  for (int t = lane; t < 2 * N + N * N; t += TEAM) {
-    if (t < N) {
-      G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(S2[t * N + l]), (G)(alpha[l]), s);
-      Sz[t] = s;
-      l0[t] = s - v2[t];
-    } else if (t < 2 * N) {
-      const int i = t - N;
-      G s = (G)(v2[i]);
-      for (int l = 0; l < N; ++l) s = fma((G)(-S2[i * N + l]), (G)(e.b()[l]), s);
-      wv[i] = s;
-    } else {
-      const int u = t - 2 * N, i = u / N, j = u % N;
-      G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(S2[i * N + l]), (G)(e.A()[l * N + j]), s);
-      T1[u] = s;
-    }
+  for (int t = lane; t < N; t += TEAM) {
+    G s = (G)(0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(S2[t * N + l]), (G)(alpha[l]), s);
+    Sz[t] = s;
+    l0[t] = s - v2[t];
+    G w = (G)(v2[t]);
+    for (int l = 0; l < N; ++l) w = fma((G)(-S2[t * N + l]), (G)(e.b()[l]), w);
+    wv[t] = w;
+  }
+  for (int u = lane; u < N * N; u += TEAM) {
+    const int i = u / N, j = u % N;
+    G s = (G)(0.0);
+    for (int l = 0; l < N; ++l) s = fma((G)(S2[i * N + l]), (G)(e.A()[l * N + j]), s);
+    T1[u] = s;
   }
   sync<TEAM>();
   constexpr int NS = N * (N + 1) / 2;
   double* So = out;
   double* vo = out + N * N;
-  for (int t = lane; t < N + NS + 1; t += TEAM) {
-    if (t < N) {
-      G s = (G)(e.eta()[t]);
-      for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + t]), (G)(wv[l]), s);
-      vo[t] = s;
-    } else if (t < N + NS) {
-      int i, j;
-      upper_ij(N, t - N, i, j);
-      G s = (G)(e.J()[i * N + j]);
-      for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + i]), (G)(T1[l * N + j]), s);
-      So[i * N + j] = s;
-      So[j * N + i] = s;
-    } else {
-      double z = *e.zeta() + zeta2;
-      for (int i = 0; i < N; ++i) {
-        G s = (G)(0.0);
-        for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(l0[l]), s);
-        z = fma(0.5 * l0[i], s, z);
-        z = fma(alpha[i], fma(0.5, Sz[i], -v2[i]), z);
-      }
-      out[N * N + N] = z;
+  for (int t = lane; t < N; t += TEAM) {
+    G s = (G)(e.eta()[t]);
+    for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + t]), (G)(wv[l]), s);
+    vo[t] = s;
+  }
+  for (int t = lane; t < NS; t += TEAM) {
+    int i, j;
+    upper_ij(N, t, i, j);
+    G s = (G)(e.J()[i * N + j]);
+    for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + i]), (G)(T1[l * N + j]), s);
+    So[i * N + j] = s;
+    So[j * N + i] = s;
+  }
+  {
+    double zt = 0.0;
+    for (int i = lane; i < N; i += TEAM) {
+      G s = (G)(0.0);
+      for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(l0[l]), s);
+      zt = fma(0.5 * l0[i], s, zt);
+      zt = fma(alpha[i], fma(0.5, Sz[i], -v2[i]), zt);
     }
+    const double z = team_sum<TEAM>(lane, zt, fs);
+    if (lane == 0) out[N * N + N] = *e.zeta() + zeta2 + z;
   }
   sync<TEAM>();
 }
