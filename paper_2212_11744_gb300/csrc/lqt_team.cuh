@@ -38,6 +38,59 @@ __device__ __forceinline__ void upper_ij(int N, int t, int& i, int& j) {
   j = r + t;
 }
 
+// Register-blocked product over a team: out(i, j, s) receives
+// s = sum_{l < INNER} a(i, l) b(l, j) for i < ROWS, j < COLS.  Each thread owns
+// an RB x CB block of outputs (RB * CB accumulators, RB + CB operand loads per
+// step of l), with the block shape chosen so that the blocks just cover the
+// team; the mapping depends only on (ROWS, COLS, TEAM), so two products of one
+// shape give every thread the same outputs (a thread may then accumulate
+// into its outputs without a barrier).  G is the product type.
+template <int ROWS, int COLS, int TEAM>
+struct GemmShape {
+  static constexpr int cb() {
+    int c = 1;
+    while (c < 4 && COLS % (2 * c) == 0 && ROWS * COLS / (2 * c) >= TEAM) c *= 2;
+    return c;
+  }
+  static constexpr int CB = cb();
+  static constexpr int rb() {
+    int r = 1;
+    while (r < 4 && ROWS % (2 * r) == 0 && ROWS * COLS / (CB * 2 * r) >= TEAM) r *= 2;
+    return r;
+  }
+  static constexpr int RB = rb();
+};
+
+template <int ROWS, int COLS, int INNER, int TEAM, typename G, class FA, class FB, class FO>
+__device__ __forceinline__ void gemm(int lane, FA a, FB b, FO out) {
+  constexpr int RB = GemmShape<ROWS, COLS, TEAM>::RB, CB = GemmShape<ROWS, COLS, TEAM>::CB;
+  constexpr int NBC = COLS / CB, NB = (ROWS / RB) * NBC;
+  for (int blk = lane; blk < NB; blk += TEAM) {
+    const int i0 = (blk / NBC) * RB, j0 = (blk % NBC) * CB;
+    G acc[RB][CB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) acc[r][c] = (G)0;
+#pragma unroll 4
+    for (int l = 0; l < INNER; ++l) {
+      G av[RB], bv[CB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) av[r] = (G)a(i0 + r, l);
+#pragma unroll
+      for (int c = 0; c < CB; ++c) bv[c] = (G)b(l, j0 + c);
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) out(i0 + r, j0 + c, acc[r][c]);
+  }
+}
+
 // An element as six field pointers (full n x n matrices), so that a record can
 // live in a packed buffer (A, b, C, eta, J, zeta back to back) or in the public
 // SoA arrays.
@@ -65,40 +118,50 @@ struct Rec {
 // element build right-hand side (factor form, see build_kernel)
 // ---------------------------------------------------------------------------
 
-// k = f(y); scratch: AL, P (N x M), w (M).
+// k = f(y); scratch: AL, P (N x M), w (M), JF (N x N).
 template <int N, int M, int TEAM>
 __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
                     const double* __restrict__ Lt, const double* __restrict__ Q, const double* __restrict__ qr,
-                    double* AL, double* P, double* w) {
+                    double* AL, double* P, double* w, double* JF) {
   const double* A = y.A();
   const double* J = y.J();
   const double* eta = y.eta();
-  // One loop per output kind (a warp's lanes then run the same code).
-  for (int e = lane; e < N * M; e += TEAM) {
-    const int i = e / M, a = e % M;
-    double s1 = 0.0, s2 = 0.0;
-    for (int l = 0; l < N; ++l) {
-      s1 = fma(A[i * N + l], Lt[l * M + a], s1);
-      s2 = fma(J[i * N + l], Lt[l * M + a], s2);
-    }
-    AL[e] = s1;
-    P[e] = s2;
-  }
+  double* kA = k.A();
+  double* kC = k.C();
+  double* kJ = k.J();
+  // AL = A Lt, P = J Lt, JF = J F, w = Lt^T eta
+  gemm<N, M, N, TEAM, double>(lane, [&](int i, int l) { return A[i * N + l]; },
+                              [&](int l, int j) { return Lt[l * M + j]; },
+                              [&](int i, int j, double v) { AL[i * M + j] = v; });
+  gemm<N, M, N, TEAM, double>(lane, [&](int i, int l) { return J[i * N + l]; },
+                              [&](int l, int j) { return Lt[l * M + j]; },
+                              [&](int i, int j, double v) { P[i * M + j] = v; });
+  gemm<N, N, N, TEAM, double>(lane, [&](int i, int l) { return J[i * N + l]; },
+                              [&](int l, int j) { return F[l * N + j]; },
+                              [&](int i, int j, double v) { JF[i * N + j] = v; });
   for (int a = lane; a < M; a += TEAM) {
     double s = 0.0;
     for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
     w[a] = s;
   }
+  // dA = -A F (first pass) ... + AL P^T (same outputs per thread, see gemm)
+  gemm<N, N, N, TEAM, double>(lane, [&](int i, int l) { return A[i * N + l]; },
+                              [&](int l, int j) { return F[l * N + j]; },
+                              [&](int i, int j, double v) { kA[i * N + j] = -v; });
   sync<TEAM>();
-  constexpr int NS = N * (N + 1) / 2;
-  // dA = AL P^T - A F
-  for (int t = lane; t < N * N; t += TEAM) {
-    const int i = t / N, j = t % N;
-    double s = 0.0;
-    for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
-    for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
-    k.A()[t] = s;
-  }
+  gemm<N, N, M, TEAM, double>(lane, [&](int i, int l) { return AL[i * M + l]; },
+                              [&](int l, int j) { return P[j * M + l]; },
+                              [&](int i, int j, double v) { kA[i * N + j] += v; });
+  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (both exactly symmetric:
+  // entry (i, j) and (j, i) run the same products in the same order)
+  gemm<N, N, M, TEAM, double>(lane, [&](int i, int l) { return AL[i * M + l]; },
+                              [&](int l, int j) { return AL[j * M + l]; },
+                              [&](int i, int j, double v) { kC[i * N + j] = -v; });
+  gemm<N, N, M, TEAM, double>(lane, [&](int i, int l) { return P[i * M + l]; },
+                              [&](int l, int j) { return P[j * M + l]; },
+                              [&](int i, int j, double v) {
+                                kJ[i * N + j] = -Q[i * N + j] - JF[i * N + j] - JF[j * N + i] + v;
+                              });
   // db = -AL w - A c ; deta = -q - F^T eta + J c + P w
   for (int t = lane; t < N; t += TEAM) {
     double s = 0.0, se = -qr[t];
@@ -114,24 +177,6 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
       }
     k.b()[t] = s;
     k.eta()[t] = se;
-  }
-  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored)
-  for (int t = lane; t < NS; t += TEAM) {
-    int i, j;
-    upper_ij(N, t, i, j);
-    double sc = 0.0, sj = -Q[i * N + j];
-    for (int a = 0; a < M; ++a) {
-      sc = fma(-AL[i * M + a], AL[j * M + a], sc);
-      sj = fma(P[i * M + a], P[j * M + a], sj);
-    }
-    for (int l = 0; l < N; ++l) {
-      sj = fma(-J[i * N + l], F[l * N + j], sj);
-      sj = fma(-J[j * N + l], F[l * N + i], sj);
-    }
-    k.C()[i * N + j] = sc;
-    k.C()[j * N + i] = sc;
-    k.J()[i * N + j] = sj;
-    k.J()[j * N + i] = sj;
   }
   if (lane == 0) {  // dzeta (O(M + N))
     double z = -0.5 * qr[N];
@@ -277,7 +322,9 @@ __host__ __device__ constexpr int combine_scratch_doubles() {
   return N * N + N * (2 * N + 1) + N * N + 4 * N;
 }
 
-// out = e1 (x) e2 (full elements; out must not alias e1 or e2).
+// out = e1 (x) e2 (full elements; out must not alias e1 or e2).  The O(N^3)
+// products are register-blocked team products (gemm above); the symmetric
+// results J, C are formed in full and stored as (X + X^T)/2.
 template <int N, int TEAM, typename G = double>
 __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr, double* fs, int* is) {
   constexpr int Q = 2 * N + 1;
@@ -288,20 +335,20 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   double* l0 = z0 + N;
   double* J2z = l0 + N;
   double* wv = J2z + N;
+  const double* A1 = e1.A();
+  const double* C1 = e1.C();
+  const double* A2 = e2.A();
+  const double* J2 = e2.J();
   // W = I + C1 J2 ; R = [A1 | C1 | b1 + C1 eta2]
-  for (int e = lane; e < N * N; e += TEAM) {
-    const int i = e / N, j = e % N;
-    G s = (G)((i == j) ? 1.0 : 0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(e2.J()[l * N + j]), s);
-    W[e] = s;
-  }
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return C1[i * N + l]; }, [&](int l, int j) { return J2[l * N + j]; },
+                         [&](int i, int j, G v) { W[i * N + j] = (double)v + (i == j ? 1.0 : 0.0); });
   for (int e = lane; e < 2 * N * N; e += TEAM) {
     const int i = e / (2 * N), j = e % (2 * N);
-    R[i * Q + j] = j < N ? e1.A()[i * N + j] : e1.C()[i * N + (j - N)];
+    R[i * Q + j] = j < N ? A1[i * N + j] : C1[i * N + (j - N)];
   }
   for (int i = lane; i < N; i += TEAM) {
     G g = (G)(e1.b()[i]);
-    for (int l = 0; l < N; ++l) g = fma((G)(e1.C()[i * N + l]), (G)(e2.eta()[l]), g);
+    for (int l = 0; l < N; ++l) g = fma((G)(C1[i * N + l]), (G)(e2.eta()[l]), g);
     R[i * Q + 2 * N] = (double)g;
   }
   sync<TEAM>();
@@ -312,51 +359,35 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   // J2 z0, l0 = J2 z0 - eta2, w = eta2 - J2 b1 ; T1 = J2 A1
   for (int e = lane; e < N; e += TEAM) {
     G s = (G)(0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[e * N + l]), (G)(z0[l]), s);
+    for (int l = 0; l < N; ++l) s = fma((G)(J2[e * N + l]), (G)(z0[l]), s);
     J2z[e] = s;
     l0[e] = s - e2.eta()[e];
     G w = (G)(e2.eta()[e]);
-    for (int l = 0; l < N; ++l) w = fma((G)(-e2.J()[e * N + l]), (G)(e1.b()[l]), w);
+    for (int l = 0; l < N; ++l) w = fma((G)(-J2[e * N + l]), (G)(e1.b()[l]), w);
     wv[e] = w;
   }
-  for (int t = lane; t < N * N; t += TEAM) {
-    const int i = t / N, j = t % N;
-    G s = (G)(0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(e2.J()[i * N + l]), (G)(e1.A()[l * N + j]), s);
-    T1[t] = s;
-  }
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return J2[i * N + l]; }, [&](int l, int j) { return A1[l * N + j]; },
+                         [&](int i, int j, G v) { T1[i * N + j] = v; });
   sync<TEAM>();
-  // eta = K1^T w + eta1 ; J = K1^T T1 + J1 (upper, mirrored) ; b = A2 z0 + b2 ;
-  // A = A2 K1 ; zeta: one term per row i, summed over the team.  Each output
-  // kind has its own loop, so that a warp's lanes run the same code.
-  constexpr int NS = N * (N + 1) / 2;
+  // eta = K1^T w + eta1 ; b = A2 z0 + b2 ; W <- K1^T T1 ; A = A2 K1 ; zeta
   for (int t = lane; t < N; t += TEAM) {
     G s = (G)(e1.eta()[t]);
     for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + t]), (G)(wv[l]), s);
     out.eta()[t] = s;
     G sb = (G)(e2.b()[t]);
-    for (int l = 0; l < N; ++l) sb = fma((G)(e2.A()[t * N + l]), (G)(z0[l]), sb);
+    for (int l = 0; l < N; ++l) sb = fma((G)(A2[t * N + l]), (G)(z0[l]), sb);
     out.b()[t] = sb;
   }
-  for (int t = lane; t < NS; t += TEAM) {
-    int i, j;
-    upper_ij(N, t, i, j);
-    G s = (G)(e1.J()[i * N + j]);
-    for (int l = 0; l < N; ++l) s = fma((G)(R[l * Q + i]), (G)(T1[l * N + j]), s);
-    out.J()[i * N + j] = s;
-    out.J()[j * N + i] = s;
-  }
-  for (int t = lane; t < N * N; t += TEAM) {
-    const int i = t / N, j = t % N;
-    G s = (G)(0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[i * N + l]), (G)(R[l * Q + j]), s);
-    out.A()[t] = s;
-  }
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return R[l * Q + i]; }, [&](int l, int j) { return T1[l * N + j]; },
+                         [&](int i, int j, G v) { W[i * N + j] = v; });
+  double* oA = out.A();
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return A2[i * N + l]; }, [&](int l, int j) { return R[l * Q + j]; },
+                         [&](int i, int j, G v) { oA[i * N + j] = v; });
   {
     double zt = 0.0;
     for (int i = lane; i < N; i += TEAM) {
       G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e1.C()[i * N + l]), (G)(l0[l]), s);
+      for (int l = 0; l < N; ++l) s = fma((G)(C1[i * N + l]), (G)(l0[l]), s);
       zt = fma(0.5 * l0[i], s, zt);
       zt = fma(z0[i], fma(0.5, J2z[i], -e2.eta()[i]), zt);
     }
@@ -364,21 +395,23 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
     if (lane == 0) *out.zeta() = *e1.zeta() + *e2.zeta() + z;
   }
   sync<TEAM>();
-  // T1 = A2 MC1 ; then C = T1 A2^T + C2
+  // J = J1 + sym(K1^T T1) ; T1 <- A2 MC1
+  double* oJ = out.J();
   for (int e = lane; e < N * N; e += TEAM) {
     const int i = e / N, j = e % N;
-    G s = (G)(0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(e2.A()[i * N + l]), (G)(R[l * Q + N + j]), s);
-    T1[e] = s;
+    oJ[e] = e1.J()[e] + 0.5 * (W[i * N + j] + W[j * N + i]);
   }
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return A2[i * N + l]; },
+                         [&](int l, int j) { return R[l * Q + N + j]; }, [&](int i, int j, G v) { T1[i * N + j] = v; });
   sync<TEAM>();
-  for (int t = lane; t < NS; t += TEAM) {
-    int i, j;
-    upper_ij(N, t, i, j);
-    G s = (G)(e2.C()[i * N + j]);
-    for (int l = 0; l < N; ++l) s = fma((G)(T1[i * N + l]), (G)(e2.A()[j * N + l]), s);
-    out.C()[i * N + j] = s;
-    out.C()[j * N + i] = s;
+  // C = C2 + sym(T1 A2^T)
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return T1[i * N + l]; }, [&](int l, int j) { return A2[j * N + l]; },
+                         [&](int i, int j, G v) { W[i * N + j] = v; });
+  sync<TEAM>();
+  double* oC = out.C();
+  for (int e = lane; e < N * N; e += TEAM) {
+    const int i = e / N, j = e % N;
+    oC[e] = e2.C()[e] + 0.5 * (W[i * N + j] + W[j * N + i]);
   }
   sync<TEAM>();
 }
@@ -408,16 +441,15 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   double* Sz = T1 + N * N;
   double* l0 = Sz + N;
   double* wv = l0 + N;
-  for (int t = lane; t < N * N; t += TEAM) {
-    const int i = t / N, j = t % N;
-    G s = (G)((i == j) ? 1.0 : 0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(S2[l * N + j]), s);
-    W[t] = s;
-    R[i * Q + j] = e.A()[t];
-  }
+  const double* A = e.A();
+  const double* C = e.C();
+  // W = I + C S2 ; R = [A | b + C v2]
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return C[i * N + l]; }, [&](int l, int j) { return S2[l * N + j]; },
+                         [&](int i, int j, G v) { W[i * N + j] = (double)v + (i == j ? 1.0 : 0.0); });
+  for (int t = lane; t < N * N; t += TEAM) R[(t / N) * Q + (t % N)] = A[t];
   for (int i = lane; i < N; i += TEAM) {
     G g = (G)(e.b()[i]);
-    for (int l = 0; l < N; ++l) g = fma((G)(e.C()[i * N + l]), (G)(v2[l]), g);
+    for (int l = 0; l < N; ++l) g = fma((G)(C[i * N + l]), (G)(v2[l]), g);
     R[i * Q + N] = (double)g;
   }
   sync<TEAM>();
@@ -437,14 +469,9 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
     for (int l = 0; l < N; ++l) w = fma((G)(-S2[t * N + l]), (G)(e.b()[l]), w);
     wv[t] = w;
   }
-  for (int u = lane; u < N * N; u += TEAM) {
-    const int i = u / N, j = u % N;
-    G s = (G)(0.0);
-    for (int l = 0; l < N; ++l) s = fma((G)(S2[i * N + l]), (G)(e.A()[l * N + j]), s);
-    T1[u] = s;
-  }
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return S2[i * N + l]; }, [&](int l, int j) { return A[l * N + j]; },
+                         [&](int i, int j, G v) { T1[i * N + j] = v; });
   sync<TEAM>();
-  constexpr int NS = N * (N + 1) / 2;
   double* So = out;
   double* vo = out + N * N;
   for (int t = lane; t < N; t += TEAM) {
@@ -452,24 +479,24 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
     for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + t]), (G)(wv[l]), s);
     vo[t] = s;
   }
-  for (int t = lane; t < NS; t += TEAM) {
-    int i, j;
-    upper_ij(N, t, i, j);
-    G s = (G)(e.J()[i * N + j]);
-    for (int l = 0; l < N; ++l) s = fma((G)(Psi[l * N + i]), (G)(T1[l * N + j]), s);
-    So[i * N + j] = s;
-    So[j * N + i] = s;
-  }
+  // W <- Psi^T T1 ; S = J + sym(W)
+  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return Psi[l * N + i]; },
+                         [&](int l, int j) { return T1[l * N + j]; }, [&](int i, int j, G v) { W[i * N + j] = v; });
   {
     double zt = 0.0;
     for (int i = lane; i < N; i += TEAM) {
       G s = (G)(0.0);
-      for (int l = 0; l < N; ++l) s = fma((G)(e.C()[i * N + l]), (G)(l0[l]), s);
+      for (int l = 0; l < N; ++l) s = fma((G)(C[i * N + l]), (G)(l0[l]), s);
       zt = fma(0.5 * l0[i], s, zt);
       zt = fma(alpha[i], fma(0.5, Sz[i], -v2[i]), zt);
     }
     const double z = team_sum<TEAM>(lane, zt, fs);
     if (lane == 0) out[N * N + N] = *e.zeta() + zeta2 + z;
+  }
+  sync<TEAM>();
+  for (int t = lane; t < N * N; t += TEAM) {
+    const int i = t / N, j = t % N;
+    So[t] = e.J()[t] + 0.5 * (W[i * N + j] + W[j * N + i]);
   }
   sync<TEAM>();
 }
