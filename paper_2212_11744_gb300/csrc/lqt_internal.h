@@ -206,6 +206,10 @@ cudaError_t batch_prepare(const BatchDev& bd, cudaStream_t st);
 cudaError_t batch_build(const BatchDev& bd, const ElemPtrs& el, char* team_scratch, cudaStream_t st);
 cudaError_t batch_build_team(const BatchDev& bd, const ElemPtrs& el, double* gscratch, cudaStream_t st);
 cudaError_t batch_build_invariant(const BatchDev& bd, const ElemPtrs& el, double* tables, cudaStream_t st);
+void launch_inv_batch_build_warp(const BatchDev& bd, const double* tables, const ElemPtrs& out, cudaStream_t st);
+template <int N, int M>
+void launch_inv_master_team(int32_t K, int32_t B, const BatchProb* probs, const double* t, const Coefs& cf,
+                            double* tables, int64_t table_doubles, cudaStream_t st);
 template <int N, int M>
 void launch_inv_batch_build(const BatchDev& bd, const double* tables, const ElemPtrs& out, cudaStream_t st);
 

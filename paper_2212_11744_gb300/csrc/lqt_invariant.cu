@@ -155,6 +155,14 @@ __global__ void __launch_bounds__(128) inv_build_kernel(InvBuildArgs a) {
   inv_element<N, M>(a.cf, a.t, j, a.K, a.table, a.out, j);
 }
 
+// n = 64: one warp per sub-interval (inv_element_warp).
+template <int N, int M>
+__global__ void __launch_bounds__(32) inv_build_warp_kernel(InvBuildArgs a) {
+  extern __shared__ double sm[];
+  for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x)
+    inv_element_warp<N, M>(threadIdx.x, a.cf, a.t, j, a.K, a.table, a.out, j, sm);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -199,24 +207,50 @@ static cudaError_t inv_dispatch(int n, int M, const InvBuildArgs* a, const Batch
   }
 }
 
-// n = 16 is compiled for a factor width of 8 (m = 5..8) only.
-bool invariant_supported(int n, int M) { return (n <= 8 && M <= kInvMaxM) || (n == 16 && M == 8); }
+// n = 16 is compiled for a factor width of 8 (m = 5..8), n = 64 for its fixed
+// width 16.
+bool invariant_supported(int n, int M) {
+  return (n <= 8 && M <= kInvMaxM) || (n == 16 && M == 8) || (n == 64 && M == 16);
+}
 
 cudaError_t launch_build_invariant(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                                    double* table, cudaStream_t st) {
-  InvMasterArgs m{p.n, lay.M, p.K, 1, nullptr, p.t, cf.F.ptr, cf.Lt.ptr, cf.Q.ptr, table};
-  inv_master_kernel<<<1, 32, 0, st>>>(m);
-  count_launch();
   InvBuildArgs a{p.T, p.K, p.t, cf, table, out};
-  cudaError_t e = inv_dispatch(p.n, lay.M, &a, nullptr, table, out, st);
+  const int64_t td = inv_table_doubles(p.n, lay.M, p.K);
+  cudaError_t e = cudaSuccess;
+  if (p.n == 16) {
+    launch_inv_master_team<16, 8>(p.K, 1, nullptr, p.t, cf, table, td, st);
+    e = inv_dispatch(p.n, lay.M, &a, nullptr, table, out, st);
+  } else if (p.n == 64) {
+    launch_inv_master_team<64, 16>(p.K, 1, nullptr, p.t, cf, table, td, st);
+    const size_t smem = (4 * (2 * 64 + 1) + 16) * sizeof(double);
+    const int64_t grid = p.T < 152 * 32 ? p.T : 152 * 32;
+    inv_build_warp_kernel<64, 16><<<(unsigned)grid, 32, smem, st>>>(a);
+    count_launch();
+    e = cudaGetLastError();
+  } else {
+    InvMasterArgs m{p.n, lay.M, p.K, 1, nullptr, p.t, cf.F.ptr, cf.Lt.ptr, cf.Q.ptr, table};
+    inv_master_kernel<<<1, 32, 0, st>>>(m);
+    count_launch();
+    e = inv_dispatch(p.n, lay.M, &a, nullptr, table, out, st);
+  }
   if (e != cudaSuccess) return e;
   return launch_terminal_element(p, out, st);
 }
 
 cudaError_t batch_build_invariant(const BatchDev& bd, const ElemPtrs& el, double* tables, cudaStream_t st) {
-  InvMasterArgs m{bd.n, bd.M, bd.K, bd.B, bd.probs, nullptr, nullptr, nullptr, nullptr, tables};
-  inv_master_kernel<<<(unsigned)((bd.B + 127) / 128), 128, 0, st>>>(m);
-  count_launch();
+  const int64_t td = inv_table_doubles(bd.n, bd.M, bd.K);
+  if (bd.n == 16) {
+    launch_inv_master_team<16, 8>(bd.K, bd.B, bd.probs, nullptr, Coefs{}, tables, td, st);
+  } else if (bd.n == 64) {
+    launch_inv_master_team<64, 16>(bd.K, bd.B, bd.probs, nullptr, Coefs{}, tables, td, st);
+    launch_inv_batch_build_warp(bd, tables, el, st);
+    return cudaGetLastError();
+  } else {
+    InvMasterArgs m{bd.n, bd.M, bd.K, bd.B, bd.probs, nullptr, nullptr, nullptr, nullptr, tables};
+    inv_master_kernel<<<(unsigned)((bd.B + 127) / 128), 128, 0, st>>>(m);
+    count_launch();
+  }
   return inv_dispatch(bd.n, bd.M, nullptr, &bd, tables, el, st);
 }
 

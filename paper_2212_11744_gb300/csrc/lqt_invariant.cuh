@@ -17,11 +17,15 @@ constexpr int kInvMaxM = 8;
 // Table of one problem, in doubles: for RK4 step i (0..K-1) and stage st
 // (0..3, in evaluation order), AL (n x M), P (n x M), A (n x n), J (n x n);
 // then the element's A, C, J (full n x n each); then the integrator's own
-// working states (four A, C, J triples), kept here rather than in the thread's
-// stack.
+// working buffers, kept here rather than in a thread's stack.
 __host__ __device__ __forceinline__ int64_t inv_stage_doubles(int n, int M) { return 2 * n * M + 2 * n * n; }
+__host__ __device__ __forceinline__ int64_t inv_work_doubles(int n, int M) {
+  // four element records, AL, P, w, J F and n + 1 zeros (team integrator), which
+  // also covers the thread integrator's four A, C, J triples
+  return 4 * (3 * n * n + 2 * n + 1) + 2 * n * M + M + n * n + n + 1 + 8;
+}
 __host__ __device__ __forceinline__ int64_t inv_table_doubles(int n, int M, int K) {
-  return 4 * (int64_t)K * inv_stage_doubles(n, M) + 3 * n * n + 12 * n * n;
+  return 4 * (int64_t)K * inv_stage_doubles(n, M) + 3 * n * n + inv_work_doubles(n, M);
 }
 
 // ---------------------------------------------------------------------------
@@ -141,6 +145,101 @@ __device__ __forceinline__ void inv_element(const Coefs& cf, const double* t, in
     out.eta[g * N + i] = y.eta[i];
   }
   if (out.zeta) out.zeta[g] = y.zeta;
+}
+
+// The same (b, eta, zeta) integration with one warp per sub-interval (n = 64:
+// the stage matrices' rows spread over the lanes).  sm: 4 (2N+1) + M doubles.
+template <int N, int M>
+__device__ __forceinline__ void inv_element_warp(int lane, const Coefs& cf, const double* t, int64_t j, int32_t K,
+                                                 const double* __restrict__ table, const ElemPtrs& out, int64_t g,
+                                                 double* sm) {
+  constexpr int V = 2 * N + 1;  // b, eta, zeta
+  constexpr int64_t SD = 2 * N * M + 2 * N * N;
+  double* y = sm;
+  double* yn = y + V;
+  double* yt = yn + V;
+  double* k = yt + V;
+  double* w = k + V;
+  const double h = (t[j + 1] - t[j]) / K;
+  const double h0 = (t[1] - t[0]) / K;
+  if (lane == 0 && !(fabs(h - h0) <= 1e-12 * fabs(h0))) flag(kStatusNonUniform);
+  const double* F = cf.F.ptr;
+  const double* Lt = cf.Lt.ptr;
+  for (int e = lane; e < V; e += 32) y[e] = 0.0;
+  __syncwarp();
+  // k = f(yy) at stage record rec with samples c, qr
+  auto rhs = [&](const double* yy, const double* rec, const double* c, const double* qr) {
+    const double* AL = rec;
+    const double* P = rec + N * M;
+    const double* A = rec + 2 * N * M;
+    const double* J = A + N * N;
+    const double* eta = yy + N;
+    for (int a = lane; a < M; a += 32) {
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
+      w[a] = s;
+    }
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) {
+      double sb = 0.0, se = -qr[i];
+      for (int a = 0; a < M; ++a) {
+        sb = fma(-AL[i * M + a], w[a], sb);
+        se = fma(P[i * M + a], w[a], se);
+      }
+      for (int l = 0; l < N; ++l) se = fma(-F[l * N + i], eta[l], se);
+      if (c)
+        for (int l = 0; l < N; ++l) {
+          sb = fma(-A[i * N + l], c[l], sb);
+          se = fma(J[i * N + l], c[l], se);
+        }
+      k[i] = sb;
+      k[N + i] = se;
+    }
+    if (lane == 0) {
+      double z = -0.5 * qr[N];
+      for (int a = 0; a < M; ++a) z = fma(0.5 * w[a], w[a], z);
+      if (c)
+        for (int l = 0; l < N; ++l) z = fma(eta[l], c[l], z);
+      k[2 * N] = z;
+    }
+    __syncwarp();
+  };
+  auto axpy = [&](double* o, const double* base, double sc) {
+    for (int e = lane; e < V; e += 32) o[e] = fma(sc, k[e], base[e]);
+    __syncwarp();
+  };
+  for (int32_t i = K - 1; i >= 0; --i) {
+    const double* rec = table + 4 * (int64_t)i * SD;
+    const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
+    const double *c[3], *qr[3];
+    for (int q = 0; q < 3; ++q) {
+      c[q] = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, ps[q], K) * N : nullptr;
+      qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
+    }
+    rhs(y, rec, c[0], qr[0]);
+    axpy(yn, y, -h / 6.0);
+    axpy(yt, y, -0.5 * h);
+    rhs(yt, rec + SD, c[1], qr[1]);
+    axpy(yn, yn, -h / 3.0);
+    axpy(yt, y, -0.5 * h);
+    rhs(yt, rec + 2 * SD, c[1], qr[1]);
+    axpy(yn, yn, -h / 3.0);
+    axpy(yt, y, -h);
+    rhs(yt, rec + 3 * SD, c[2], qr[2]);
+    axpy(y, yn, -h / 6.0);
+  }
+  const double* fin = table + 4 * (int64_t)K * SD;
+  for (int e = lane; e < N * N; e += 32) {
+    out.A[g * N * N + e] = fin[e];
+    out.C[g * N * N + e] = fin[N * N + e];
+    out.J[g * N * N + e] = fin[2 * N * N + e];
+  }
+  for (int i = lane; i < N; i += 32) {
+    out.b[g * N + i] = y[i];
+    out.eta[g * N + i] = y[N + i];
+  }
+  if (lane == 0 && out.zeta) out.zeta[g] = y[2 * N];
+  __syncwarp();
 }
 
 }  // namespace lqt

@@ -690,6 +690,100 @@ void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, doub
   team_launch<N>(prefix_down_team_kernel<N>, tdiv(cnt, 2), prefix_slot_doubles<N>(), a, st);
 }
 
+// Time-invariant element build (lqt_invariant.cu), n = 16 and 64: the shared
+// A, C, J integration by one team per problem.  The full element is integrated
+// with zero r and c (the b, eta, zeta parts are unused here and cost O(n^2));
+// after every right-hand side the stage's AL = A Lt, P = J Lt (the RHS's own
+// scratch) and its input A, J are recorded into the problem's table, laid out
+// as the thread integrator's (inv_table_doubles).
+struct InvTeamMasterArgs {
+  int32_t K, B;
+  const BatchProb* probs;  // batch descriptors, or null (single problem: t, cf)
+  const double* t;
+  Coefs cf;
+  double* tables;
+  int64_t table_doubles;
+};
+
+template <int N, int M>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) inv_master_team_kernel(InvTeamMasterArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int SZ = Rec<N>::SIZE;
+  constexpr int64_t SD = 2 * N * M + 2 * N * N;
+  const int lane = threadIdx.x;
+  const int K = a.K;
+  for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
+    const Coefs& cf = a.probs ? a.probs[b].cf : a.cf;
+    const double* t = a.probs ? a.probs[b].t : a.t;
+    double* table = a.tables + b * a.table_doubles;
+    double* fin = table + 4 * (int64_t)K * SD;
+    double* yb = fin + 3 * N * N;
+    double* ynb = yb + SZ;
+    double* ytb = ynb + SZ;
+    double* kb = ytb + SZ;
+    double* AL = kb + SZ;
+    double* P = AL + N * M;
+    double* w = P + N * M;
+    double* JF = w + M;
+    double* zq = JF + N * N;  // N + 1 zeros: q = 0, rho = 0
+    const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
+    for (int e = lane; e < SZ; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
+    for (int e = lane; e <= N; e += TEAM) zq[e] = 0.0;
+    team::sync<TEAM>();
+    const double h = (t[1] - t[0]) / K;
+    const double* F = cf.F.ptr;
+    const double* Lt = cf.Lt.ptr;
+    const double* Q = cf.Q.ptr;
+    auto record = [&](double* rec, const Rec<N>& st) {
+      for (int e = lane; e < N * M; e += TEAM) {
+        rec[e] = AL[e];
+        rec[N * M + e] = P[e];
+      }
+      for (int e = lane; e < N * N; e += TEAM) {
+        rec[2 * N * M + e] = st.A()[e];
+        rec[2 * N * M + N * N + e] = st.J()[e];
+      }
+    };
+    for (int32_t i = K - 1; i >= 0; --i) {
+      double* rec = table + 4 * (int64_t)i * SD;
+      team::rhs<N, M, TEAM>(lane, y, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      record(rec, y);
+      team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
+      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      record(rec + SD, yt);
+      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
+      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      record(rec + 2 * SD, yt);
+      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
+      team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      record(rec + 3 * SD, yt);
+      team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
+    }
+    for (int e = lane; e < N * N; e += TEAM) {
+      fin[e] = y.A()[e];
+      fin[N * N + e] = y.C()[e];
+      fin[2 * N * N + e] = y.J()[e];
+    }
+    team::sync<TEAM>();
+  }
+}
+
+template <int N, int M>
+void launch_inv_master_team(int32_t K, int32_t B, const BatchProb* probs, const double* t, const Coefs& cf,
+                            double* tables, int64_t table_doubles, cudaStream_t st) {
+  InvTeamMasterArgs a{K, B, probs, t, cf, tables, table_doubles};
+  const unsigned grid = (unsigned)(B < TeamCfg<N>::SLOTS ? B : TeamCfg<N>::SLOTS);
+  inv_master_team_kernel<N, M><<<grid, TeamCfg<N>::TEAM, 0, st>>>(a);
+  count_launch();
+}
+template void launch_inv_master_team<16, 8>(int32_t, int32_t, const BatchProb*, const double*, const Coefs&, double*,
+                                            int64_t, cudaStream_t);
+template void launch_inv_master_team<64, 16>(int32_t, int32_t, const BatchProb*, const double*, const Coefs&,
+                                             double*, int64_t, cudaStream_t);
+
 #define LQT_TEAM_UPPER(N)                                                                                 \
   template void team_upper_reduce<N, double>(const double*, int64_t, double*, cudaStream_t);             \
   template void team_upper_reduce<N, float>(const double*, int64_t, double*, cudaStream_t);              \

@@ -45,9 +45,17 @@ __device__ __forceinline__ void upper_ij(int N, int t, int& i, int& j) {
 // team; the mapping depends only on (ROWS, COLS, TEAM), so two products of one
 // shape give every thread the same outputs (a thread may then accumulate
 // into its outputs without a barrier).  G is the product type.
+//
+// Shapes: a warp-sized team (n = 16, buffers in shared memory) gives each lane
+// one column and RB consecutive rows, so that consecutive lanes read
+// consecutive words of b and share rows of a (an operand read from several
+// rows of one column would hit one shared-memory bank: the row stride is a
+// multiple of 32 words); a larger team (n = 64, buffers in global memory) takes
+// square 4 x 4 blocks, which need the fewest loads per FMA.
 template <int ROWS, int COLS, int TEAM>
 struct GemmShape {
   static constexpr int cb() {
+    if (TEAM <= 32) return 1;
     int c = 1;
     while (c < 4 && COLS % (2 * c) == 0 && ROWS * COLS / (2 * c) >= TEAM) c *= 2;
     return c;
@@ -55,7 +63,8 @@ struct GemmShape {
   static constexpr int CB = cb();
   static constexpr int rb() {
     int r = 1;
-    while (r < 4 && ROWS % (2 * r) == 0 && ROWS * COLS / (CB * 2 * r) >= TEAM) r *= 2;
+    const int lim = TEAM <= 32 ? 8 : 4;
+    while (r < lim && ROWS % (2 * r) == 0 && ROWS * COLS / (CB * 2 * r) >= TEAM) r *= 2;
     return r;
   }
   static constexpr int RB = rb();

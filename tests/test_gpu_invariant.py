@@ -26,6 +26,9 @@ CASES = [
     ("batched_member_n8", lambda: W.batched_member(13, T=301, n=8)),
     ("batched_member_n16", lambda: W.batched_member(14, T=129, n=16)),
     ("T1", lambda: W.general_time_varying(3, 1, 3, T=1, K=4, seed=54, tf=0.5, modes=ALL_CONST)),
+    ("general_n16_m8_H_c", lambda: W.general_time_varying(16, 8, 16, T=33, K=2, seed=56, tf=0.8, modes=ALL_CONST)),
+    ("large_state_n64_T64", lambda: W.large_state_n64(T=64)),
+    ("large_state_n64_T129", lambda: W.large_state_n64(T=129)),
 ]
 IDS = [c[0] for c in CASES]
 
