@@ -468,114 +468,7 @@ __global__ void elem_adjoint_kernel(ElemAdjArgs a) {
 //   G = B J, beta = B eta
 //   dA = A G - A F, db = -A beta, dC = sym(-A B A^T), deta = -q - F^T eta + J beta,
 //   dJ = sym(-Q - J F - F^T J + J G), dz = -rho/2 + eta^T beta / 2
-__device__ void rhs_full(int n, const double* y, const double* F, const double* B, const double* Q, const double* q,
-                         double rho, double* k, double* t1, double* t2) {
-  const int nn = n * n;
-  FE Y = fe_view(n, const_cast<double*>(y)), K = fe_view(n, k);
-  double beta[AN];
-  mv(n, B, Y.eta, beta);
-  mm(n, B, Y.J, t1);                          // G
-  for (int i = 0; i < nn; ++i) t1[i] -= F[i];  // G - F
-  mm(n, Y.A, t1, K.A);
-  for (int i = 0; i < nn; ++i) t1[i] += F[i];  // G again
-  mv(n, Y.A, beta, K.b);
-  for (int i = 0; i < n; ++i) K.b[i] = -K.b[i];
-  mm(n, Y.A, B, t2);
-  mmt(n, t2, Y.A, K.C);
-  for (int i = 0; i < nn; ++i) K.C[i] = -K.C[i];
-  symm(n, K.C);
-  double Fe[AN], Jb[AN];
-  mtv(n, F, Y.eta, Fe);
-  mv(n, Y.J, beta, Jb);
-  for (int i = 0; i < n; ++i) K.eta[i] = -q[i] - Fe[i] + Jb[i];
-  mm(n, Y.J, F, t2);  // JF
-  double JG[AN * AN];
-  mm(n, Y.J, t1, JG);
-  for (int i = 0; i < n; ++i)
-    for (int c = 0; c < n; ++c) K.J[i * n + c] = -Q[i * n + c] - t2[i * n + c] - t2[c * n + i] + JG[i * n + c];
-  symm(n, K.J);
-  double z = -0.5 * rho;
-  for (int i = 0; i < n; ++i) z += 0.5 * Y.eta[i] * beta[i];
-  *K.z = z;
-}
-
-// Vector-Jacobian product of rhs_full at y with output adjoint kb (C, J parts
-// symmetrised first).  Accumulates into yb and the coefficient adjoints.
-__device__ void rhs_vjp(int n, const double* y, const double* F, const double* B, double* kb, double* yb,
-                        double* Fb, double* Bb, double* Qb, double* qb, double* rhob, double* t1, double* t2,
-                        double* t3) {
-  const int nn = n * n;
-  FE Y = fe_view(n, const_cast<double*>(y)), Kb = fe_view(n, kb), YB = fe_view(n, yb);
-  symm(n, Kb.C);
-  symm(n, Kb.J);
-  double beta[AN], betab[AN];
-  mv(n, B, Y.eta, beta);
-  for (int i = 0; i < n; ++i) betab[i] = 0.0;
-  // G = B J in t1
-  mm(n, B, Y.J, t1);
-  // dA = A (G - F):  Abar += Abar' (G - F)^T ; Gbar = A^T Abar' ; Fbar += -A^T Abar'
-  for (int i = 0; i < nn; ++i) t2[i] = t1[i] - F[i];
-  mmt(n, Kb.A, t2, t3);
-  for (int i = 0; i < nn; ++i) YB.A[i] += t3[i];
-  mtm(n, Y.A, Kb.A, t3);  // Gbar
-  for (int i = 0; i < nn; ++i) Fb[i] -= t3[i];
-  // G = B J: Bbar += Gbar J^T ; Jbar += B^T Gbar
-  mmt(n, t3, Y.J, t2);
-  for (int i = 0; i < nn; ++i) Bb[i] += t2[i];
-  mtm(n, B, t3, t2);
-  for (int i = 0; i < nn; ++i) YB.J[i] += t2[i];
-  // db = -A beta: Abar += -bbar' beta^T ; betabar += -A^T bbar'
-  for (int i = 0; i < n; ++i)
-    for (int c = 0; c < n; ++c) YB.A[i * n + c] -= Kb.b[i] * beta[c];
-  mtv(n, Y.A, Kb.b, t2);
-  for (int i = 0; i < n; ++i) betab[i] -= t2[i];
-  // dC = -A B A^T (Cbar' sym): Abar += -2 Cbar' A B ; Bbar += -A^T Cbar' A
-  mm(n, Kb.C, Y.A, t2);
-  mm(n, t2, B, t3);
-  for (int i = 0; i < nn; ++i) YB.A[i] -= 2.0 * t3[i];
-  mtm(n, Y.A, t2, t3);
-  for (int i = 0; i < nn; ++i) Bb[i] -= t3[i];
-  // deta = -q - F^T eta + J beta
-  for (int i = 0; i < n; ++i) qb[i] -= Kb.eta[i];
-  for (int i = 0; i < n; ++i)
-    for (int c = 0; c < n; ++c) {
-      Fb[i * n + c] -= Y.eta[i] * Kb.eta[c];
-      YB.J[i * n + c] += Kb.eta[i] * beta[c];
-    }
-  mv(n, F, Kb.eta, t2);
-  for (int i = 0; i < n; ++i) YB.eta[i] -= t2[i];
-  mtv(n, Y.J, Kb.eta, t2);
-  for (int i = 0; i < n; ++i) betab[i] += t2[i];
-  // dJ = -Q - J F - F^T J + J G  (Jbar' sym):
-  //   Qbar += -Jbar' ; Jbar += -Jbar' F^T - F Jbar' + Jbar' G^T ; Fbar += -J^T Jbar' - J Jbar'^T
-  //   Gbar2 = J^T Jbar' -> Bbar += Gbar2 J^T ; Jbar += B^T Gbar2
-  for (int i = 0; i < nn; ++i) Qb[i] -= Kb.J[i];
-  mmt(n, Kb.J, F, t2);
-  for (int i = 0; i < nn; ++i) YB.J[i] -= t2[i];
-  mm(n, F, Kb.J, t2);
-  for (int i = 0; i < nn; ++i) YB.J[i] -= t2[i];
-  mmt(n, Kb.J, t1, t2);
-  for (int i = 0; i < nn; ++i) YB.J[i] += t2[i];
-  mtm(n, Y.J, Kb.J, t3);  // Gbar2 = J^T Jbar'
-  for (int i = 0; i < nn; ++i) Fb[i] -= t3[i];
-  mmt(n, Y.J, Kb.J, t2);  // J Jbar'^T
-  for (int i = 0; i < nn; ++i) Fb[i] -= t2[i];
-  mmt(n, t3, Y.J, t2);
-  for (int i = 0; i < nn; ++i) Bb[i] += t2[i];
-  mtm(n, B, t3, t2);
-  for (int i = 0; i < nn; ++i) YB.J[i] += t2[i];
-  // dz = -rho/2 + eta^T beta / 2
-  *rhob -= 0.5 * *Kb.z;
-  for (int i = 0; i < n; ++i) {
-    YB.eta[i] += 0.5 * *Kb.z * beta[i];
-    betab[i] += 0.5 * *Kb.z * Y.eta[i];
-  }
-  // beta = B eta
-  for (int i = 0; i < n; ++i)
-    for (int c = 0; c < n; ++c) Bb[i * n + c] += betab[i] * Y.eta[c];
-  mtv(n, B, betab, t2);
-  for (int i = 0; i < n; ++i) YB.eta[i] += t2[i];
-}
+// and its vector-Jacobian product; one warp per sub-interval (below).
 
 struct RK4AdjArgs {
   int n, K, M;
@@ -587,137 +480,17 @@ struct RK4AdjArgs {
   const double* r;      // may be null
   int32_t r_mode;
   const double* ebar;   // [T+1][fe]
-  double* ys;           // scratch [T][K][fe]
+  double* ys;           // scratch [T][K][4][fe]: the stage inputs of every RK4 step
   // per-sub-interval partials
   double *pF, *pB, *pX;  // [T][n^2]
   double* pr;            // [T][2K+1][n] (per stage sample) or null
 };
 
-__global__ void __launch_bounds__(64) rk4_adjoint_kernel(RK4AdjArgs a) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.T) return;
-  const int n = a.n, nn = n * n, fs = fe_size(n), K = a.K, M = a.M;
-  const double h = (a.t[j + 1] - a.t[j]) / K;
-  // block-constant coefficients (F, B = Lt Lt^T, Q = X)
-  const double* F = a.cf.F.ptr + sample_index(a.cf.F.mode, j, 0, K) * nn;
-  const double* Lt = a.cf.Lt.ptr + sample_index(a.cf.Lt.mode, j, 0, K) * n * M;
-  const double* Q = a.X + sample_index(a.X_mode, j, 0, K) * nn;
-  double B[AN * AN];
-  for (int i = 0; i < n; ++i)
-    for (int c = 0; c < n; ++c) {
-      double s = 0.0;
-      for (int l = 0; l < M; ++l) s = fma(Lt[i * M + l], Lt[c * M + l], s);
-      B[i * n + c] = s;
-    }
-  auto qr_at = [&](int p) { return a.cf.qr.ptr + sample_index(a.cf.qr.mode, j, p, K) * (n + 1); };
-  double y[AS], k1[AS], k2[AS], k3[AS], y2[AS], y3[AS], y4[AS], t1[AN * AN], t2[AN * AN], t3[AN * AN];
-  // forward, storing the state before every step
-  for (int i = 0; i < fs; ++i) y[i] = 0.0;
-  for (int i = 0; i < n; ++i) y[i * n + i] = 1.0;
-  double* ysj = a.ys + j * (int64_t)K * fs;
-  for (int i = K - 1; i >= 0; --i) {
-    for (int e = 0; e < fs; ++e) ysj[i * fs + e] = y[e];
-    const double* q1 = qr_at(2 * i + 2);
-    const double* q2 = qr_at(2 * i + 1);
-    const double* q3 = qr_at(2 * i);
-    rhs_full(n, y, F, B, Q, q1, q1[n], k1, t1, t2);
-    for (int e = 0; e < fs; ++e) y2[e] = y[e] - 0.5 * h * k1[e];
-    rhs_full(n, y2, F, B, Q, q2, q2[n], k2, t1, t2);
-    for (int e = 0; e < fs; ++e) y3[e] = y[e] - 0.5 * h * k2[e];
-    rhs_full(n, y3, F, B, Q, q2, q2[n], k3, t1, t2);
-    for (int e = 0; e < fs; ++e) y4[e] = y[e] - h * k3[e];
-    rhs_full(n, y4, F, B, Q, q3, q3[n], y2, t1, t2);  // k4 into y2
-    for (int e = 0; e < fs; ++e) y[e] = y[e] - (h / 6.0) * (k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + y2[e]);
-  }
-  // adjoint
-  double yb[AS], kb1[AS], kb2[AS], kb3[AS], kb4[AS];
-  double Fb[AN * AN], Bb[AN * AN], Qb[AN * AN];
-  double qb[17 * AN], rhob[17];
-  for (int i = 0; i < nn; ++i) { Fb[i] = 0.0; Bb[i] = 0.0; Qb[i] = 0.0; }
-  for (int i = 0; i < (2 * K + 1) * n; ++i) qb[i] = 0.0;
-  for (int i = 0; i <= 2 * K; ++i) rhob[i] = 0.0;
-  const double* eb = a.ebar + j * fs;
-  for (int e = 0; e < fs; ++e) yb[e] = eb[e];
-  for (int i = 0; i < K; ++i) {
-    for (int e = 0; e < fs; ++e) y[e] = ysj[i * fs + e];
-    const int p1 = 2 * i + 2, p2 = 2 * i + 1, p3 = 2 * i;
-    const double* q1 = qr_at(p1);
-    const double* q2 = qr_at(p2);
-    const double* q3 = qr_at(p3);
-    rhs_full(n, y, F, B, Q, q1, q1[n], k1, t1, t2);
-    for (int e = 0; e < fs; ++e) y2[e] = y[e] - 0.5 * h * k1[e];
-    rhs_full(n, y2, F, B, Q, q2, q2[n], k2, t1, t2);
-    for (int e = 0; e < fs; ++e) y3[e] = y[e] - 0.5 * h * k2[e];
-    rhs_full(n, y3, F, B, Q, q2, q2[n], k3, t1, t2);
-    for (int e = 0; e < fs; ++e) y4[e] = y[e] - h * k3[e];
-    // y_new = y - h/6 (k1 + 2 k2 + 2 k3 + k4)
-    for (int e = 0; e < fs; ++e) {
-      kb1[e] = -(h / 6.0) * yb[e];
-      kb2[e] = -(h / 3.0) * yb[e];
-      kb3[e] = -(h / 3.0) * yb[e];
-      kb4[e] = -(h / 6.0) * yb[e];
-    }
-    // stage 4 at y4 (sample p3): ybar += y4bar, k3bar += -h y4bar
-    for (int e = 0; e < fs; ++e) k1[e] = 0.0;  // reuse k1 as the stage-input adjoint accumulator
-    rhs_vjp(n, y4, F, B, kb4, k1, Fb, Bb, Qb, qb + p3 * n, rhob + p3, t1, t2, t3);
-    for (int e = 0; e < fs; ++e) {
-      yb[e] += k1[e];
-      kb3[e] += -h * k1[e];
-    }
-    for (int e = 0; e < fs; ++e) k1[e] = 0.0;
-    rhs_vjp(n, y3, F, B, kb3, k1, Fb, Bb, Qb, qb + p2 * n, rhob + p2, t1, t2, t3);
-    for (int e = 0; e < fs; ++e) {
-      yb[e] += k1[e];
-      kb2[e] += -0.5 * h * k1[e];
-    }
-    for (int e = 0; e < fs; ++e) k1[e] = 0.0;
-    rhs_vjp(n, y2, F, B, kb2, k1, Fb, Bb, Qb, qb + p2 * n, rhob + p2, t1, t2, t3);
-    for (int e = 0; e < fs; ++e) {
-      yb[e] += k1[e];
-      kb1[e] += -0.5 * h * k1[e];
-    }
-    for (int e = 0; e < fs; ++e) k1[e] = 0.0;
-    rhs_vjp(n, y, F, B, kb1, k1, Fb, Bb, Qb, qb + p1 * n, rhob + p1, t1, t2, t3);
-    for (int e = 0; e < fs; ++e) yb[e] += k1[e];
-  }
-  // coefficient adjoints of this sub-interval:
-  //   Xbar = sym(Qbar) + sum_p (qbar_p r_p^T + rhobar_p r_p r_p^T)
-  //   rbar_p = X^T qbar_p + rhobar_p (X + X^T) r_p
-  double* oF = a.pF + j * nn;
-  double* oB = a.pB + j * nn;
-  double* oX = a.pX + j * nn;
-  for (int i = 0; i < nn; ++i) {
-    oF[i] = Fb[i];
-    oB[i] = Bb[i];
-  }
-  for (int i = 0; i < n; ++i)
-    for (int c = 0; c < n; ++c) oX[i * n + c] = 0.5 * (Qb[i * n + c] + Qb[c * n + i]);
-  for (int p = 0; p <= 2 * K; ++p) {
-    const double* rp = a.r ? a.r + sample_index(a.r_mode, j, p, K) * n : nullptr;
-    double* orp = a.pr ? a.pr + (j * (2 * K + 1) + p) * n : nullptr;
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int l = 0; l < n; ++l) s = fma(Q[l * n + i], qb[p * n + l], s);
-      if (rp)
-        for (int l = 0; l < n; ++l) s += rhob[p] * (Q[i * n + l] + Q[l * n + i]) * rp[l];
-      if (orp) orp[i] = s;
-    }
-    if (rp)
-      for (int i = 0; i < n; ++i)
-        for (int c = 0; c < n; ++c) oX[i * n + c] += qb[p * n + i] * rp[c] + rhob[p] * rp[i] * rp[c];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// 5'. the same discrete RK4 adjoint with one warp per sub-interval
-// ---------------------------------------------------------------------------
-//
-// One thread per sub-interval leaves the FP64 pipe mostly idle at the adjoint
-// workload's size (2^14 sub-intervals = 512 warps for 608 sub-partitions, each
-// a long dependent chain with its matrices in local memory).  Here a warp owns
-// a sub-interval: every matrix product spreads its n^2 outputs over the 32
-// lanes, all buffers live in shared memory, and there are 32x more warps.  The
-// arithmetic is the thread version's, step for step.
+// One warp per sub-interval: one thread per sub-interval would leave the FP64
+// pipe mostly idle at the adjoint workload's size (2^14 sub-intervals = 512
+// warps for 608 sub-partitions, each a long dependent chain with its matrices
+// in local memory).  A warp owns a sub-interval: every matrix product spreads
+// its n^2 outputs over the 32 lanes and all buffers live in shared memory.
 
 namespace warp {
 
@@ -796,7 +569,7 @@ struct Tmp {
   double *t1, *t2, *t3, *JG, *beta, *betab, *v1, *v2;
 };
 
-// k = f(y): the thread version's rhs_full, lanes over entries.
+// k = f(y), lanes over entries.
 __device__ void rhs_full(int lane, int n, const double* y, const double* F, const double* B, const double* Q,
                          const double* q, double rho, double* k, const Tmp& t) {
   const int nn = n * n;
@@ -835,9 +608,10 @@ __device__ void rhs_full(int lane, int n, const double* y, const double* F, cons
   sync();
 }
 
-// The thread version's rhs_vjp, lanes over entries; Fb, Bb, Qb accumulate
-// entry-wise (each lane owns the same entries throughout), qb, rhob by lanes
-// < n and lane 0.
+// Vector-Jacobian product of rhs_full at y with output adjoint kb (its C, J
+// parts symmetrised first), accumulated into yb and the coefficient adjoints;
+// lanes over entries: Fb, Bb, Qb accumulate entry-wise (each lane owns the same
+// entries throughout), qb, rhob by lanes < n and lane 0.
 __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const double* B, double* kb, double* yb,
                         double* Fb, double* Bb, double* Qb, double* qb, double* rhob, const Tmp& t) {
   const int nn = n * n;
@@ -980,21 +754,33 @@ __global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
     for (int e = lane; e < fs; e += 32) y[e] = (e < nn && e % (n + 1) == 0) ? 1.0 : 0.0;
     warp::sync();
     auto qr_at = [&](int p) { return a.cf.qr.ptr + sample_index(a.cf.qr.mode, j, p, K) * (n + 1); };
-    double* ysj = a.ys + j * (int64_t)K * fs;
-    // forward, storing the state before every step
+    // the four stage inputs of every step, stored by the forward pass for the
+    // reverse sweep (instead of recomputing them there)
+    double* ysj = a.ys + j * (int64_t)K * 4 * fs;
+    // forward
     for (int i = K - 1; i >= 0; --i) {
-      for (int e = lane; e < fs; e += 32) ysj[i * fs + e] = y[e];
+      double* st = ysj + (int64_t)i * 4 * fs;
       const double* q1 = qr_at(2 * i + 2);
       const double* q2 = qr_at(2 * i + 1);
       const double* q3 = qr_at(2 * i);
       warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], k1, tmp);
-      for (int e = lane; e < fs; e += 32) y2[e] = y[e] - 0.5 * h * k1[e];
+      for (int e = lane; e < fs; e += 32) {
+        st[e] = y[e];
+        y2[e] = y[e] - 0.5 * h * k1[e];
+        st[fs + e] = y2[e];
+      }
       warp::sync();
       warp::rhs_full(lane, n, y2, F, B, Q, q2, q2[n], k2, tmp);
-      for (int e = lane; e < fs; e += 32) y3[e] = y[e] - 0.5 * h * k2[e];
+      for (int e = lane; e < fs; e += 32) {
+        y3[e] = y[e] - 0.5 * h * k2[e];
+        st[2 * fs + e] = y3[e];
+      }
       warp::sync();
       warp::rhs_full(lane, n, y3, F, B, Q, q2, q2[n], k3, tmp);
-      for (int e = lane; e < fs; e += 32) y4[e] = y[e] - h * k3[e];
+      for (int e = lane; e < fs; e += 32) {
+        y4[e] = y[e] - h * k3[e];
+        st[3 * fs + e] = y4[e];
+      }
       warp::sync();
       warp::rhs_full(lane, n, y4, F, B, Q, q3, q3[n], y2, tmp);  // k4 into y2
       for (int e = lane; e < fs; e += 32) y[e] = y[e] - (h / 6.0) * (k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + y2[e]);
@@ -1005,21 +791,15 @@ __global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
     for (int e = lane; e < fs; e += 32) yb[e] = eb[e];
     warp::sync();
     for (int i = 0; i < K; ++i) {
-      for (int e = lane; e < fs; e += 32) y[e] = ysj[i * fs + e];
+      const double* st = ysj + (int64_t)i * 4 * fs;
+      for (int e = lane; e < fs; e += 32) {
+        y[e] = st[e];
+        y2[e] = st[fs + e];
+        y3[e] = st[2 * fs + e];
+        y4[e] = st[3 * fs + e];
+      }
       warp::sync();
       const int p1 = 2 * i + 2, p2 = 2 * i + 1, p3 = 2 * i;
-      const double* q1 = qr_at(p1);
-      const double* q2 = qr_at(p2);
-      const double* q3 = qr_at(p3);
-      warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], k1, tmp);
-      for (int e = lane; e < fs; e += 32) y2[e] = y[e] - 0.5 * h * k1[e];
-      warp::sync();
-      warp::rhs_full(lane, n, y2, F, B, Q, q2, q2[n], k2, tmp);
-      for (int e = lane; e < fs; e += 32) y3[e] = y[e] - 0.5 * h * k2[e];
-      warp::sync();
-      warp::rhs_full(lane, n, y3, F, B, Q, q2, q2[n], k3, tmp);
-      for (int e = lane; e < fs; e += 32) y4[e] = y[e] - h * k3[e];
-      warp::sync();
       // y_new = y - h/6 (k1 + 2 k2 + 2 k3 + k4): stage output adjoints
       // kb4 = -h/6 yb, kb3 = -h/3 yb (+ -h acc4), kb2 = -h/3 yb (+ -h/2 acc3),
       // kb1 = -h/6 yb (+ -h/2 acc2)
@@ -1054,7 +834,9 @@ __global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
       for (int e = lane; e < fs; e += 32) yb[e] += acc[e];
       warp::sync();
     }
-    // coefficient adjoints of this sub-interval (as in the thread version)
+    // coefficient adjoints of this sub-interval:
+    //   Xbar = sym(Qbar) + sum_p (qbar_p r_p^T + rhobar_p r_p r_p^T)
+    //   rbar_p = X^T qbar_p + rhobar_p (X + X^T) r_p
     double* oF = a.pF + j * nn;
     double* oB = a.pB + j * nn;
     double* oX = a.pX + j * nn;
@@ -1250,7 +1032,7 @@ static BackwardPlan backward_plan(const lqt_problem& p, const Layout& L, size_t 
     off = al(off + c);
   }
   b.ebar = off; off = al(off + T1 * fs * 8);
-  b.ys = off; off = al(off + T * K * fs * 8);
+  b.ys = off; off = al(off + T * K * 4 * fs * 8);
   b.pF = off; off = al(off + T * n * n * 8);
   b.pB = off; off = al(off + T * n * n * 8);
   b.pX = off; off = al(off + T * n * n * 8);

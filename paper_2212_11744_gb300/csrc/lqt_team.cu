@@ -52,7 +52,7 @@ struct TeamCfg<64> {
 
 // Doubles of per-slot scratch of each kernel.
 template <int N, int M>
-constexpr int build_slot_doubles() { return 4 * Rec<N>::SIZE + 2 * N * M + M + N * N + 8; }
+constexpr int build_slot_doubles() { return 4 * Rec<N>::SIZE + 2 * N * M + M + 8; }
 template <int N>
 constexpr int reduce_slot_doubles() { return 2 * Rec<N>::SIZE + team::combine_scratch_doubles<N>() + 8; }
 template <int N>
@@ -101,8 +101,7 @@ struct TeamBuildArgs {
 // yb; the other buffers are scratch.
 template <int N, int M>
 __device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64_t j, int32_t K, double* yb,
-                               double* ynb, double* ytb, double* kb, double* AL, double* P, double* w,
-                               double* JF) {
+                               double* ynb, double* ytb, double* kb, double* AL, double* P, double* w) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
   const double h = (t[j + 1] - t[j]) / K;
@@ -118,16 +117,16 @@ __device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64
       Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * N * N;
       qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
     }
-    team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w, JF);
+    team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w);
     team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
     team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w, JF);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
     team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
     team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w, JF);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
     team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
     team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
-    team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w, JF);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w);
     team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
   }
 }
@@ -145,9 +144,8 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_kernel(TeamBuildA
   double* AL = kb + Rec<N>::SIZE;
   double* P = AL + N * M;
   double* w = P + N * M;
-  double* JF = w + M;
   for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
-    team_build_one<N, M>(lane, a.cf, a.t, j, a.K, yb, ynb, ytb, kb, AL, P, w, JF);
+    team_build_one<N, M>(lane, a.cf, a.t, j, a.K, yb, ynb, ytb, kb, AL, P, w);
     double zz = 0.0;
     Rec<N> dst = Rec<N>::pub(a.out, j, &zz);
     team::copy_rec<N, TEAM>(lane, dst, Rec<N>::packed(yb));
@@ -169,13 +167,12 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) batch_build_team_kernel(Batc
   double* AL = kb + Rec<N>::SIZE;
   double* P = AL + N * M;
   double* w = P + N * M;
-  double* JF = w + M;
   for (int64_t g = blockIdx.x; g < bd.total; g += gridDim.x) {
     const int32_t b = batch_find(bd.off, bd.B, g);
     const BatchProb& pb = bd.probs[b];
     const int64_t j = g - pb.off;
     if (j < pb.T) {
-      team_build_one<N, M>(lane, pb.cf, pb.t, j, bd.K, yb, ynb, ytb, kb, AL, P, w, JF);
+      team_build_one<N, M>(lane, pb.cf, pb.t, j, bd.K, yb, ynb, ytb, kb, AL, P, w);
     } else {
       const Rec<N> y = Rec<N>::packed(yb);
       for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = 0.0;
@@ -746,19 +743,19 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) inv_master_team_kernel(InvTe
     };
     for (int32_t i = K - 1; i >= 0; --i) {
       double* rec = table + 4 * (int64_t)i * SD;
-      team::rhs<N, M, TEAM>(lane, y, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      team::rhs<N, M, TEAM>(lane, y, k, F, nullptr, Lt, Q, zq, AL, P, w);
       record(rec, y);
       team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
       team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w);
       record(rec + SD, yt);
       team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
       team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w);
       record(rec + 2 * SD, yt);
       team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
       team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, JF);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w);
       record(rec + 3 * SD, yt);
       team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
     }

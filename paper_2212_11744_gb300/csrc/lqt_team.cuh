@@ -127,50 +127,43 @@ struct Rec {
 // element build right-hand side (factor form, see build_kernel)
 // ---------------------------------------------------------------------------
 
-// k = f(y); scratch: AL, P (N x M), w (M), JF (N x N).
+// k = f(y); scratch: AL, P (N x M), w (M).  Plain loops, one output per
+// thread at a time, with the symmetric C, J formed on their upper triangles:
+// measured faster here than the register-blocked team products (the products
+// are thin, inner length M, and the triangles halve the C and J work).
 template <int N, int M, int TEAM>
 __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
                     const double* __restrict__ Lt, const double* __restrict__ Q, const double* __restrict__ qr,
-                    double* AL, double* P, double* w, double* JF) {
+                    double* AL, double* P, double* w) {
   const double* A = y.A();
   const double* J = y.J();
   const double* eta = y.eta();
-  double* kA = k.A();
-  double* kC = k.C();
-  double* kJ = k.J();
-  // AL = A Lt, P = J Lt, JF = J F, w = Lt^T eta
-  gemm<N, M, N, TEAM, double>(lane, [&](int i, int l) { return A[i * N + l]; },
-                              [&](int l, int j) { return Lt[l * M + j]; },
-                              [&](int i, int j, double v) { AL[i * M + j] = v; });
-  gemm<N, M, N, TEAM, double>(lane, [&](int i, int l) { return J[i * N + l]; },
-                              [&](int l, int j) { return Lt[l * M + j]; },
-                              [&](int i, int j, double v) { P[i * M + j] = v; });
-  gemm<N, N, N, TEAM, double>(lane, [&](int i, int l) { return J[i * N + l]; },
-                              [&](int l, int j) { return F[l * N + j]; },
-                              [&](int i, int j, double v) { JF[i * N + j] = v; });
+  // One loop per output kind (a warp's lanes then run the same code).
+  for (int e = lane; e < N * M; e += TEAM) {
+    const int i = e / M, a = e % M;
+    double s1 = 0.0, s2 = 0.0;
+    for (int l = 0; l < N; ++l) {
+      s1 = fma(A[i * N + l], Lt[l * M + a], s1);
+      s2 = fma(J[i * N + l], Lt[l * M + a], s2);
+    }
+    AL[e] = s1;
+    P[e] = s2;
+  }
   for (int a = lane; a < M; a += TEAM) {
     double s = 0.0;
     for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
     w[a] = s;
   }
-  // dA = -A F (first pass) ... + AL P^T (same outputs per thread, see gemm)
-  gemm<N, N, N, TEAM, double>(lane, [&](int i, int l) { return A[i * N + l]; },
-                              [&](int l, int j) { return F[l * N + j]; },
-                              [&](int i, int j, double v) { kA[i * N + j] = -v; });
   sync<TEAM>();
-  gemm<N, N, M, TEAM, double>(lane, [&](int i, int l) { return AL[i * M + l]; },
-                              [&](int l, int j) { return P[j * M + l]; },
-                              [&](int i, int j, double v) { kA[i * N + j] += v; });
-  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (both exactly symmetric:
-  // entry (i, j) and (j, i) run the same products in the same order)
-  gemm<N, N, M, TEAM, double>(lane, [&](int i, int l) { return AL[i * M + l]; },
-                              [&](int l, int j) { return AL[j * M + l]; },
-                              [&](int i, int j, double v) { kC[i * N + j] = -v; });
-  gemm<N, N, M, TEAM, double>(lane, [&](int i, int l) { return P[i * M + l]; },
-                              [&](int l, int j) { return P[j * M + l]; },
-                              [&](int i, int j, double v) {
-                                kJ[i * N + j] = -Q[i * N + j] - JF[i * N + j] - JF[j * N + i] + v;
-                              });
+  constexpr int NS = N * (N + 1) / 2;
+  // dA = AL P^T - A F
+  for (int t = lane; t < N * N; t += TEAM) {
+    const int i = t / N, j = t % N;
+    double s = 0.0;
+    for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
+    for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
+    k.A()[t] = s;
+  }
   // db = -AL w - A c ; deta = -q - F^T eta + J c + P w
   for (int t = lane; t < N; t += TEAM) {
     double s = 0.0, se = -qr[t];
@@ -186,6 +179,24 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
       }
     k.b()[t] = s;
     k.eta()[t] = se;
+  }
+  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored)
+  for (int t = lane; t < NS; t += TEAM) {
+    int i, j;
+    upper_ij(N, t, i, j);
+    double sc = 0.0, sj = -Q[i * N + j];
+    for (int a = 0; a < M; ++a) {
+      sc = fma(-AL[i * M + a], AL[j * M + a], sc);
+      sj = fma(P[i * M + a], P[j * M + a], sj);
+    }
+    for (int l = 0; l < N; ++l) {
+      sj = fma(-J[i * N + l], F[l * N + j], sj);
+      sj = fma(-J[j * N + l], F[l * N + i], sj);
+    }
+    k.C()[i * N + j] = sc;
+    k.C()[j * N + i] = sc;
+    k.J()[i * N + j] = sj;
+    k.J()[j * N + i] = sj;
   }
   if (lane == 0) {  // dzeta (O(M + N))
     double z = -0.5 * qr[N];

@@ -193,3 +193,46 @@ def test_config4_gradients_full_size_fd_and_reverse_mode():
         # central difference of this loss (~34) carries ~1e-7 absolute rounding
         worst = max(worst, abs(an - fd) / max(abs(fd), 0.05))
     assert worst <= 1e-5, worst
+
+
+def test_backward_full_size_against_gpu_central_differences():
+    """n = 8, T = 2^14 (the adjoint workload): the gradient's directional
+    derivative along 4 seeded directions in (diag X, F, r) against central
+    differences of the GPU's own forward solve (h = 1e-6, rel 1e-5, the
+    denominator floored at 0.05 as in the oracle finite-difference test)."""
+    import paper_2212_11744_gb300 as lqt
+    p = W.differentiable_n8(T=1 << 14)
+    xt = torch.tensor(p.extra["x_target"], device="cuda")
+    dp = lqt.DeviceProblem(p)
+    fwd = lqt.lqt_solve(dp)
+    gx = torch.zeros(p.T + 1, p.n, dtype=torch.float64, device="cuda")
+    gx[-1] = 2.0 * (fwd["x"][-1] - xt)
+    g = lqt.lqt_backward(dp, fwd, gx=gx, g_cost=1.0)
+    torch.cuda.synchronize()
+    assert lqt.lqt_get_status() == 0
+    for k, v in g.items():
+        assert bool(torch.isfinite(v).all()), k
+
+    def loss(dq, dF, dr, h):
+        q = p.X.values[0].copy(); q[np.diag_indices(p.n)] += h * dq
+        pp = W.differentiable_n8(T=p.T)
+        pp.X.values[0] = q
+        pp.F.values[0] = p.F.values[0] + h * dF
+        pp.r.values[:] = p.r.values + h * dr
+        o = lqt.lqt_solve(lqt.DeviceProblem(pp))
+        return float(o["cost"][0]) + float(((o["x"][-1] - xt) ** 2).sum())
+
+    rng = np.random.default_rng(77)
+    worst = 0.0
+    for _ in range(4):
+        dq, dF = rng.standard_normal(p.n), rng.standard_normal((p.n, p.n))
+        dr = np.zeros_like(p.r.values)
+        rows = rng.choice(p.T, 64, replace=False)
+        dr[rows] = rng.standard_normal((64, p.n))
+        nrm = np.sqrt((dq ** 2).sum() + (dF ** 2).sum() + (dr ** 2).sum())
+        dq, dF, dr = dq / nrm, dF / nrm, dr / nrm
+        fd = (loss(dq, dF, dr, 1e-6) - loss(dq, dF, dr, -1e-6)) / 2e-6
+        an = float((np.diag(g["X"][0].cpu().numpy()) * dq).sum() + (g["F"][0].cpu().numpy() * dF).sum() +
+                   (g["r"].cpu().numpy() * dr).sum())
+        worst = max(worst, abs(an - fd) / max(abs(fd), 0.05))
+    assert worst <= 1e-5, worst
