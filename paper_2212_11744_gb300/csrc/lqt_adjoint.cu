@@ -277,103 +277,110 @@ __global__ void map_adjoint_kernel(MapAdjArgs a) {
 // ---------------------------------------------------------------------------
 
 // Composite of maps (P, D) over a group: (P2 P1, P2 D1 P2^T + D2).  Map k is
-// (P_k from maps, D_{k+1}).  Level 0 reads P from the optimal-state maps.
-__device__ void load_P(int n, const double* mapk, double* P) {
-  const int n1 = n + 1;
-  for (int i = 0; i < n; ++i) {
-    for (int c = 0; c < n; ++c) P[i * n1 + c] = mapk[i * n + c];
-    P[i * n1 + n] = mapk[n * n + i];
+// (P_k from the optimal-state maps, D_{k+1}).
+//
+// Congruence-scan levels, one warp per group: the n1^2 entries of every
+// congruence over the lanes, buffers in shared memory (a thread per group
+// leaves the levels latency-bound: 2^13 threads at the first level of
+// T = 2^14, far fewer above, each a chain of ~2k dependent FP64 operations).
+// Level maps are stored as [P (n1^2) | D (n1^2)].
+__device__ __forceinline__ void wcongruence(int lane, int n1, const double* P, const double* X, const double* D,
+                                            double* y, double* tmp) {
+  const int m2 = n1 * n1;
+  for (int e = lane; e < m2; e += 32) {
+    const int i = e / n1, c = e % n1;
+    double s = 0.0;
+    for (int l = 0; l < n1; ++l) s = fma(P[i * n1 + l], X[l * n1 + c], s);
+    tmp[e] = s;
   }
-  for (int c = 0; c < n; ++c) P[n * n1 + c] = 0.0;
-  P[n * n1 + n] = 1.0;
+  __syncwarp();
+  for (int e = lane; e < m2; e += 32) {
+    const int i = e / n1, c = e % n1;
+    double s = D ? D[e] : 0.0;
+    for (int l = 0; l < n1; ++l) s = fma(tmp[i * n1 + l], P[c * n1 + l], s);
+    y[e] = s;
+  }
+  __syncwarp();
 }
 
-// y = P X P^T + D  (all n1 x n1; tmp n1 x n1)
-__device__ void congruence(int n1, const double* P, const double* X, const double* D, double* y, double* tmp) {
-  for (int i = 0; i < n1; ++i)
-    for (int c = 0; c < n1; ++c) {
-      double s = 0.0;
-      for (int l = 0; l < n1; ++l) s = fma(P[i * n1 + l], X[l * n1 + c], s);
-      tmp[i * n1 + c] = s;
-    }
-  for (int i = 0; i < n1; ++i)
-    for (int c = 0; c < n1; ++c) {
-      double s = D ? D[i * n1 + c] : 0.0;
-      for (int l = 0; l < n1; ++l) s = fma(tmp[i * n1 + l], P[c * n1 + l], s);
-      y[i * n1 + c] = s;
-    }
-}
-
-// Level maps stored as [P (n1^2) | D (n1^2)].
-__global__ void cong_reduce_kernel(int n, int64_t cnt, int G, int level0, const double* __restrict__ maps0,
-                                   const double* __restrict__ D, const double* __restrict__ in,
-                                   double* __restrict__ out) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t first = g * G;
-  if (first >= cnt) return;
-  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+__device__ __forceinline__ void wload_level(int lane, int n, int level0, const double* maps0, const double* D,
+                                            const double* in, int64_t k, double* Pm, double* Dm) {
   const int n1 = n + 1, m2 = n1 * n1;
-  double P[AH * AH], Dc[AH * AH], Pk[AH * AH], Dk[AH * AH], t1[AH * AH], t2[AH * AH];
-  auto load = [&](int64_t k, double* Pm, double* Dm) {
+  for (int e = lane; e < m2; e += 32) {
     if (level0) {
-      load_P(n, maps0 + k * (n * n + n), Pm);
-      for (int i = 0; i < m2; ++i) Dm[i] = D[(k + 1) * m2 + i];
+      const int i = e / n1, c = e % n1;
+      const double* mapk = maps0 + k * (n * n + n);
+      Pm[e] = i < n ? (c < n ? mapk[i * n + c] : mapk[n * n + i]) : (c == n ? 1.0 : 0.0);
+      Dm[e] = D[(k + 1) * m2 + e];
     } else {
-      for (int i = 0; i < m2; ++i) {
-        Pm[i] = in[k * 2 * m2 + i];
-        Dm[i] = in[k * 2 * m2 + m2 + i];
-      }
+      Pm[e] = in[k * 2 * m2 + e];
+      Dm[e] = in[k * 2 * m2 + m2 + e];
     }
-  };
-  load(first, P, Dc);
-  for (int64_t k = first + 1; k <= last; ++k) {
-    load(k, Pk, Dk);
-    // (Pk, Dk) o (P, Dc) = (Pk P, Pk Dc Pk^T + Dk)
-    congruence(n1, Pk, Dc, Dk, t1, t2);
-    for (int i = 0; i < m2; ++i) Dc[i] = t1[i];
-    for (int i = 0; i < n1; ++i)
-      for (int c = 0; c < n1; ++c) {
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) cong_reduce_warp_kernel(int n, int64_t cnt, int G, int level0,
+                                                              const double* __restrict__ maps0,
+                                                              const double* __restrict__ D,
+                                                              const double* __restrict__ in, double* __restrict__ out) {
+  __shared__ double P[AH * AH], Dc[AH * AH], Pk[AH * AH], Dk[AH * AH], t1[AH * AH], t2[AH * AH];
+  const int lane = threadIdx.x;
+  const int n1 = n + 1, m2 = n1 * n1;
+  for (int64_t g = blockIdx.x; g * G < cnt; g += gridDim.x) {
+    const int64_t first = g * G;
+    const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+    wload_level(lane, n, level0, maps0, D, in, first, P, Dc);
+    for (int64_t k = first + 1; k <= last; ++k) {
+      wload_level(lane, n, level0, maps0, D, in, k, Pk, Dk);
+      // (Pk, Dk) o (P, Dc) = (Pk P, Pk Dc Pk^T + Dk)
+      wcongruence(lane, n1, Pk, Dc, Dk, t1, t2);
+      for (int e = lane; e < m2; e += 32) {
+        Dc[e] = t1[e];
+        const int i = e / n1, c = e % n1;
         double s = 0.0;
         for (int l = 0; l < n1; ++l) s = fma(Pk[i * n1 + l], P[l * n1 + c], s);
-        t1[i * n1 + c] = s;
+        t2[e] = s;
       }
-    for (int i = 0; i < m2; ++i) P[i] = t1[i];
-  }
-  for (int i = 0; i < m2; ++i) {
-    out[g * 2 * m2 + i] = P[i];
-    out[g * 2 * m2 + m2 + i] = Dc[i];
+      __syncwarp();
+      for (int e = lane; e < m2; e += 32) P[e] = t2[e];
+      __syncwarp();
+    }
+    for (int e = lane; e < m2; e += 32) {
+      out[g * 2 * m2 + e] = P[e];
+      out[g * 2 * m2 + m2 + e] = Dc[e];
+    }
+    __syncwarp();
   }
 }
 
-// states[first..last+1] from the group's start (above[g] or the initial).
-__global__ void cong_down_kernel(int n, int64_t cnt, int G, int level0, const double* __restrict__ maps0,
-                                 const double* __restrict__ D, const double* __restrict__ in,
-                                 const double* __restrict__ above, const double* __restrict__ init,
-                                 double* __restrict__ states) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t first = g * G;
-  if (first >= cnt) return;
-  const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+__global__ void __launch_bounds__(32) cong_down_warp_kernel(int n, int64_t cnt, int G, int level0,
+                                                            const double* __restrict__ maps0,
+                                                            const double* __restrict__ D,
+                                                            const double* __restrict__ in,
+                                                            const double* __restrict__ above,
+                                                            const double* __restrict__ init,
+                                                            double* __restrict__ states) {
+  __shared__ double X[AH * AH], P[AH * AH], Dk[AH * AH], y[AH * AH], t[AH * AH];
+  const int lane = threadIdx.x;
   const int n1 = n + 1, m2 = n1 * n1;
-  double X[AH * AH], P[AH * AH], Dk[AH * AH], y[AH * AH], t[AH * AH];
-  const double* xs = above ? above + g * m2 : init;
-  for (int i = 0; i < m2; ++i) X[i] = xs[i];
-  for (int64_t k = first; k <= last; ++k) {
-    for (int i = 0; i < m2; ++i) states[k * m2 + i] = X[i];
-    if (level0) {
-      load_P(n, maps0 + k * (n * n + n), P);
-      for (int i = 0; i < m2; ++i) Dk[i] = D[(k + 1) * m2 + i];
-    } else {
-      for (int i = 0; i < m2; ++i) {
-        P[i] = in[k * 2 * m2 + i];
-        Dk[i] = in[k * 2 * m2 + m2 + i];
-      }
+  for (int64_t g = blockIdx.x; g * G < cnt; g += gridDim.x) {
+    const int64_t first = g * G;
+    const int64_t last = (first + G < cnt ? first + G : cnt) - 1;
+    const double* xs = above ? above + g * m2 : init;
+    for (int e = lane; e < m2; e += 32) X[e] = xs[e];
+    __syncwarp();
+    for (int64_t k = first; k <= last; ++k) {
+      for (int e = lane; e < m2; e += 32) states[k * m2 + e] = X[e];
+      wload_level(lane, n, level0, maps0, D, in, k, P, Dk);
+      wcongruence(lane, n1, P, X, Dk, y, t);
+      for (int e = lane; e < m2; e += 32) X[e] = y[e];
+      __syncwarp();
     }
-    congruence(n1, P, X, Dk, y, t);
-    for (int i = 0; i < m2; ++i) X[i] = y[i];
+    if (last == cnt - 1)
+      for (int e = lane; e < m2; e += 32) states[cnt * m2 + e] = X[e];
+    __syncwarp();
   }
-  if (last == cnt - 1)
-    for (int i = 0; i < m2; ++i) states[cnt * m2 + i] = X[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -979,8 +986,8 @@ static void cong_scan(int n, int64_t T, const double* maps0, const double* D, do
     const int64_t nc = cdiv(mc, G);
     double* out = (double*)(ws + off);
     off = al(off + nc * 2 * m2 * sizeof(double));
-    cong_reduce_kernel<<<(unsigned)cdiv(nc, 64), 64, 0, st>>>(n, mc, G, nlev == 0, maps0, D,
-                                                             nlev ? lv[nlev - 1] : nullptr, out);
+    cong_reduce_warp_kernel<<<(unsigned)(nc < 152 * 32 ? nc : 152 * 32), 32, 0, st>>>(
+        n, mc, G, nlev == 0, maps0, D, nlev ? lv[nlev - 1] : nullptr, out);
     count_launch();
     c[nlev] = nc;
     lv[nlev] = out;
@@ -993,15 +1000,16 @@ static void cong_scan(int n, int64_t T, const double* maps0, const double* D, do
   {
     const int64_t tc = nlev ? c[nlev - 1] : T;
     double* tst = nlev ? sv[nlev - 1] : Sigma;
-    cong_down_kernel<<<1, 64, 0, st>>>(n, tc, (int)tc, nlev == 0, maps0, D, nlev ? lv[nlev - 1] : nullptr, nullptr,
-                                       D, tst);
+    cong_down_warp_kernel<<<1, 32, 0, st>>>(n, tc, (int)tc, nlev == 0, maps0, D, nlev ? lv[nlev - 1] : nullptr,
+                                            nullptr, D, tst);
     count_launch();
   }
   for (int l = nlev - 1; l >= 0; --l) {
     const int64_t cnt = (l == 0) ? T : c[l - 1];
     double* out = (l == 0) ? Sigma : sv[l - 1];
-    cong_down_kernel<<<(unsigned)cdiv(cdiv(cnt, G), 64), 64, 0, st>>>(n, cnt, G, l == 0, maps0, D,
-                                                                      l == 0 ? nullptr : lv[l - 1], sv[l], D, out);
+    const int64_t groups = cdiv(cnt, G);
+    cong_down_warp_kernel<<<(unsigned)(groups < 152 * 32 ? groups : 152 * 32), 32, 0, st>>>(
+        n, cnt, G, l == 0, maps0, D, l == 0 ? nullptr : lv[l - 1], sv[l], D, out);
     count_launch();
   }
 }

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) qr_identity_kernel(const double* __restri
 // thread i forming row i of X r: a warp reads 32 consecutive rows, so the
 // stream of X samples (the largest input when X is sampled per half-step) is
 // read in full 128-byte lines; rho is reduced over the N lanes.
-template <int N>
+template <int N, bool VEC>
 __global__ void __launch_bounds__(256) qr_rows_kernel(const double* __restrict__ X, int32_t X_mode,
                                                       const double* __restrict__ r, int32_t r_mode, int32_t dmode,
                                                       int64_t cnt, int32_t K, int64_t T, double* __restrict__ qr) {
@@ -203,8 +203,21 @@ __global__ void __launch_bounds__(256) qr_rows_kernel(const double* __restrict__
     const double* row = X + input_index(X_mode, dmode, s, K, T) * N * N + i * N;
     if (r) {
       const double* rs = r + input_index(r_mode, dmode, s, K, T) * N;
+      if constexpr (VEC) {
+        // X and r start on 16-byte boundaries (checked by the launcher) and N is
+        // even, so every row and sample does: read them in pairs
+        const double2* row2 = reinterpret_cast<const double2*>(row);
+        const double2* rs2 = reinterpret_cast<const double2*>(rs);
 #pragma unroll
-      for (int l = 0; l < N; ++l) q = fma(row[l], rs[l], q);
+        for (int l = 0; l < N / 2; ++l) {
+          const double2 a = __ldg(row2 + l), b = __ldg(rs2 + l);
+          q = fma(a.x, b.x, q);
+          q = fma(a.y, b.y, q);
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < N; ++l) q = fma(row[l], rs[l], q);
+      }
       ri = rs[i];
     }
   }
@@ -222,8 +235,14 @@ static void launch_qr_identity(const PrepArgs& a, cudaStream_t st) {
   const int threads = 256;
   if constexpr (N >= 2 && N <= 32 && (N & (N - 1)) == 0) {
     const int64_t total = a.cnt_qr * N;
-    qr_rows_kernel<N><<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
-        a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr, a.K, a.T, a.qr);
+    const unsigned grid = (unsigned)((total + threads - 1) / threads);
+    const bool vec = ((reinterpret_cast<uintptr_t>(a.X.ptr) | reinterpret_cast<uintptr_t>(a.r.ptr)) & 15u) == 0;
+    if (vec)
+      qr_rows_kernel<N, true><<<grid, threads, 0, st>>>(a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr,
+                                                         a.K, a.T, a.qr);
+    else
+      qr_rows_kernel<N, false><<<grid, threads, 0, st>>>(a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr,
+                                                          a.K, a.T, a.qr);
   } else {
     qr_identity_kernel<N><<<(unsigned)((a.cnt_qr + threads - 1) / threads), threads, 0, st>>>(
         a.X.ptr, a.X.mode, a.r.ptr, a.r.mode, a.mode_qr, a.cnt_qr, a.K, a.T, a.qr);

@@ -33,11 +33,12 @@ int scan_chunk_override() { return t_chunk_override; }
 // Level-0 chunk length from T, or the caller's override.  Level 0 is FP64
 // throughput-bound with one thread per chunk, and a sub-partition runs one
 // FP64 warp instruction per 64 cycles whatever its warp count, so the chunks
-// are sized to give every one of the 152 x 4 sub-partitions exactly one warp
-// (152 * 4 * 32 = 19456 threads): any more warps only leave some
-// sub-partitions with one warp more than others at the end.  At least 2, at
-// most 64 elements per chunk.
-constexpr int64_t kLevel0Threads = 152 * 4 * 32;
+// are sized to give every one of the 152 x 4 sub-partitions the same number of
+// warps -- two, so that one warp's memory and dependency stalls are covered by
+// the other (152 * 4 * 32 * 2 = 38912 threads); an uneven count would leave
+// some sub-partitions with one warp more than others at the end.  At least 2,
+// at most 64 elements per chunk.
+constexpr int64_t kLevel0Threads = 152 * 4 * 32 * 2;
 static int level0_group(int64_t T) {
   if (t_chunk_override >= 2) return t_chunk_override;
   int64_t g = (T + 1 + kLevel0Threads - 1) / kLevel0Threads;
