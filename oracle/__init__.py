@@ -25,6 +25,13 @@ _lib = None
 _dp = ct.POINTER(ct.c_double)
 
 
+class _GridProblem(ct.Structure):
+    _fields_ = [("G", ct.c_int), ("x_min", ct.c_double), ("dx", ct.c_double), ("d0", ct.c_double),
+                ("d1", ct.c_double), ("d2", ct.c_double), ("q", ct.c_double), ("rho", ct.c_double),
+                ("qf", ct.c_double), ("tau", ct.c_double), ("substeps", ct.c_int), ("T", ct.c_long),
+                ("interp", ct.c_int)]
+
+
 class _Problem(ct.Structure):
     _fields_ = [
         ("n", ct.c_int), ("m", ct.c_int), ("nr", ct.c_int), ("T", ct.c_long), ("K", ct.c_int),
@@ -61,11 +68,18 @@ def _configure(L):
     L.orc_build_elements_forward.argtypes = [P, ct.c_long, ct.c_long, _dp]
     L.orc_prefix.argtypes = [ct.c_int, ct.c_long, _dp, _dp]
     L.orc_trajectory_method2.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
+    GP = ct.POINTER(_GridProblem)
+    L.orc_grid_combine.argtypes = [GP, _dp, _dp, _dp]
+    L.orc_grid_apply.argtypes = [GP, _dp, _dp, _dp]
+    L.orc_grid_block.argtypes = [GP, _dp]
+    L.orc_grid_values_sequential.argtypes = [GP, _dp, _dp]
+    L.orc_grid_values.argtypes = [GP, _dp, _dp]
     L.orc_element_size.argtypes = [ct.c_int]
     L.orc_element_size.restype = ct.c_long
     for f in ("orc_build_elements", "orc_combine", "orc_suffix_values", "orc_trajectory", "orc_solve",
               "orc_sequential", "orc_densify", "orc_build_elements_forward", "orc_prefix",
-              "orc_trajectory_method2"):
+              "orc_trajectory_method2", "orc_grid_combine", "orc_grid_apply", "orc_grid_block",
+              "orc_grid_values_sequential", "orc_grid_values"):
         getattr(L, f).restype = ct.c_int
     return L
 
@@ -289,3 +303,43 @@ def trajectory_method2(p, S, v, x0=None) -> dict:
     if lib().orc_trajectory_method2(m.ref(), _ptr(c(S)), _ptr(c(v)), _ptr(x0), _ptr(x), _ptr(u)):
         raise FloatingPointError("oracle: singular matrix in Method 2")
     return {"x": x, "u": u}
+
+
+def _grid_struct(g) -> "_GridProblem":
+    return _GridProblem(g.G, g.x_min, g.dx, g.d0, g.d1, g.d2, g.q, g.rho, g.qf, g.tau, g.substeps, g.T,
+                        1 if g.interp else 0)
+
+
+def grid_combine(g, A, B) -> np.ndarray:
+    """(A (x) B)(i, j) = min_k A(i, k) + B(k, j) on the grid (App. E refinement if g.interp)."""
+    out = np.zeros((g.G, g.G))
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    lib().orc_grid_combine(ct.byref(_grid_struct(g)), _ptr(c(A)), _ptr(c(B)), _ptr(out))
+    return out
+
+
+def grid_apply(g, M, w) -> np.ndarray:
+    out = np.zeros(g.G)
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    lib().orc_grid_apply(ct.byref(_grid_struct(g)), _ptr(c(M)), _ptr(c(w)), _ptr(out))
+    return out
+
+
+def grid_block(g) -> np.ndarray:
+    """The block's conditional value function on the grid (G x G)."""
+    out = np.zeros((g.G, g.G))
+    lib().orc_grid_block(ct.byref(_grid_struct(g)), _ptr(out))
+    return out
+
+
+def grid_values_sequential(g, Vblock) -> np.ndarray:
+    out = np.zeros((g.T + 1, g.G))
+    lib().orc_grid_values_sequential(ct.byref(_grid_struct(g)), _ptr(np.ascontiguousarray(Vblock)), _ptr(out))
+    return out
+
+
+def grid_values(g, Vblock) -> np.ndarray:
+    """Values at every block boundary in the doubling-scan order."""
+    out = np.zeros((g.T + 1, g.G))
+    lib().orc_grid_values(ct.byref(_grid_struct(g)), _ptr(np.ascontiguousarray(Vblock)), _ptr(out))
+    return out

@@ -946,5 +946,147 @@ int orc_densify(const orc_problem *P, const double *S, const double *v, const do
   return bad;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Nonlinear scalar problem on a state grid (Sec. VI-B, App. E)              */
+/* ------------------------------------------------------------------------ */
+
+/* Scalar control-affine problem dx/dt = d0 + d1 x + d2 x^2 + u, running cost
+ * q x^2 / 2 + rho u^2 / 2, terminal cost qf x^2 / 2 (Sec. VI-B: d0 = 1, d1 = 0,
+ * d2 = -1/10, q = rho = 1, qf = 4), on the grid x_i = x_min + i dx,
+ * i = 0..G-1; blocks of length tau split into `substeps` steps of
+ * dt = tau / substeps, T blocks. */
+typedef struct {
+  int G;
+  double x_min, dx;
+  double d0, d1, d2, q, rho, qf;
+  double tau;
+  int substeps;
+  long T;
+  int interp; /* 1: every grid minimisation refined by App. E's quadratic interpolation */
+} orc_grid_problem;
+
+/* App. E: min over the grid of g_j + f_j, refined by the quadratic
+ * interpolants of g and f through the discrete minimiser i and its two
+ * neighbours (lowest index on ties; no refinement at the grid ends or when the
+ * summed curvature a_g + a_f is not positive). */
+static double grid_min(int G, double dx, const double *g, long gs, const double *f, long fs, int interp) {
+  int bi = 0;
+  double best = g[0] + f[0];
+  for (int j = 1; j < G; ++j) {
+    double v = g[j * gs] + f[j * fs];
+    if (v < best) { best = v; bi = j; }
+  }
+  if (!interp || bi == 0 || bi == G - 1) return best;
+  double gm = g[(bi - 1) * gs], g0 = g[bi * gs], gp = g[(bi + 1) * gs];
+  double fm = f[(bi - 1) * fs], f0 = f[bi * fs], fp = f[(bi + 1) * fs];
+  double ag = (gp + gm - 2.0 * g0) / (2.0 * dx * dx), bg = (gp - gm) / (2.0 * dx);
+  double af = (fp + fm - 2.0 * f0) / (2.0 * dx * dx), bf = (fp - fm) / (2.0 * dx);
+  double a = ag + af, b = bg + bf;
+  if (!(a > 0.0)) return best;
+  return best - b * b / (4.0 * a);
+}
+
+/* out(i, j) = min_k A(i, k) + B(k, j) (Theorem "HJB-comb" on the grid: the
+ * combination of conditional value functions V(x_i; x_k) and V(x_k; x_j)),
+ * G x G row-major. */
+int orc_grid_combine(const orc_grid_problem *P, const double *A, const double *B, double *out) {
+  int G = P->G;
+  for (int i = 0; i < G; ++i)
+    for (int j = 0; j < G; ++j) out[(size_t)i * G + j] = grid_min(G, P->dx, A + (size_t)i * G, 1, B + j, G, P->interp);
+  return 0;
+}
+
+/* out(i) = min_k M(i, k) + w(k): a conditional value function combined with a
+ * value function (the last step of the fold, Theorem "parallel_HJB"). */
+int orc_grid_apply(const orc_grid_problem *P, const double *M, const double *w, double *out) {
+  int G = P->G;
+  for (int i = 0; i < G; ++i) out[i] = grid_min(G, P->dx, M + (size_t)i * G, 1, w, 1, P->interp);
+  return 0;
+}
+
+/* One step's conditional value function: from x_i to x_j in dt with the
+ * explicit Euler step x_j = x_i + dt (drift(x_i) + u), so
+ * u = (x_j - x_i)/dt - drift(x_i), cost dt (q x_i^2 + rho u^2)/2. */
+static void grid_one_step(const orc_grid_problem *P, double *C) {
+  int G = P->G;
+  double dt = P->tau / P->substeps;
+  for (int i = 0; i < G; ++i) {
+    double xi = P->x_min + i * P->dx;
+    double drift = P->d0 + P->d1 * xi + P->d2 * xi * xi;
+    for (int j = 0; j < G; ++j) {
+      double xj = P->x_min + j * P->dx;
+      double u = (xj - xi) / dt - drift;
+      C[(size_t)i * G + j] = dt * 0.5 * (P->q * xi * xi + P->rho * u * u);
+    }
+  }
+}
+
+/* The block's conditional value function V(x_i, t; x_j, t + tau): the one-step
+ * function combined with itself substeps times, left to right
+ * (M_1 = C, M_{m+1} = M_m (x) C).  Out: G x G. */
+int orc_grid_block(const orc_grid_problem *P, double *out) {
+  size_t GG = (size_t)P->G * P->G;
+  double *C = (double *)malloc(sizeof(double) * 2 * GG), *tmp = C + GG;
+  grid_one_step(P, C);
+  memcpy(out, C, sizeof(double) * GG);
+  for (int m = 1; m < P->substeps; ++m) {
+    orc_grid_combine(P, out, C, tmp);
+    memcpy(out, tmp, sizeof(double) * GG);
+  }
+  free(C);
+  return 0;
+}
+
+/* Terminal value phi(x_i) = qf x_i^2 / 2. */
+static void grid_terminal(const orc_grid_problem *P, double *phi) {
+  for (int i = 0; i < P->G; ++i) {
+    double x = P->x_min + i * P->dx;
+    phi[i] = 0.5 * P->qf * x * x;
+  }
+}
+
+/* Values V(., t_k), k = 0..T, by the sequential right-to-left fold
+ * V_T = phi, V_k = Vblock (x) V_{k+1} (Theorem "parallel_HJB" with one
+ * conditional value function for every block: the model is time-invariant,
+ * Sec. VI-B).  Out: [T+1][G]. */
+int orc_grid_values_sequential(const orc_grid_problem *P, const double *Vblock, double *V) {
+  int G = P->G;
+  long T = P->T;
+  grid_terminal(P, V + (size_t)T * G);
+  for (long k = T - 1; k >= 0; --k) orc_grid_apply(P, Vblock, V + (size_t)(k + 1) * G, V + (size_t)k * G);
+  return 0;
+}
+
+/* The same values in the order of the doubling scan: the powers
+ * P_0 = Vblock, P_{l+1} = P_l (x) P_l, and for every k, with T - k =
+ * sum of 2^{l_1} < 2^{l_2} < ..., V_k = P_{l_r} (x) (... (P_{l_1} (x) phi)).
+ * Without the interpolation this is the sequential fold exactly (the grid
+ * minimum is associative); with it, the two differ by the interpolation
+ * error.  Out: [T+1][G]. */
+int orc_grid_values(const orc_grid_problem *P, const double *Vblock, double *V) {
+  int G = P->G;
+  long T = P->T;
+  size_t GG = (size_t)G * G;
+  int L = 0;
+  while ((1L << L) <= T) ++L;
+  double *pw = (double *)malloc(sizeof(double) * ((size_t)L * GG + 2 * (size_t)G));
+  double *w = pw + (size_t)L * GG, *w2 = w + G;
+  memcpy(pw, Vblock, sizeof(double) * GG);
+  for (int l = 1; l < L; ++l) orc_grid_combine(P, pw + (size_t)(l - 1) * GG, pw + (size_t)(l - 1) * GG, pw + (size_t)l * GG);
+  grid_terminal(P, V + (size_t)T * G);
+  for (long k = 0; k < T; ++k) {
+    long e = T - k;
+    memcpy(w, V + (size_t)T * G, sizeof(double) * G);
+    for (int l = 0; l < L; ++l)
+      if (e & (1L << l)) {
+        orc_grid_apply(P, pw + (size_t)l * GG, w, w2);
+        memcpy(w, w2, sizeof(double) * G);
+      }
+    memcpy(V + (size_t)k * G, w, sizeof(double) * G);
+  }
+  free(pw);
+  return 0;
+}
+
 /* Size in doubles of one packed element, for callers. */
 long orc_element_size(int n) { return (long)elem_size(n); }

@@ -2,8 +2,8 @@
 
 Each case below plants one mistake in a copy of oracle/lqt_oracle.c (a dropped
 term, a flipped sign, a transposed operand, a wrong index or weight), compiles
-the copy, and runs every pin of test_oracle_pins.py, test_oracle_densify.py
-and test_oracle_method2.py against it.  At least one
+the copy, and runs every pin of test_oracle_pins.py, test_oracle_densify.py,
+test_oracle_method2.py and test_oracle_grid.py against it.  At least one
 pin has to fail for every mutant; otherwise the pins would also have let that
 mistake through in the real oracle.  Nothing here touches the GPU.
 """
@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_densify as densify_pins
+from tests import test_oracle_grid as grid_pins
 from tests import test_oracle_method2 as method2_pins
 from tests import test_oracle_pins as pins
 
@@ -98,6 +99,16 @@ MUTATIONS = [
      "orc_combine(n, elems + (size_t)k * es, prefixes + (size_t)k * es,", 0),
     ("method 2: dropped C v", "for (int i = 0; i < n; ++i) rhs[i] += pk.b[i] + tv[i];",
      "for (int i = 0; i < n; ++i) rhs[i] += pk.b[i];", 0),
+    # grid method (Sec. VI-B, App. E)
+    ("grid: interpolation correction sign", "return best - b * b / (4.0 * a);", "return best + b * b / (4.0 * a);", 0),
+    ("grid: curvature factor", "double ag = (gp + gm - 2.0 * g0) / (2.0 * dx * dx)", "double ag = (gp + gm - 2.0 * g0) / (dx * dx)", 0),
+    ("grid: slope factor", "bg = (gp - gm) / (2.0 * dx);", "bg = (gp - gm) / dx;", 0),
+    ("grid: one-step control", "double u = (xj - xi) / dt - drift;", "double u = (xj - xi) / dt + drift;", 0),
+    ("grid: one-step cost factor", "C[(size_t)i * G + j] = dt * 0.5 * (P->q * xi * xi + P->rho * u * u);",
+     "C[(size_t)i * G + j] = dt * (P->q * xi * xi + P->rho * u * u);", 0),
+    ("grid: terminal factor", "phi[i] = 0.5 * P->qf * x * x;", "phi[i] = P->qf * x * x;", 0),
+    ("grid: block substeps", "for (int m = 1; m < P->substeps; ++m) {", "for (int m = 2; m < P->substeps; ++m) {", 0),
+    ("grid: doubling skips a power", "if (e & (1L << l)) {", "if (l > 0 && (e & (1L << l))) {", 0),
     # shared small linear algebra
     ("mtm: operand not transposed", "for (int l = 0; l < k; ++l) s += a[l * p + i] * b[l * q + j];",
      "for (int l = 0; l < k; ++l) s += a[i * k + l] * b[l * q + j];", 0),
@@ -115,7 +126,7 @@ def _replace_nth(text, old, new, nth):
 def _pin_calls():
     """Every (name, zero-argument callable) for the pins, parametrisations expanded."""
     calls = []
-    mods = (pins, densify_pins, method2_pins)
+    mods = (pins, densify_pins, method2_pins, grid_pins)
     members = [m for mod in mods for m in inspect.getmembers(mod, inspect.isfunction)]
     for name, fn in members:
         if not name.startswith("test_") or fn.__module__ not in tuple(mod.__name__ for mod in mods):

@@ -406,3 +406,37 @@ def window(p: Problem, j0: int, count: int) -> Problem:
     return Problem(name=p.name + f"_w{j0}+{count}", n=p.n, m=p.m, nr=p.nr, T=count, K=K,
                    t=p.t[j0:j0 + count + 1].copy(), Hf=p.Hf, Xf=p.Xf, rf=p.rf, x0=p.x0, extra=p.extra,
                    funcs=p.funcs, **co)
+
+
+
+@dataclass
+class GridProblem:
+    """Scalar control-affine problem dx/dt = d0 + d1 x + d2 x^2 + u with cost
+    q x^2/2 + rho u^2/2 and terminal cost qf x^2/2 on a uniform state grid,
+    blocks of length tau with `substeps` Euler steps each, T blocks."""
+    G: int
+    x_min: float
+    dx: float
+    d0: float
+    d1: float
+    d2: float
+    q: float
+    rho: float
+    qf: float
+    tau: float
+    substeps: int
+    T: int
+    interp: bool = True
+
+    def grid(self) -> np.ndarray:
+        return self.x_min + self.dx * np.arange(self.G)
+
+
+def falling_body(G: int = 201, T: int = 100, x_range: float = 6.0, interp: bool = True) -> GridProblem:
+    """The nonlinear example of Sec. VI-B: dx/dt = 1 - x^2/10 + u (velocity of a
+    falling body with air resistance, controlled by the force u), running cost
+    (x^2 + u^2)/2, terminal cost 2 x^2; blocks of 1/10 time unit with 10 steps
+    each; state grid [-x_range, x_range] with G points."""
+    dx = 2.0 * x_range / (G - 1)
+    return GridProblem(G=G, x_min=-x_range, dx=dx, d0=1.0, d1=0.0, d2=-0.1, q=1.0, rho=1.0, qf=4.0, tau=0.1,
+                       substeps=10, T=T, interp=interp)
