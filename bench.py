@@ -220,6 +220,17 @@ def cpu_baseline_sample(p, seconds_hint=True):
             "sample": f"first {Ts} of the {p.T} sub-intervals (same grid and samples), one solve, {dt:.1f} s"}
 
 
+def cpu_baseline_grid(g):
+    """Times the oracle's grid method (block function, then values in the
+    doubling order), single thread, on the whole problem."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.grid_values(g, oracle.grid_block(g))
+    dt = time.perf_counter() - t0
+    return {"value": g.T / dt, "unit": "blocks/s", "cores": 1, "kind": "oracle",
+            "sample": f"the whole G = {g.G}, T = {g.T} problem, {dt:.2f} s"}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
@@ -440,6 +451,41 @@ def measure_rows(T_headline):
             res["large_state_n64_T2^16"] = str(exc)
         return res
 
+    def grid():
+        """The nonlinear example of Sec. VI-B on state grids of 20, 40, 60 (the
+        paper's) and 201 points, 10^4 blocks of 1/10 with 10 Euler steps each:
+        block function plus values at every block boundary.  Each candidate of
+        a grid minimisation costs one FP64 add (the comparison runs on integer
+        keys), so the bound is the FP64 pipe at one add per DFMA slot."""
+        import workloads as Wk
+        T = 10000
+        out = {"workload": "falling body dx/dt = 1 - x^2/10 + u on [-6, 6], T = 10^4 blocks, 10 steps per block, "
+                           "App. E interpolated minimum", "unit": "blocks/s", "per_G": {}}
+        add_peak = FP64_PEAK_TFLOPS * 1e12 / 2  # DFMA issue slots per second
+        for G in (20, 40, 60, 201):
+            g = Wk.falling_body(G=G, T=T)
+            wb = torch.empty(lqt.lqt_grid_workspace_size(g, 0), dtype=torch.uint8, device="cuda")
+            wv = torch.empty(lqt.lqt_grid_workspace_size(g, 1), dtype=torch.uint8, device="cuda")
+            Vb = lqt.lqt_grid_block(g, ws=wb)
+            V = lqt.lqt_grid_values(g, Vb, ws=wv)
+
+            def path():
+                lqt.lqt_grid_block(g, out=Vb, ws=wb)
+                lqt.lqt_grid_values(g, Vb, out=V, ws=wv)
+
+            for _ in range(3):
+                path()
+            ms = _events_ms(path, 5)
+            vms = _events_ms(lambda: lqt.lqt_grid_values(g, Vb, out=V, ws=wv), 5)
+            L = T.bit_length()
+            adds = ((g.substeps - 1) + (L - 1)) * G ** 3 + sum(bin(e).count("1") for e in range(1, T + 1)) * G * G
+            out["per_G"][str(G)] = {"ms": ms, "ms_values": vms, "value": T / (ms * 1e-3),
+                                    "fp64_adds": adds, "fp64_add_frac": adds / (ms * 1e-3) / add_peak}
+        out["value"] = out["per_G"]["60"]["value"]
+        out["status"] = lqt.lqt_get_status()
+        out["cpu_baseline"] = cpu_baseline_grid(Wk.falling_body(G=60, T=T))
+        return out
+
     guard("a4_batched", batched)
     guard("a5_mixed", mixed)
     guard("a6_adjoint", adjoint)
@@ -447,6 +493,7 @@ def measure_rows(T_headline):
     guard("next1_densify", densify)
     guard("next2_method2", method2)
     guard("next3_invariant", invariant)
+    guard("next4_grid", grid)
     return rows
 
 

@@ -360,6 +360,71 @@ lqt_status lqt_solve_host(const lqt_problem *p, const double *x0, double *S, dou
 lqt_status lqt_scan_value_noalloc(const lqt_problem *p, const lqt_elements *el, double *S, double *v, double *zeta,
                                   void *stream);
 
+/* ------------------------------------------------------------------------
+ * The general method on a state grid (Sec. VI-B, App. E)
+ *
+ * The scalar nonlinear problem of Sec. VI-B, generalised to a quadratic drift:
+ *     dx/dt = d0 + d1 x + d2 x^2 + u,   cost  qf x(tf)^2/2 + int q x^2/2 + rho u^2/2 dt
+ * (the paper's falling body: d0 = 1, d1 = 0, d2 = -1/10, q = rho = 1, qf = 4,
+ * blocks of length 1/10 split into 10 steps).  Functions of the state are held
+ * at the G grid points x_i = x_min + i dx; a conditional value function
+ * V(x_i, s; x_j, s') is a G x G row-major array (row: start point, column: end
+ * point).  Its combination (Theorem HJB-comb) is the minimisation over the
+ * grid of the intermediate state,
+ *     (A (x) B)(i, j) = min_k A(i, k) + B(k, j),
+ * the lowest k winning ties, refined (interp = 1) by App. E's quadratic
+ * interpolation: with a, b the summed curvature and slope of the quadratics
+ * through (k-1, k, k+1) of A(i, .) and B(., j), the minimum is lowered by
+ * b^2 / (4a) when a > 0 and k is not at an end of the grid.
+ *
+ * The block's conditional value function is built from the one-step function
+ * of an explicit Euler step dt = tau / substeps (from x_i to x_j with control
+ * u = (x_j - x_i)/dt - drift(x_i), cost dt (q x_i^2 + rho u^2)/2), combined
+ * with itself `substeps` times left to right.  This replaces the paper's
+ * direct-shooting solve of the block problem.
+ *
+ * Every floating-point operation is IEEE round-to-nearest double in the order
+ * the formulas above state, without multiply-add contraction.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t G;         /* grid points, 3 <= G <= 16384                            */
+  double x_min, dx;  /* x_i = x_min + i dx, dx > 0                               */
+  double d0, d1, d2; /* drift d0 + d1 x + d2 x^2                                 */
+  double q, rho, qf; /* running state weight, control weight (> 0), terminal     */
+  double tau;        /* block length (> 0)                                       */
+  int32_t substeps;  /* Euler steps per block (>= 1)                             */
+  int64_t T;         /* blocks (>= 1)                                            */
+  int32_t interp;    /* 1: App. E refinement of every minimisation; 0: plain     */
+} lqt_grid_problem;
+
+/* Workspace bytes: which = 0 for lqt_grid_block (2 G^2 doubles), 1 for
+ * lqt_grid_values (G^2 ceil(log2(T+1)) + (T+1) G doubles).  0 when p is
+ * invalid or `which` unknown. */
+size_t lqt_grid_workspace_size(const lqt_grid_problem *p, int32_t which);
+
+/* The block's conditional value function Vblock (G x G, device) as described
+ * above.  Workspace: lqt_grid_workspace_size(p, 0).  Non-finite outputs are
+ * recorded in the status word. */
+lqt_status lqt_grid_block(const lqt_grid_problem *p, double *Vblock, void *ws, size_t ws_bytes, void *stream);
+
+/* out = A (x) B, all G x G device arrays; out must not overlap A or B.  No
+ * workspace. */
+lqt_status lqt_grid_combine(const lqt_grid_problem *p, const double *A, const double *B, double *out, void *stream);
+
+/* The value functions V(., t_k) = V[k][0..G-1], k = 0..T (device,
+ * (T+1) x G), of the time-invariant problem whose every block has the
+ * conditional value function Vblock (G x G, device; Sec. VI-B: one block
+ * function serves every block).  V[T] is the terminal cost.  Evaluation order
+ * (Theorem parallel_HJB, grouped for a logarithmic span): the powers
+ * P_0 = Vblock, P_{l+1} = P_l (x) P_l; then V[k] = P_{l_r} (x) (... (P_{l_1} (x) phi))
+ * over the set bits l_1 < ... < l_r of T - k.  Without the refinement this
+ * equals the sequential fold V[k] = Vblock (x) V[k+1] exactly (the grid
+ * minimum is associative); with it the two differ by the interpolation error.
+ * Workspace: lqt_grid_workspace_size(p, 1).  V must not overlap Vblock or the
+ * workspace. */
+lqt_status lqt_grid_values(const lqt_grid_problem *p, const double *Vblock, double *V, void *ws, size_t ws_bytes,
+                           void *stream);
+
 /* Waits for `stream` (polling, at most timeout_ms; < 0 waits forever), then
  * reads and clears the current device's status word.  Returns LQT_OK,
  * LQT_ENONFINITE, LQT_ESINGULAR, LQT_ETIMEOUT or LQT_ECUDA. */

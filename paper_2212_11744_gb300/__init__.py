@@ -21,7 +21,7 @@ from . import _abi
 from ._abi import (LQT_CONST, LQT_PER_INTERVAL, LQT_PER_STAGE, LQT_WS_BACKWARD, LQT_WS_BUILD, LQT_WS_DENSIFY,
                    LQT_WS_INVARIANT, LQT_WS_METHOD2, LQT_WS_SEQUENTIAL, LQT_WS_SOLVE, LQT_WS_SOLVE_INVARIANT,
                    LQT_WS_SOLVE_METHOD2, LQT_WS_TRAJ,
-                   LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_problem)
+                   LQT_WS_VALUE, LQTError, lqt_coef, lqt_elements, lqt_grid_problem, lqt_problem)
 
 __all__ = [
     "DeviceProblem", "HostProblem", "lqt_workspace_size", "lqt_build_elements", "lqt_scan_value",
@@ -29,6 +29,7 @@ __all__ = [
     "lqt_solve_sequential", "lqt_solve_host", "lqt_host_staging_size", "lqt_build_elements_forward",
     "lqt_trajectory_method2", "lqt_solve_method2", "lqt_build_elements_invariant", "lqt_solve_invariant",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
+    "grid_struct", "lqt_grid_workspace_size", "lqt_grid_block", "lqt_grid_combine", "lqt_grid_values",
 ]
 
 _COEFS = ("F", "L", "c", "H", "X", "U", "r")
@@ -324,6 +325,54 @@ def lqt_backward(dp: DeviceProblem, fwd: dict, gS=None, gv=None, gzeta=None, gx=
         None, float(g_cost), _ptr(out["F"]), _ptr(out["L"]), _ptr(out["X"]), _ptr(out["U"]), _ptr(out["r"]),
         _ptr(out["Xf"]), _ptr(out["rf"]), _ptr(out["x0"]), ws.data_ptr(), ws.numel(), _stream_handle(stream)),
         "lqt_backward")
+    return out
+
+
+def grid_struct(g) -> lqt_grid_problem:
+    """lqt_grid_problem from any object with the fields G, x_min, dx, d0, d1,
+    d2, q, rho, qf, tau, substeps, T, interp."""
+    return lqt_grid_problem(int(g.G), float(g.x_min), float(g.dx), float(g.d0), float(g.d1), float(g.d2),
+                            float(g.q), float(g.rho), float(g.qf), float(g.tau), int(g.substeps), int(g.T),
+                            int(bool(g.interp)))
+
+
+def lqt_grid_workspace_size(g, which: int) -> int:
+    return int(_abi.lib().lqt_grid_workspace_size(ct.byref(grid_struct(g)), which))
+
+
+def _grid_workspace(g, which: int, ws, device):
+    need = lqt_grid_workspace_size(g, which)
+    if need == 0:
+        raise LQTError(_abi.LQT_EINVAL, "lqt_grid_workspace_size")
+    return torch.empty(need, dtype=torch.uint8, device=device) if ws is None else ws
+
+
+def lqt_grid_block(g, out: Optional[torch.Tensor] = None, ws=None, device="cuda", stream=None) -> torch.Tensor:
+    """The block's conditional value function on the grid (G x G)."""
+    out = torch.empty(g.G, g.G, dtype=torch.float64, device=device) if out is None else out
+    ws = _grid_workspace(g, 0, ws, out.device)
+    _abi.check(_abi.lib().lqt_grid_block(ct.byref(grid_struct(g)), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                                         _stream_handle(stream)), "lqt_grid_block")
+    return out
+
+
+def lqt_grid_combine(g, A: torch.Tensor, B: torch.Tensor, out: Optional[torch.Tensor] = None,
+                     stream=None) -> torch.Tensor:
+    """A (x) B: min over the grid of the intermediate state (App. E refinement
+    when g.interp)."""
+    out = torch.empty_like(A) if out is None else out
+    _abi.check(_abi.lib().lqt_grid_combine(ct.byref(grid_struct(g)), A.data_ptr(), B.data_ptr(), out.data_ptr(),
+                                           _stream_handle(stream)), "lqt_grid_combine")
+    return out
+
+
+def lqt_grid_values(g, Vblock: torch.Tensor, out: Optional[torch.Tensor] = None, ws=None,
+                    stream=None) -> torch.Tensor:
+    """V(., t_k) for k = 0..T, shape (T+1, G)."""
+    out = torch.empty(g.T + 1, g.G, dtype=torch.float64, device=Vblock.device) if out is None else out
+    ws = _grid_workspace(g, 1, ws, Vblock.device)
+    _abi.check(_abi.lib().lqt_grid_values(ct.byref(grid_struct(g)), Vblock.data_ptr(), out.data_ptr(),
+                                          ws.data_ptr(), ws.numel(), _stream_handle(stream)), "lqt_grid_values")
     return out
 
 

@@ -25,7 +25,7 @@ EXPORTED = (
     "lqt_last_launch_count", "lqt_scan_value_noalloc", "lqt_backward", "lqt_batch_workspace_size",
     "lqt_batch_boundaries", "lqt_batch_plan", "lqt_solve_batched", "lqt_solve_mixed", "lqt_densify",
     "lqt_build_elements_forward", "lqt_trajectory_method2", "lqt_solve_method2", "lqt_build_elements_invariant",
-    "lqt_solve_invariant",
+    "lqt_solve_invariant", "lqt_grid_workspace_size", "lqt_grid_block", "lqt_grid_combine", "lqt_grid_values",
 )
 
 _dp = ct.POINTER(ct.c_double)
@@ -57,6 +57,13 @@ class lqt_batch(ct.Structure):
 
 class lqt_tuning(ct.Structure):
     _fields_ = [("chunk", ct.c_int32), ("flags", ct.c_int32)]
+
+
+class lqt_grid_problem(ct.Structure):
+    _fields_ = [("G", ct.c_int32), ("x_min", ct.c_double), ("dx", ct.c_double), ("d0", ct.c_double),
+                ("d1", ct.c_double), ("d2", ct.c_double), ("q", ct.c_double), ("rho", ct.c_double),
+                ("qf", ct.c_double), ("tau", ct.c_double), ("substeps", ct.c_int32), ("T", ct.c_int64),
+                ("interp", ct.c_int32)]
 
 
 class LQTError(RuntimeError):
@@ -113,12 +120,18 @@ def lib():
     L.lqt_solve_batched.restype = ct.c_int
     L.lqt_scan_value_noalloc.argtypes = [P, E, v, v, v, v]
     L.lqt_scan_value_noalloc.restype = ct.c_int
+    GP = ct.POINTER(lqt_grid_problem)
+    L.lqt_grid_workspace_size.argtypes = [GP, ct.c_int32]
+    L.lqt_grid_workspace_size.restype = ct.c_size_t
+    L.lqt_grid_block.argtypes = [GP, v, v, ct.c_size_t, v]
+    L.lqt_grid_combine.argtypes = [GP, v, v, v, v]
+    L.lqt_grid_values.argtypes = [GP, v, v, v, ct.c_size_t, v]
     L.lqt_last_launch_count.argtypes = []
     L.lqt_last_launch_count.restype = ct.c_int32
     for f in ("lqt_build_elements", "lqt_scan_value", "lqt_scan_trajectory", "lqt_solve", "lqt_solve_sequential",
               "lqt_densify", "lqt_build_elements_forward", "lqt_trajectory_method2", "lqt_solve_method2",
-              "lqt_build_elements_invariant", "lqt_solve_invariant",
-              "lqt_solve_host", "lqt_get_status"):
+              "lqt_build_elements_invariant", "lqt_solve_invariant", "lqt_grid_block", "lqt_grid_combine",
+              "lqt_grid_values", "lqt_solve_host", "lqt_get_status"):
         getattr(L, f).restype = ct.c_int
     _lib = L
     return L

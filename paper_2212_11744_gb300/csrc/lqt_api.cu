@@ -2,6 +2,7 @@
 // argument validation, workspace layout, dispatch to the kernels, the device
 // status word and the host-buffer convenience call.
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <thread>
 
@@ -514,6 +515,65 @@ const char* lqt_strerror(lqt_status s) {
     case LQT_EUNSUPPORTED: return "dimension not supported by this build";
     default: return "unknown status";
   }
+}
+
+// ---------------------------------------------------------------------------
+// grid method (Sec. VI-B, App. E)
+// ---------------------------------------------------------------------------
+
+static lqt_status validate_grid(const lqt_grid_problem* p) {
+  if (!p) return LQT_EINVAL;
+  if (p->G < 3 || p->G > 16384 || p->substeps < 1 || p->T < 1 || p->T > ((int64_t)1 << 40)) return LQT_EINVAL;
+  if (!(p->dx > 0.0) || !(p->tau > 0.0) || !(p->rho > 0.0)) return LQT_EINVAL;
+  if (p->interp != 0 && p->interp != 1) return LQT_EINVAL;
+  const double vals[] = {p->x_min, p->dx, p->d0, p->d1, p->d2, p->q, p->rho, p->qf, p->tau};
+  for (double v : vals)
+    if (!std::isfinite(v)) return LQT_EINVAL;
+  return LQT_OK;
+}
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
+size_t lqt_grid_workspace_size(const lqt_grid_problem* p, int32_t which) {
+  if (validate_grid(p) != LQT_OK || (which != 0 && which != 1)) return 0;
+  return grid_workspace_bytes(*p, which);
+}
+
+lqt_status lqt_grid_block(const lqt_grid_problem* p, double* Vblock, void* ws, size_t ws_bytes, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate_grid(p);
+  if (s != LQT_OK) return s;
+  if (!Vblock || !aligned8(Vblock)) return LQT_EINVAL;
+  const size_t need = grid_workspace_bytes(*p, 0);
+  if (!ws || ws_bytes < need || !aligned8(ws)) return LQT_EWORKSPACE;
+  if (overlaps(Vblock, (size_t)p->G * p->G * 8, ws, need)) return LQT_EINVAL;
+  return from_cuda(run_grid_block(*p, Vblock, (char*)ws, (cudaStream_t)stream));
+}
+
+lqt_status lqt_grid_combine(const lqt_grid_problem* p, const double* A, const double* B, double* out, void* stream) {
+  t_launches = 0;
+  lqt_status s = validate_grid(p);
+  if (s != LQT_OK) return s;
+  if (!A || !B || !out || !aligned8(A) || !aligned8(B) || !aligned8(out)) return LQT_EINVAL;
+  const size_t bytes = (size_t)p->G * p->G * 8;
+  if (overlaps(out, bytes, A, bytes) || overlaps(out, bytes, B, bytes)) return LQT_EINVAL;
+  return from_cuda(run_grid_combine(*p, A, B, out, (cudaStream_t)stream));
+}
+
+lqt_status lqt_grid_values(const lqt_grid_problem* p, const double* Vblock, double* V, void* ws, size_t ws_bytes,
+                           void* stream) {
+  t_launches = 0;
+  lqt_status s = validate_grid(p);
+  if (s != LQT_OK) return s;
+  if (!Vblock || !V || !aligned8(Vblock) || !aligned8(V)) return LQT_EINVAL;
+  const size_t need = grid_workspace_bytes(*p, 1);
+  if (!ws || ws_bytes < need || !aligned8(ws)) return LQT_EWORKSPACE;
+  const size_t vb = ((size_t)p->T + 1) * p->G * 8, gb = (size_t)p->G * p->G * 8;
+  if (overlaps(V, vb, Vblock, gb) || overlaps(V, vb, ws, need)) return LQT_EINVAL;
+  return from_cuda(run_grid_values(*p, Vblock, V, (char*)ws, (cudaStream_t)stream));
 }
 
 int32_t lqt_last_launch_count(void) { return t_launches; }

@@ -1,0 +1,283 @@
+// The general method on a state grid: the nonlinear scalar example of
+// Sec. VI-B (dx/dt = d0 + d1 x + d2 x^2 + u, running cost q x^2/2 + rho u^2/2,
+// terminal cost qf x^2/2), each conditional value function held as the G x G
+// array V(x_i, s; x_j, s') on the grid x_i = x_min + i dx, combined by the
+// minimisation of Theorem HJB-comb over the grid and refined by the
+// quadratic interpolation of App. E.
+//
+//   block    the one-step function (an explicit Euler step with any control)
+//            combined with itself `substeps` times, left to right;
+//   combine  out(i, j) = min_k A(i, k) + B(k, j), refined;
+//   values   V(., t_k) for k = 0..T.  The model is time-invariant, so every
+//            block has the same conditional value function (Sec. VI-B) and
+//            the scan's partial products are its powers.  The powers
+//            P_{l+1} = P_l (x) P_l are formed once (log2 T products); then for
+//            each bit l, lowest first, every k whose T - k has bit l set
+//            updates w_k <- P_l (x) w_k, all such k and all grid points in one
+//            launch.  After the last bit w_k = V(., t_k).
+//
+// Both products are one kernel: a 16 x 16 tile of outputs per CTA, one output
+// per thread, the reduction index in steps of 32 staged in shared memory and
+// walked in ascending order, strict improvement only (the lowest index wins a
+// tie).  Each candidate costs one FP64 add; the comparison runs on integer
+// keys that order doubles like the FP64 comparison does (the two zeros equal),
+// which keeps the FP64 pipe for the add.  This is tropical (min, +) algebra:
+// no multiply-accumulate, so no tensor-core form applies.
+//
+// Every floating-point expression uses explicit round-to-nearest intrinsics,
+// in the order the definitions state them, so no multiply-add contraction
+// changes a rounding: on the same inputs the grid minimisers are the same as
+// those of any evaluation that follows the same formulas in IEEE double.
+#include <climits>
+
+#include <cuda_runtime.h>
+
+#include "lqt_device.cuh"
+#include "lqt_internal.h"
+
+namespace lqt {
+
+namespace {
+
+struct GridArgs {
+  int32_t G;
+  double x_min, dx, d0, d1, d2, q, rho, qf, tau;
+  int32_t substeps;
+  int64_t T;
+  int32_t interp;
+};
+
+GridArgs grid_args(const lqt_grid_problem& p) {
+  return GridArgs{p.G, p.x_min, p.dx, p.d0, p.d1, p.d2, p.q, p.rho, p.qf, p.tau, p.substeps, p.T, p.interp};
+}
+
+constexpr int kGT = 16;  // output tile edge
+constexpr int kGK = 32;  // reduction step staged in shared memory
+
+__device__ __forceinline__ double grid_x(const GridArgs& a, int i) { return __dadd_rn(a.x_min, __dmul_rn((double)i, a.dx)); }
+
+// Integer key with key(u) < key(v) exactly when u < v for non-NaN doubles
+// (and key(-0) == key(+0)): the bit pattern for u >= +0, its negated
+// magnitude for u <= -0.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 ? LLONG_MIN - b : b;
+}
+
+// App. E: the grid minimum `best` = g_k + f_k at index k lowered by
+// b^2 / (4a), a and b the curvature and slope sums of the quadratics through
+// (k-1, k, k+1) of g and of f; unchanged when a <= 0.
+__device__ __forceinline__ double refine(const GridArgs& a, double best, double gm, double g0, double gp, double fm,
+                                         double f0, double fp) {
+  const double den2 = __dmul_rn(2.0, __dmul_rn(a.dx, a.dx));
+  const double den1 = __dmul_rn(2.0, a.dx);
+  const double ag = __ddiv_rn(__dsub_rn(__dadd_rn(gp, gm), __dmul_rn(2.0, g0)), den2);
+  const double bg = __ddiv_rn(__dsub_rn(gp, gm), den1);
+  const double af = __ddiv_rn(__dsub_rn(__dadd_rn(fp, fm), __dmul_rn(2.0, f0)), den2);
+  const double bf = __ddiv_rn(__dsub_rn(fp, fm), den1);
+  const double cv = __dadd_rn(ag, af), sl = __dadd_rn(bg, bf);
+  if (!(cv > 0.0)) return best;
+  return __dsub_rn(best, __ddiv_rn(__dmul_rn(sl, sl), __dmul_rn(4.0, cv)));
+}
+
+// C(i, j): from x_i to x_j in one step dt = tau / substeps of
+// x' = x + dt (drift(x) + u), so u = (x_j - x_i)/dt - drift(x_i) and the cost
+// is dt (q x_i^2 + rho u^2) / 2.
+__global__ void grid_one_step_kernel(GridArgs a, double* __restrict__ C) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)a.G * a.G) return;
+  const int i = (int)(e / a.G), j = (int)(e % a.G);
+  const double dt = __ddiv_rn(a.tau, (double)a.substeps);
+  const double xi = grid_x(a, i), xj = grid_x(a, j);
+  const double drift = __dadd_rn(__dadd_rn(a.d0, __dmul_rn(a.d1, xi)), __dmul_rn(__dmul_rn(a.d2, xi), xi));
+  const double u = __dsub_rn(__ddiv_rn(__dsub_rn(xj, xi), dt), drift);
+  C[e] = __dmul_rn(__dmul_rn(dt, 0.5), __dadd_rn(__dmul_rn(__dmul_rn(a.q, xi), xi), __dmul_rn(__dmul_rn(a.rho, u), u)));
+}
+
+// Values mode: column c of the product is the c-th k (ascending e = T - k)
+// whose e has bit l set.  Such e run in blocks of 2^l: e = (2m+1) 2^l + r.
+// Row k starts in buffer popc(e) & 1 and moves to the other buffer at every
+// set bit of e, so before level l it is in buffer popc(e >> l) & 1 and after
+// its last set bit in buffer 0.
+struct ValCol {
+  const double* in;
+  double* out;
+};
+
+__device__ __forceinline__ ValCol value_column(const GridArgs& a, int l, int64_t c, double* X0, double* X1) {
+  const int64_t low = ((int64_t)1 << l) - 1;
+  const int64_t e = ((2 * (c >> l) + 1) << l) + (c & low);
+  const int64_t k = a.T - e;
+  const bool odd = __popcll((unsigned long long)(e >> l)) & 1;
+  const int64_t off = k * a.G;
+  return odd ? ValCol{X1 + off, X0 + off} : ValCol{X0 + off, X1 + off};
+}
+
+// kValues = false: out(i, j) = min_k A(i, k) + B(k, j), all G x G row-major.
+// kValues = true:  for column c (see value_column), w_out(i) = min_j A(i, j) + w_in(j)
+//                  with A = P_l; ncols columns.
+// Rows run over i (grid y), columns over j or c (grid x).  In the values mode
+// consecutive threads walk i so that the w_out stores are coalesced.
+template <bool kValues>
+__global__ void __launch_bounds__(kGT* kGT)
+    grid_minplus_kernel(GridArgs a, const double* __restrict__ A, const double* Bm, double* Om, double* X0,
+                        double* X1, int l, int64_t ncols) {
+  __shared__ double As[kGT][kGK + 1];
+  __shared__ double Bs[kGK][kGT + 1];
+  const int G = a.G;
+  const int t = threadIdx.x;
+  const int r_loc = kValues ? t % kGT : t / kGT;  // output row inside the tile
+  const int c_loc = kValues ? t / kGT : t % kGT;  // output column inside the tile
+  const int i0 = blockIdx.y * kGT;
+  const int64_t c0 = (int64_t)blockIdx.x * kGT;
+  const int i = i0 + r_loc;
+  const int64_t c = c0 + c_loc;
+
+  long long bestk = LLONG_MAX;
+  double best = 0.0;
+  int bk = 0;
+  for (int k0 = 0; k0 < G; k0 += kGK) {
+    // A tile: rows i0.., reduction k0.. (consecutive threads along k)
+    for (int e = t; e < kGT * kGK; e += kGT * kGT) {
+      const int r = e / kGK, kk = e % kGK;
+      const int gi = i0 + r, gk = k0 + kk;
+      As[r][kk] = (gi < G && gk < G) ? A[(int64_t)gi * G + gk] : 0.0;
+    }
+    // B tile: reduction k0.., columns c0.. (consecutive threads along the
+    // stored direction)
+    for (int e = t; e < kGT * kGK; e += kGT * kGT) {
+      int kk, cc;
+      if (kValues) {
+        cc = e / kGK; kk = e % kGK;
+      } else {
+        kk = e / kGT; cc = e % kGT;
+      }
+      const int gk = k0 + kk;
+      const int64_t gc = c0 + cc;
+      double v = 0.0;
+      if (gk < G && gc < ncols) {
+        if (kValues) v = value_column(a, l, gc, X0, X1).in[gk];
+        else v = Bm[(int64_t)gk * G + gc];
+      }
+      Bs[kk][cc] = v;
+    }
+    __syncthreads();
+    const int kend = G - k0 < kGK ? G - k0 : kGK;
+    for (int kk = 0; kk < kend; ++kk) {
+      const double v = __dadd_rn(As[r_loc][kk], Bs[kk][c_loc]);
+      const long long key = order_key(v);
+      if (key < bestk) {
+        bestk = key;
+        best = v;
+        bk = k0 + kk;
+      }
+    }
+    __syncthreads();
+  }
+  if (i >= G || c >= ncols) return;
+  const double* Ai = A + (int64_t)i * G;
+  double res = best;
+  if (kValues) {
+    const ValCol col = value_column(a, l, c, X0, X1);
+    if (a.interp && bk > 0 && bk < G - 1)
+      res = refine(a, best, Ai[bk - 1], Ai[bk], Ai[bk + 1], col.in[bk - 1], col.in[bk], col.in[bk + 1]);
+    col.out[i] = res;
+  } else {
+    if (a.interp && bk > 0 && bk < G - 1)
+      res = refine(a, best, Ai[bk - 1], Ai[bk], Ai[bk + 1], Bm[(int64_t)(bk - 1) * G + c], Bm[(int64_t)bk * G + c],
+                   Bm[(int64_t)(bk + 1) * G + c]);
+    Om[(int64_t)i * G + c] = res;
+  }
+  if (!isfinite(res)) flag(kStatusNonFinite);
+}
+
+// Row k of the values starts as phi(x_i) = qf x_i^2 / 2 in the buffer it
+// occupies before level 0: X0 when popc(T - k) is even, so that after its
+// last update it lands in X0.
+__global__ void grid_terminal_kernel(GridArgs a, double* __restrict__ X0, double* __restrict__ X1) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (a.T + 1) * a.G) return;
+  const int64_t k = e / a.G;
+  const double x = grid_x(a, (int)(e % a.G));
+  const double phi = __dmul_rn(__dmul_rn(__dmul_rn(0.5, a.qf), x), x);
+  const bool odd = __popcll((unsigned long long)(a.T - k)) & 1;
+  (odd ? X1 : X0)[e] = phi;
+}
+
+unsigned cdiv_u(int64_t x, int64_t y) { return (unsigned)((x + y - 1) / y); }
+
+int grid_levels(int64_t T) {
+  int L = 0;
+  while (((int64_t)1 << L) <= T) ++L;
+  return L;
+}
+
+// Number of e in [1, T] with bit l set.
+int64_t set_count(int64_t T, int l) {
+  const int64_t blk = (int64_t)1 << (l + 1), half = (int64_t)1 << l;
+  const int64_t full = (T + 1) / blk, rem = (T + 1) % blk;
+  return full * half + (rem > half ? rem - half : 0);
+}
+
+cudaError_t launch_combine(const GridArgs& a, const double* A, const double* B, double* out, cudaStream_t st) {
+  const dim3 grid(cdiv_u(a.G, kGT), cdiv_u(a.G, kGT));
+  grid_minplus_kernel<false><<<grid, kGT * kGT, 0, st>>>(a, A, B, out, nullptr, nullptr, 0, a.G);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t grid_workspace_bytes(const lqt_grid_problem& p, int which) {
+  const size_t GG = (size_t)p.G * p.G;
+  if (which == 0) return 2 * GG * sizeof(double);
+  return ((size_t)grid_levels(p.T) * GG + ((size_t)p.T + 1) * p.G) * sizeof(double);
+}
+
+cudaError_t run_grid_block(const lqt_grid_problem& p, double* Vblock, char* ws, cudaStream_t st) {
+  const GridArgs a = grid_args(p);
+  const size_t GG = (size_t)p.G * p.G;
+  double* C = (double*)ws;
+  double* tmp = C + GG;
+  grid_one_step_kernel<<<cdiv_u((int64_t)GG, 256), 256, 0, st>>>(a, C);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  // M_1 = C, M_{m+1} = M_m (x) C, ping-ponging between Vblock and tmp so that
+  // M_substeps ends in Vblock.
+  double* cur = (p.substeps & 1) ? Vblock : tmp;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cur, C, GG * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  for (int m = 1; m < p.substeps && e == cudaSuccess; ++m) {
+    double* nxt = cur == Vblock ? tmp : Vblock;
+    e = launch_combine(a, cur, C, nxt, st);
+    cur = nxt;
+  }
+  return e;
+}
+
+cudaError_t run_grid_combine(const lqt_grid_problem& p, const double* A, const double* B, double* out,
+                             cudaStream_t st) {
+  return launch_combine(grid_args(p), A, B, out, st);
+}
+
+cudaError_t run_grid_values(const lqt_grid_problem& p, const double* Vblock, double* V, char* ws, cudaStream_t st) {
+  const GridArgs a = grid_args(p);
+  const size_t GG = (size_t)p.G * p.G;
+  const int L = grid_levels(p.T);
+  double* pw = (double*)ws;          // P_0 .. P_{L-1}
+  double* X1 = pw + (size_t)L * GG;  // second buffer of the values (V is the first)
+  cudaError_t e = cudaMemcpyAsync(pw, Vblock, GG * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  for (int l = 1; l < L && e == cudaSuccess; ++l)
+    e = launch_combine(a, pw + (l - 1) * GG, pw + (l - 1) * GG, pw + l * GG, st);
+  if (e != cudaSuccess) return e;
+  grid_terminal_kernel<<<cdiv_u((p.T + 1) * p.G, 256), 256, 0, st>>>(a, V, X1);
+  count_launch();
+  for (int l = 0; l < L; ++l) {
+    const int64_t nc = set_count(p.T, l);
+    const dim3 grid(cdiv_u(nc, kGT), cdiv_u(p.G, kGT));
+    grid_minplus_kernel<true><<<grid, kGT * kGT, 0, st>>>(a, pw + l * GG, nullptr, nullptr, V, X1, l, nc);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lqt

@@ -239,4 +239,11 @@ int scan_chunk_override();
 void set_mixed_precision(bool on);
 bool mixed_precision();
 
+// grid method for the nonlinear scalar example (lqt_grid.cu)
+size_t grid_workspace_bytes(const lqt_grid_problem& p, int which);  // 0: block, 1: values
+cudaError_t run_grid_block(const lqt_grid_problem& p, double* Vblock, char* ws, cudaStream_t st);
+cudaError_t run_grid_combine(const lqt_grid_problem& p, const double* A, const double* B, double* out,
+                             cudaStream_t st);
+cudaError_t run_grid_values(const lqt_grid_problem& p, const double* Vblock, double* V, char* ws, cudaStream_t st);
+
 }  // namespace lqt

@@ -114,3 +114,26 @@ def test_densify_validation_on_host(lib):
     assert L.lqt_densify(hp.ref(), d, d, d, d, d, d, d, d, None, d, ws - 1, None) == _abi.LQT_EWORKSPACE
     hp.struct.K = 17
     assert L.lqt_densify(hp.ref(), d, d, d, d, d, d, d, d, None, d, 1 << 40, None) == _abi.LQT_EUNSUPPORTED
+
+
+def test_grid_validation_on_host(lib):
+    import paper_2212_11744_gb300 as m
+    from paper_2212_11744_gb300 import _abi
+    L = _abi.lib()
+    g = W.falling_body(G=60, T=100)
+    gs = m.grid_struct(g)
+    # block: 2 G^2 doubles; values: G^2 per power (7 powers for T = 100) + (T+1) G
+    assert L.lqt_grid_workspace_size(ct.byref(gs), 0) == 2 * 60 * 60 * 8
+    assert L.lqt_grid_workspace_size(ct.byref(gs), 1) == (7 * 60 * 60 + 101 * 60) * 8
+    assert L.lqt_grid_workspace_size(ct.byref(gs), 2) == 0
+    d = ct.c_void_p(256)
+    need = L.lqt_grid_workspace_size(ct.byref(gs), 1)
+    assert L.lqt_grid_values(ct.byref(gs), d, d, d, need, None) == _abi.LQT_EINVAL  # V overlaps Vblock
+    assert L.lqt_grid_values(ct.byref(gs), d, ct.c_void_p(1 << 30), d, need - 8, None) == _abi.LQT_EWORKSPACE
+    assert L.lqt_grid_combine(ct.byref(gs), d, ct.c_void_p(1 << 30), d, None) == _abi.LQT_EINVAL  # out is A
+    for field, bad in (("G", 2), ("substeps", 0), ("T", 0), ("dx", 0.0), ("rho", -1.0), ("tau", float("nan")),
+                       ("interp", 2)):
+        b = m.grid_struct(g)
+        setattr(b, field, bad)
+        assert L.lqt_grid_workspace_size(ct.byref(b), 0) == 0, field
+        assert L.lqt_grid_block(ct.byref(b), d, d, 1 << 30, None) == _abi.LQT_EINVAL, field
