@@ -393,7 +393,7 @@ typedef struct {
   double q, rho, qf; /* running state weight, control weight (> 0), terminal     */
   double tau;        /* block length (> 0)                                       */
   int32_t substeps;  /* Euler steps per block (>= 1)                             */
-  int64_t T;         /* blocks (>= 1)                                            */
+  int64_t T;         /* blocks, 1 <= T < 2^31                                    */
   int32_t interp;    /* 1: App. E refinement of every minimisation; 0: plain     */
 } lqt_grid_problem;
 

@@ -523,7 +523,7 @@ const char* lqt_strerror(lqt_status s) {
 
 static lqt_status validate_grid(const lqt_grid_problem* p) {
   if (!p) return LQT_EINVAL;
-  if (p->G < 3 || p->G > 16384 || p->substeps < 1 || p->T < 1 || p->T > ((int64_t)1 << 40)) return LQT_EINVAL;
+  if (p->G < 3 || p->G > 16384 || p->substeps < 1 || p->T < 1 || p->T > INT32_MAX) return LQT_EINVAL;
   if (!(p->dx > 0.0) || !(p->tau > 0.0) || !(p->rho > 0.0)) return LQT_EINVAL;
   if (p->interp != 0 && p->interp != 1) return LQT_EINVAL;
   const double vals[] = {p->x_min, p->dx, p->d0, p->d1, p->d2, p->q, p->rho, p->qf, p->tau};

@@ -131,8 +131,8 @@ def test_grid_validation_on_host(lib):
     assert L.lqt_grid_values(ct.byref(gs), d, d, d, need, None) == _abi.LQT_EINVAL  # V overlaps Vblock
     assert L.lqt_grid_values(ct.byref(gs), d, ct.c_void_p(1 << 30), d, need - 8, None) == _abi.LQT_EWORKSPACE
     assert L.lqt_grid_combine(ct.byref(gs), d, ct.c_void_p(1 << 30), d, None) == _abi.LQT_EINVAL  # out is A
-    for field, bad in (("G", 2), ("substeps", 0), ("T", 0), ("dx", 0.0), ("rho", -1.0), ("tau", float("nan")),
-                       ("interp", 2)):
+    for field, bad in (("G", 2), ("G", 16385), ("substeps", 0), ("T", 0), ("T", 1 << 31), ("dx", 0.0),
+                       ("rho", -1.0), ("tau", float("nan")), ("interp", 2)):
         b = m.grid_struct(g)
         setattr(b, field, bad)
         assert L.lqt_grid_workspace_size(ct.byref(b), 0) == 0, field
