@@ -186,8 +186,9 @@ lqt_status lqt_solve_sequential(const lqt_problem *p, const double *x0, double *
  * stage matrices; one thread per sub-interval then integrates only b, eta,
  * zeta.  The elements equal lqt_build_elements' up to rounding.  The grid must
  * be uniform: a sub-interval whose length differs from the first one's by
- * more than 1e-12 relative sets the status word (lqt_get_status gives
- * LQT_EINVAL).  Coefficients not constant, or other n, m: LQT_EUNSUPPORTED.
+ * more than 1e-12 relative plus the rounding of its end points
+ * (8 DBL_EPSILON (|t_j| + |t_j+1| + |t_0| + |t_1|)) sets the status word
+ * (lqt_get_status gives LQT_EINVAL).  Coefficients not constant, or other n, m: LQT_EUNSUPPORTED.
  * lqt_build_elements_invariant: as lqt_build_elements (T+1 elements incl. the
  * terminal one); workspace lqt_workspace_size(p, LQT_WS_INVARIANT).
  * lqt_solve_invariant: as lqt_solve with this build; workspace

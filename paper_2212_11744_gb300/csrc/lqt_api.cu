@@ -419,6 +419,26 @@ size_t lqt_host_staging_size(const lqt_problem* p) {
   return b;
 }
 
+// Sub-intervals j0 .. j0+cnt-1 of d as a problem of its own: the time points
+// and every sampled coefficient start at sub-interval j0's first sample.
+static lqt_problem window_problem(const lqt_problem& d, int64_t j0, int64_t cnt) {
+  lqt_problem w = d;
+  w.T = cnt;
+  w.t = d.t + j0;
+  const size_t n = d.n, m = d.m, nr = d.nr;
+  lqt_coef* cs[7] = {&w.F, &w.L, &w.c, &w.H, &w.X, &w.U, &w.r};
+  const size_t per[7] = {n * n, n * m, n, nr * n, nr * nr, m * m, nr};
+  for (int i = 0; i < 7; ++i)
+    if (cs[i]->ptr) cs[i]->ptr += sample_index(cs[i]->mode, j0, 0, d.K) * per[i];
+  return w;
+}
+
+// Sub-intervals per overlapped chunk of lqt_solve_host.
+static int64_t host_chunk(int64_t T) {
+  const int64_t c = (T + 15) / 16;
+  return c < (1 << 15) ? (1 << 15) : c;
+}
+
 lqt_status lqt_solve_host(const lqt_problem* hp, const double* x0, double* S, double* v, double* zeta, double* x,
                           double* u, double* cost, void* ws, size_t ws_bytes, void* stream) {
   lqt_status s = validate(hp);
@@ -429,24 +449,58 @@ lqt_status lqt_solve_host(const lqt_problem* hp, const double* x0, double* S, do
   if (!ws || ws_bytes < solve_ws + staging) return LQT_EWORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = hp->n, m = hp->m, nr = hp->nr, T1 = (size_t)hp->T + 1;
-  char* cur = (char*)ws + align_up(solve_ws);
+  // Chunked path: for n <= 8 and long horizons the sampled coefficients are
+  // copied in chunks on a second stream while the derived coefficients and
+  // elements of the chunks already copied are built (a chunk's build also
+  // waits for the next chunk's copy, which holds its last sample).
+  const int64_t chunk = host_chunk(hp->T);
+  const bool chunked = hp->n <= 8 && hp->T >= 2 * chunk;
+  cudaStream_t cs = st;
+  cudaEvent_t evs[20] = {};
+  int n_ev = 0;
   cudaError_t e = cudaSuccess;
+  if (chunked) {
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[n_ev++], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[0], st);  // the workspace is free once st's earlier work is done
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evs[0], 0);
+    if (e != cudaSuccess) {
+      if (cs != st) cudaStreamDestroy(cs);
+      if (evs[0]) cudaEventDestroy(evs[0]);
+      return LQT_ECUDA;
+    }
+  }
+  char* cur = (char*)ws + align_up(solve_ws);
+  struct Deferred {
+    const lqt_coef* src;
+    double* dst;
+    size_t per;
+  } deferred[7];
+  int n_def = 0;
   auto stage = [&](const void* src, size_t bytes) -> const double* {
     if (!src || bytes == 0) return nullptr;
     char* dst = cur;
     cur += align_up(bytes);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs);
     return (const double*)dst;
+  };
+  auto stage_coef = [&](const lqt_coef& c, size_t per) -> const double* {
+    if (!c.ptr) return nullptr;
+    if (!chunked || c.mode == LQT_CONST) return stage(c.ptr, coef_bytes_of(c, *hp, per));
+    double* dst = (double*)cur;
+    cur += align_up(coef_bytes_of(c, *hp, per));
+    deferred[n_def++] = Deferred{&c, dst, per};
+    return dst;
   };
   lqt_problem d = *hp;
   d.t = stage(hp->t, T1 * 8);
-  d.F.ptr = stage(hp->F.ptr, coef_bytes_of(hp->F, *hp, n * n));
-  d.L.ptr = stage(hp->L.ptr, coef_bytes_of(hp->L, *hp, n * m));
-  d.c.ptr = stage(hp->c.ptr, coef_bytes_of(hp->c, *hp, n));
-  d.H.ptr = stage(hp->H.ptr, coef_bytes_of(hp->H, *hp, nr * n));
-  d.X.ptr = stage(hp->X.ptr, coef_bytes_of(hp->X, *hp, nr * nr));
-  d.U.ptr = stage(hp->U.ptr, coef_bytes_of(hp->U, *hp, m * m));
-  d.r.ptr = stage(hp->r.ptr, coef_bytes_of(hp->r, *hp, nr));
+  d.F.ptr = stage_coef(hp->F, n * n);
+  d.L.ptr = stage_coef(hp->L, n * m);
+  d.c.ptr = stage_coef(hp->c, n);
+  d.H.ptr = stage_coef(hp->H, nr * n);
+  d.X.ptr = stage_coef(hp->X, nr * nr);
+  d.U.ptr = stage_coef(hp->U, m * m);
+  d.r.ptr = stage_coef(hp->r, nr);
   d.Hf = stage(hp->Hf, nr * n * 8);
   d.Xf = stage(hp->Xf, nr * nr * 8);
   d.rf = stage(hp->rf, nr * 8);
@@ -462,16 +516,71 @@ lqt_status lqt_solve_host(const lqt_problem* hp, const double* x0, double* S, do
   double* dxo = carve(T1 * n * 8);
   double* du = carve(T1 * m * 8);
   double* dc = carve(8);
-  if (e != cudaSuccess) return LQT_ECUDA;
-  s = lqt_solve(&d, dx0, dS, dv, dz, dxo, u ? du : nullptr, dc, ws, solve_ws, stream);
+  if (e == cudaSuccess && chunked) {
+    t_launches = 0;
+    const Layout L = make_layout(d);
+    char* base = (char*)ws;
+    double* Lt = (double*)(base + L.off_Lt);
+    double* Q = (double*)(base + L.off_Q);
+    double* qr = (double*)(base + L.off_qr);
+    double* Ku = (double*)(base + L.off_Ku);
+    const bool ku_const = d.L.mode == LQT_CONST && d.U.mode == LQT_CONST;
+    const ElemPtrs el = carve_elements(d, base + L.coef_bytes);
+    const int64_t P = (d.T + chunk - 1) / chunk;
+    for (int64_t c = 0; c < P && e == cudaSuccess; ++c) {
+      const int64_t j0 = c * chunk, j1 = j0 + chunk < d.T ? j0 + chunk : d.T;
+      for (int k = 0; k < n_def && e == cudaSuccess; ++k) {
+        const Deferred& df = deferred[k];
+        const int64_t s0 = sample_index(df.src->mode, j0, 0, d.K);
+        const int64_t s1 = c == P - 1 ? sample_count(df.src->mode, d.T, d.K) : sample_index(df.src->mode, j1, 0, d.K);
+        e = cudaMemcpyAsync(df.dst + s0 * df.per, df.src->ptr + s0 * df.per, (size_t)(s1 - s0) * df.per * 8,
+                            cudaMemcpyHostToDevice, cs);
+      }
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[n_ev], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(evs[n_ev++], cs);
+    }
+    for (int64_t c = 0; c < P && e == cudaSuccess; ++c) {
+      const int64_t j0 = c * chunk, cnt = (j0 + chunk < d.T ? j0 + chunk : d.T) - j0;
+      e = cudaStreamWaitEvent(st, evs[1 + (c + 1 < P ? c + 1 : P - 1)], 0);
+      if (e != cudaSuccess) break;
+      const lqt_problem pw = window_problem(d, j0, cnt);
+      const Layout Lw = make_layout(pw);
+      Coefs cfw;
+      e = launch_prepare_into(pw, Lw, Lt + sample_index(L.mode_Lt, j0, 0, d.K) * n * L.M,
+                              Q + sample_index(L.mode_Q, j0, 0, d.K) * n * n,
+                              qr + sample_index(L.mode_qr, j0, 0, d.K) * (n + 1), ku_const ? Ku : Ku + j0 * m * n, cfw,
+                              st);
+      const ElemPtrs elw{el.A + j0 * n * n, el.b + j0 * n, el.C + j0 * n * n, el.eta + j0 * n, el.J + j0 * n * n,
+                         el.zeta + j0};
+      if (e == cudaSuccess) e = launch_build_range(pw, Lw, cfw, elw, st);
+    }
+    if (e == cudaSuccess) e = launch_terminal_element(d, el, st);
+    if (e == cudaSuccess) {
+      const Coefs cf = coefs_view(d, L, Lt, Q, qr, Ku);
+      char* team_scr = base + L.coef_bytes + element_bytes(d) + align_up(((size_t)d.T + 1) * 8);
+      char* scan = team_scr + team_build_scratch_bytes(d.n);
+      e = run_value_and_traj(d, L, cf, el, dS, dv, dz, dx0, dxo, u ? du : nullptr, dc, true, true, nullptr, nullptr,
+                             scan, solve_ws - (scan - base), st);
+    }
+  } else if (e == cudaSuccess) {
+    s = lqt_solve(&d, dx0, dS, dv, dz, dxo, u ? du : nullptr, dc, ws, solve_ws, stream);
+  }
+  if (s == LQT_OK && e == cudaSuccess) {
+    e = cudaMemcpyAsync(S, dS, T1 * n * n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, T1 * n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && zeta) e = cudaMemcpyAsync(zeta, dz, T1 * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, dxo, T1 * n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, T1 * m * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && cost) e = cudaMemcpyAsync(cost, dc, 8, cudaMemcpyDeviceToHost, st);
+  }
+  const cudaError_t sync = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = sync;
+  if (chunked) {
+    cudaStreamSynchronize(cs);
+    for (int k = 0; k < n_ev; ++k) cudaEventDestroy(evs[k]);
+    cudaStreamDestroy(cs);
+  }
   if (s != LQT_OK) return s;
-  e = cudaMemcpyAsync(S, dS, T1 * n * n * 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, T1 * n * 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && zeta) e = cudaMemcpyAsync(zeta, dz, T1 * 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(x, dxo, T1 * n * 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, T1 * m * 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && cost) e = cudaMemcpyAsync(cost, dc, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return from_cuda(e);
 }
 

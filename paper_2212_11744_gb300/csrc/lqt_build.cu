@@ -250,7 +250,11 @@ static void launch_qr_identity(const PrepArgs& a, cudaStream_t st) {
   count_launch();
 }
 
-cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* ws, Coefs& cf, cudaStream_t st) {
+// The derived coefficients of problem p into the given arrays (Lt, Q, qr, Ku
+// laid out as the Layout's modes say); cf describes p's coefficients with
+// those arrays.  Q is written only when H is given.
+cudaError_t launch_prepare_into(const lqt_problem& p, const Layout& lay, double* Lt, double* Q, double* qr,
+                                double* Ku, Coefs& cf, cudaStream_t st) {
   PrepArgs a;
   a.n = p.n; a.m = p.m; a.nr = p.nr; a.K = p.K; a.M = lay.M; a.T = p.T;
   a.L = {p.L.ptr, p.L.mode};
@@ -264,10 +268,10 @@ cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* 
   a.cnt_qr = sample_count(lay.mode_qr, p.T, p.K);
   const bool ku_const = p.L.mode == LQT_CONST && p.U.mode == LQT_CONST;
   a.cnt_Ku = ku_const ? 1 : p.T + 1;
-  a.Lt = (double*)(ws + lay.off_Lt);
-  a.Q = (double*)(ws + lay.off_Q);
-  a.qr = (double*)(ws + lay.off_qr);
-  a.Ku = (double*)(ws + lay.off_Ku);
+  a.Lt = Lt;
+  a.Q = Q;
+  a.qr = qr;
+  a.Ku = Ku;
   // Lt and Ku always; H^T X H only when H is given; H^T X r by the dedicated
   // kernel when H is the identity.
   const bool h_identity = p.H.ptr == nullptr;
@@ -296,15 +300,28 @@ cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* 
     prepare_kernel<<<dim3((unsigned)blocks, 4), threads, 0, st>>>(a);
     count_launch();
   }
+  cf = coefs_view(p, lay, Lt, Q, qr, Ku);
+  return cudaGetLastError();
+}
+
+Coefs coefs_view(const lqt_problem& p, const Layout& lay, double* Lt, double* Q, double* qr, double* Ku) {
+  const bool h_identity = p.H.ptr == nullptr;
+  const bool ku_const = p.L.mode == LQT_CONST && p.U.mode == LQT_CONST;
+  Coefs cf;
   cf.F = {p.F.ptr, p.F.mode};
   cf.c = {p.c.ptr, p.c.ptr ? p.c.mode : kConst};
-  cf.Lt = {a.Lt, lay.mode_Lt};
-  cf.Q = h_identity ? Coef{p.X.ptr, p.X.mode} : Coef{a.Q, lay.mode_Q};
-  cf.qr = {a.qr, lay.mode_qr};
-  cf.Ku = a.Ku;
+  cf.Lt = {Lt, lay.mode_Lt};
+  cf.Q = h_identity ? Coef{p.X.ptr, p.X.mode} : Coef{Q, lay.mode_Q};
+  cf.qr = {qr, lay.mode_qr};
+  cf.Ku = Ku;
   cf.Ku_per_boundary = ku_const ? 0 : 1;
   cf.M = lay.M;
-  return cudaGetLastError();
+  return cf;
+}
+
+cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* ws, Coefs& cf, cudaStream_t st) {
+  return launch_prepare_into(p, lay, (double*)(ws + lay.off_Lt), (double*)(ws + lay.off_Q),
+                             (double*)(ws + lay.off_qr), (double*)(ws + lay.off_Ku), cf, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -735,6 +752,21 @@ static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st) {
     default: return cudaErrorInvalidValue;
   }
   return cudaSuccess;
+}
+
+// Elements 0..T-1 of p alone (no terminal element), n <= 8.
+cudaError_t launch_build_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                               cudaStream_t st) {
+  BuildArgs a;
+  a.T = p.T; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
+  switch (p.n) {
+    case 1: return launch_build_n<1>(a, lay.M, st);
+    case 2: return launch_build_n<2>(a, lay.M, st);
+    case 3: return launch_build_n<3>(a, lay.M, st);
+    case 4: return launch_build_n<4>(a, lay.M, st);
+    case 8: return launch_build_n<8>(a, lay.M, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,

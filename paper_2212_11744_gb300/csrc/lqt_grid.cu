@@ -17,12 +17,17 @@
 //            launch.  After the last bit w_k = V(., t_k).
 //
 // Both products are one kernel: a 16 x 16 tile of outputs per CTA, one output
-// per thread, the reduction index in steps of 32 staged in shared memory and
-// walked in ascending order, strict improvement only (the lowest index wins a
-// tie).  Each candidate costs one FP64 add; the comparison runs on integer
-// keys that order doubles like the FP64 comparison does (the two zeros equal),
-// which keeps the FP64 pipe for the add.  This is tropical (min, +) algebra:
-// no multiply-accumulate, so no tensor-core form applies.
+// per thread, the reduction index in steps of 32 staged in shared memory.  The
+// minimum is defined on FP64 sums, ascending k, strict improvement only (the
+// lowest index wins a tie).  GB300 retires FP64 adds at 1/64 of its FP32
+// rate, so every candidate is first screened in FP32 (a bracket around its
+// sum) and only the few whose bracket reaches the smallest upper bound are
+// summed in FP64; the screen provably keeps every k that could be the FP64
+// minimum, so the result is the one of the plain FP64 scan (which remains the
+// path for operands outside the screen's float range).  FP64 comparisons run
+// on integer keys that order doubles like the FP64 comparison does (the two
+// zeros equal).  This is tropical (min, +) algebra: no multiply-accumulate, so
+// no tensor-core form applies.
 //
 // Every floating-point expression uses explicit round-to-nearest intrinsics,
 // in the order the definitions state them, so no multiply-add contraction
@@ -113,38 +118,136 @@ __device__ __forceinline__ ValCol value_column(const GridArgs& a, int l, int64_t
   return odd ? ValCol{X1 + off, X0 + off} : ValCol{X0 + off, X1 + off};
 }
 
-// kValues = false: out(i, j) = min_k A(i, k) + B(k, j), all G x G row-major.
-// kValues = true:  for column c (see value_column), w_out(i) = min_j A(i, j) + w_in(j)
-//                  with A = P_l; ncols columns.
-// Rows run over i (grid y), columns over j or c (grid x).  In the values mode
-// consecutive threads walk i so that the w_out stores are coalesced.
+// Operands of one product.  kValues = false: A(i, k), B(k, j), out(i, j), all
+// G x G row-major.  kValues = true: A = P_l, column c of B is w_in of the c-th
+// updated row (see value_column), out column c is its w_out.
 template <bool kValues>
-__global__ void __launch_bounds__(kGT* kGT)
-    grid_minplus_kernel(GridArgs a, const double* __restrict__ A, const double* Bm, double* Om, double* X0,
-                        double* X1, int l, int64_t ncols) {
-  __shared__ double As[kGT][kGK + 1];
-  __shared__ double Bs[kGK][kGT + 1];
-  const int G = a.G;
-  const int t = threadIdx.x;
-  const int r_loc = kValues ? t % kGT : t / kGT;  // output row inside the tile
-  const int c_loc = kValues ? t / kGT : t % kGT;  // output column inside the tile
-  const int i0 = blockIdx.y * kGT;
-  const int64_t c0 = (int64_t)blockIdx.x * kGT;
-  const int i = i0 + r_loc;
-  const int64_t c = c0 + c_loc;
+struct Operands {
+  const GridArgs& a;
+  const double* __restrict__ A;
+  const double* Bm;
+  double* Om;
+  double* X0;
+  double* X1;
+  int l;
+  __device__ __forceinline__ double av(int i, int k) const { return A[(int64_t)i * a.G + k]; }
+  // Column c of B: combine mode strides by G, values mode is contiguous.
+  __device__ __forceinline__ const double* bcol(int64_t c) const {
+    return kValues ? value_column(a, l, c, X0, X1).in : Bm + c;
+  }
+  __device__ __forceinline__ double bv(const double* col, int k) const {
+    return kValues ? col[k] : col[(int64_t)k * a.G];
+  }
+};
 
+// FP32 screen of a grid minimum (exactness argument below).  The operands are
+// truncated to float by bit operations (relative error < 2^-23; magnitudes
+// below 2^-126 become 0), summed in float, and bracketed:
+//   lo_k = s_k - c t_k - d  <=  g_k + f_k  <=  hi_k = s_k + c t_k,
+// t_k = |a_k| + |b_k|, c = 2^-20, d = 2^-100, with margins of more than four
+// times the truncation and rounding errors and of the gap between two doubles
+// that round to the same FP64 sum.  With U = min_k hi_k (+ d), every k whose
+// FP64 sum g_k + f_k equals the FP64 minimum has lo_k <= U; every k with
+// lo_k > U has a larger FP64 sum.  So the exact minimum, with the lowest-index
+// rule, is taken over the survivors lo_k <= U alone, in ascending k, in FP64.
+// Operands of magnitude >= 2^100 (or not finite) fall outside the screen's
+// float range: a CTA that meets one takes the FP64 path for all its outputs.
+constexpr float kScreenC = 9.5367431640625e-07f;  // 2^-20
+constexpr float kScreenD = 7.888609052210118e-31f;  // 2^-100
+constexpr float kScreenPad = 1.329227995784916e+36f;  // 2^120: k beyond the grid
+constexpr int kMaxSurvivors = 4;
+
+__device__ __forceinline__ bool screen_range(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return ((b >> 52) & 0x7ff) < 1023 + 100;
+}
+
+// Truncation toward zero of a double in the screen's range to float.
+__device__ __forceinline__ float screen_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ff);
+  if (eb < 1023 - 126) return 0.0f;
+  const unsigned fb = ((unsigned)(b >> 63) << 31) | ((unsigned)(eb - 1023 + 127) << 23) |
+                      (unsigned)((b >> 29) & 0x7fffff);
+  return __uint_as_float(fb);
+}
+
+union GridSmem {
+  struct {
+    double A[kGT][kGK + 1];
+    double B[kGK][kGT + 1];
+  } d;  // FP64 path
+  struct {
+    float A[kGT][kGK + 2];
+    float Bt[kGT][kGK + 2];  // B transposed: one row of k per output column
+  } f;  // screen; rows of 34 floats keep float2 reads aligned and conflict-free
+};
+
+__device__ __forceinline__ float screen_hi(float a, float b) {
+  return __fmaf_rn(kScreenC, __fadd_rn(fabsf(a), fabsf(b)), __fadd_rn(a, b));
+}
+__device__ __forceinline__ float screen_lo(float a, float b) {
+  return __fmaf_rn(-kScreenC, __fadd_rn(fabsf(a), fabsf(b)), __fadd_rn(a, b));
+}
+
+// Float tiles of A (rows i0.., reduction k0..) and B (reduction k0..,
+// columns c0..); k beyond the grid holds kScreenPad.  Returns whether an
+// operand lies outside the screen's range.
+template <bool kValues>
+__device__ __forceinline__ bool stage_float(const Operands<kValues>& op, GridSmem& sm, int t, int i0, int64_t c0,
+                                            int64_t ncols, int k0) {
+  const int G = op.a.G;
+  bool bad = false;
+  for (int e = t; e < kGT * kGK; e += kGT * kGT) {
+    const int r = e / kGK, kk = e % kGK;
+    const int gi = i0 + r, gk = k0 + kk;
+    float v = kScreenPad;
+    if (gk < G) {
+      v = 0.0f;
+      if (gi < G) {
+        const double x = op.av(gi, gk);
+        bad |= !screen_range(x);
+        v = screen_float(x);
+      }
+    }
+    sm.f.A[r][kk] = v;
+  }
+  for (int e = t; e < kGT * kGK; e += kGT * kGT) {
+    int kk, cc;
+    if (kValues) {
+      cc = e / kGK; kk = e % kGK;
+    } else {
+      kk = e / kGT; cc = e % kGT;
+    }
+    const int gk = k0 + kk;
+    const int64_t gc = c0 + cc;
+    float v = kScreenPad;
+    if (gk < G) {
+      v = 0.0f;
+      if (gc < ncols) {
+        const double x = op.bv(op.bcol(gc), gk);
+        bad |= !screen_range(x);
+        v = screen_float(x);
+      }
+    }
+    sm.f.Bt[cc][kk] = v;
+  }
+  return bad;
+}
+
+// The FP64 evaluation of every candidate (CTAs whose operands leave the
+// screen's range): double tiles, ascending k, strict improvement.
+template <bool kValues>
+__device__ __forceinline__ void fp64_scan(const Operands<kValues>& op, GridSmem& sm, int t, int i0, int64_t c0,
+                                          int64_t ncols, int r_loc, int c_loc, double& best, int& bk) {
+  const int G = op.a.G;
   long long bestk = LLONG_MAX;
-  double best = 0.0;
-  int bk = 0;
   for (int k0 = 0; k0 < G; k0 += kGK) {
-    // A tile: rows i0.., reduction k0.. (consecutive threads along k)
     for (int e = t; e < kGT * kGK; e += kGT * kGT) {
       const int r = e / kGK, kk = e % kGK;
       const int gi = i0 + r, gk = k0 + kk;
-      As[r][kk] = (gi < G && gk < G) ? A[(int64_t)gi * G + gk] : 0.0;
+      sm.d.A[r][kk] = (gi < G && gk < G) ? op.av(gi, gk) : 0.0;
     }
-    // B tile: reduction k0.., columns c0.. (consecutive threads along the
-    // stored direction)
     for (int e = t; e < kGT * kGK; e += kGT * kGT) {
       int kk, cc;
       if (kValues) {
@@ -154,17 +257,12 @@ __global__ void __launch_bounds__(kGT* kGT)
       }
       const int gk = k0 + kk;
       const int64_t gc = c0 + cc;
-      double v = 0.0;
-      if (gk < G && gc < ncols) {
-        if (kValues) v = value_column(a, l, gc, X0, X1).in[gk];
-        else v = Bm[(int64_t)gk * G + gc];
-      }
-      Bs[kk][cc] = v;
+      sm.d.B[kk][cc] = (gk < G && gc < ncols) ? op.bv(op.bcol(gc), gk) : 0.0;
     }
     __syncthreads();
     const int kend = G - k0 < kGK ? G - k0 : kGK;
     for (int kk = 0; kk < kend; ++kk) {
-      const double v = __dadd_rn(As[r_loc][kk], Bs[kk][c_loc]);
+      const double v = __dadd_rn(sm.d.A[r_loc][kk], sm.d.B[kk][c_loc]);
       const long long key = order_key(v);
       if (key < bestk) {
         bestk = key;
@@ -174,20 +272,97 @@ __global__ void __launch_bounds__(kGT* kGT)
     }
     __syncthreads();
   }
-  if (i >= G || c >= ncols) return;
-  const double* Ai = A + (int64_t)i * G;
-  double res = best;
-  if (kValues) {
-    const ValCol col = value_column(a, l, c, X0, X1);
-    if (a.interp && bk > 0 && bk < G - 1)
-      res = refine(a, best, Ai[bk - 1], Ai[bk], Ai[bk + 1], col.in[bk - 1], col.in[bk], col.in[bk + 1]);
-    col.out[i] = res;
-  } else {
-    if (a.interp && bk > 0 && bk < G - 1)
-      res = refine(a, best, Ai[bk - 1], Ai[bk], Ai[bk + 1], Bm[(int64_t)(bk - 1) * G + c], Bm[(int64_t)bk * G + c],
-                   Bm[(int64_t)(bk + 1) * G + c]);
-    Om[(int64_t)i * G + c] = res;
+}
+
+// One output (i, c) per thread, a 16 x 16 tile per CTA: the FP32 screen over
+// all k (two passes: the bound U, then the survivors), the FP64 minimum over
+// the survivors, App. E's refinement, the store.  Rows run over i (grid y),
+// columns over j or c (grid x); in the values mode consecutive threads walk i
+// so that the w_out stores are coalesced.
+template <bool kValues>
+__global__ void __launch_bounds__(kGT* kGT, 4)
+    grid_minplus_kernel(GridArgs a, const double* __restrict__ A, const double* Bm, double* Om, double* X0,
+                        double* X1, int l, int64_t ncols) {
+  __shared__ GridSmem sm;
+  const Operands<kValues> op{a, A, Bm, Om, X0, X1, l};
+  const int G = a.G;
+  const int t = threadIdx.x;
+  const int r_loc = kValues ? t % kGT : t / kGT;  // output row inside the tile
+  const int c_loc = kValues ? t / kGT : t % kGT;  // output column inside the tile
+  const int i0 = blockIdx.y * kGT;
+  const int64_t c0 = (int64_t)blockIdx.x * kGT;
+  const int i = i0 + r_loc;
+  const int64_t c = c0 + c_loc;
+  const bool valid = i < G && c < ncols;
+
+  double best = 0.0;
+  int bk = 0;
+  // pass 1: U = min_k hi_k
+  bool bad = false;
+  float U = __int_as_float(0x7f800000);  // +inf
+  for (int k0 = 0; k0 < G; k0 += kGK) {
+    bad |= stage_float(op, sm, t, i0, c0, ncols, k0);
+    __syncthreads();
+    const int kend = G - k0 < kGK ? G - k0 : kGK;
+    float U1 = U;  // two chains
+    for (int kk = 0; kk < kend; kk += 2) {  // an odd kend reads one padded k
+      const float2 a2 = *reinterpret_cast<const float2*>(&sm.f.A[r_loc][kk]);
+      const float2 b2 = *reinterpret_cast<const float2*>(&sm.f.Bt[c_loc][kk]);
+      U = fminf(U, screen_hi(a2.x, b2.x));
+      U1 = fminf(U1, screen_hi(a2.y, b2.y));
+    }
+    U = fminf(U, U1);
+    __syncthreads();
   }
+  if (__syncthreads_or(bad)) {
+    fp64_scan(op, sm, t, i0, c0, ncols, r_loc, c_loc, best, bk);
+  } else {
+    // pass 2: survivors lo_k <= U + d, ascending, up to kMaxSurvivors packed
+    // as 16-bit indices (G <= 16384)
+    const float Ub = __fadd_ru(U, kScreenD);
+    unsigned long long pk = 0;
+    int ns = 0;
+    for (int k0 = 0; k0 < G; k0 += kGK) {
+      stage_float(op, sm, t, i0, c0, ncols, k0);
+      __syncthreads();
+      const int kend = G - k0 < kGK ? G - k0 : kGK;
+      for (int kk = 0; kk < kend; kk += 2) {
+        const float2 a2 = *reinterpret_cast<const float2*>(&sm.f.A[r_loc][kk]);
+        const float2 b2 = *reinterpret_cast<const float2*>(&sm.f.Bt[c_loc][kk]);
+        if (screen_lo(a2.x, b2.x) <= Ub) {
+          if (ns < kMaxSurvivors) pk |= (unsigned long long)(k0 + kk) << (16 * ns);
+          ++ns;
+        }
+        if (screen_lo(a2.y, b2.y) <= Ub) {  // a padded k never passes
+          if (ns < kMaxSurvivors) pk |= (unsigned long long)(k0 + kk + 1) << (16 * ns);
+          ++ns;
+        }
+      }
+      __syncthreads();
+    }
+    if (!valid) return;
+    const double* col = op.bcol(c);
+    long long bestk = LLONG_MAX;
+    const int cnt = ns <= kMaxSurvivors ? ns : G;  // too many survivors: every k
+    for (int r = 0; r < cnt; ++r) {
+      const int k = ns <= kMaxSurvivors ? (int)((pk >> (16 * r)) & 0xffff) : r;
+      const double v = __dadd_rn(op.av(i, k), op.bv(col, k));
+      const long long key = order_key(v);
+      if (key < bestk) {
+        bestk = key;
+        best = v;
+        bk = k;
+      }
+    }
+  }
+  if (!valid) return;
+  const double* col = op.bcol(c);
+  double res = best;
+  if (a.interp && bk > 0 && bk < G - 1)
+    res = refine(a, best, op.av(i, bk - 1), op.av(i, bk), op.av(i, bk + 1), op.bv(col, bk - 1), op.bv(col, bk),
+                 op.bv(col, bk + 1));
+  if (kValues) value_column(a, l, c, X0, X1).out[i] = res;
+  else Om[(int64_t)i * G + c] = res;
   if (!isfinite(res)) flag(kStatusNonFinite);
 }
 

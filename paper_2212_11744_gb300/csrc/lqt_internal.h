@@ -95,6 +95,11 @@ void reset_launch_count();
 // launchers (defined in the .cu files, dispatched on n)
 // -------------------------------------------------------------------------
 cudaError_t launch_prepare_coefs(const lqt_problem& p, const Layout& lay, char* ws, Coefs& out, cudaStream_t s);
+cudaError_t launch_prepare_into(const lqt_problem& p, const Layout& lay, double* Lt, double* Q, double* qr,
+                                double* Ku, Coefs& cf, cudaStream_t st);
+Coefs coefs_view(const lqt_problem& p, const Layout& lay, double* Lt, double* Q, double* qr, double* Ku);
+cudaError_t launch_build_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                               cudaStream_t st);
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                          cudaStream_t s, double* team_scratch = nullptr);
 // n = 16, 64 (team kernels, lqt_team.cu)

@@ -4,6 +4,8 @@
 // integration.  The method is described in lqt_invariant.cu.
 #pragma once
 
+#include <cfloat>
+
 #include <cuda_runtime.h>
 
 #include "lqt_device.cuh"
@@ -92,13 +94,21 @@ __device__ __forceinline__ void bez_rhs(const BEZ<N>& y, const double* __restric
   k.zeta = z;
 }
 
+// Sub-interval j has the first one's length: equal to 1e-12 relative plus
+// the rounding of the time points themselves (a linspace over [0, 100] with
+// 2^20 sub-intervals has lengths that differ by ~1e-11 relative).
+__device__ __forceinline__ bool same_length(const double* t, int64_t j) {
+  const double h = t[j + 1] - t[j], h0 = t[1] - t[0];
+  const double tol = 1e-12 * fabs(h0) + 8.0 * DBL_EPSILON * (fabs(t[j]) + fabs(t[j + 1]) + fabs(t[0]) + fabs(t[1]));
+  return fabs(h - h0) <= tol;
+}
+
 // Element j of one problem into the public arrays at index g.
 template <int N, int M>
 __device__ __forceinline__ void inv_element(const Coefs& cf, const double* t, int64_t j, int32_t K,
                                             const double* __restrict__ table, const ElemPtrs& out, int64_t g) {
   const double h = (t[j + 1] - t[j]) / K;
-  const double h0 = (t[1] - t[0]) / K;
-  if (!(fabs(h - h0) <= 1e-12 * fabs(h0))) flag(kStatusNonUniform);
+  if (!same_length(t, j)) flag(kStatusNonUniform);
   constexpr int64_t SD = 2 * N * M + 2 * N * N;
   const double* F = cf.F.ptr;
   const double* Lt = cf.Lt.ptr;
@@ -161,8 +171,7 @@ __device__ __forceinline__ void inv_element_warp(int lane, const Coefs& cf, cons
   double* k = yt + V;
   double* w = k + V;
   const double h = (t[j + 1] - t[j]) / K;
-  const double h0 = (t[1] - t[0]) / K;
-  if (lane == 0 && !(fabs(h - h0) <= 1e-12 * fabs(h0))) flag(kStatusNonUniform);
+  if (lane == 0 && !same_length(t, j)) flag(kStatusNonUniform);
   const double* F = cf.F.ptr;
   const double* Lt = cf.Lt.ptr;
   for (int e = lane; e < V; e += 32) y[e] = 0.0;

@@ -4,7 +4,9 @@ the C ABI against the oracle.
 Both sides evaluate the same IEEE double formulas in the same order without
 multiply-add contraction (the oracle is ISO C compiled without contraction, the
 kernels use explicit round-to-nearest intrinsics), so the grid minimisers agree
-and the results agree bit for bit: these tests ask for equality.
+and the results agree bit for bit: these tests ask for equality.  The kernel
+screens candidates in FP32 before the FP64 minimum; the edge cases below aim at
+that screen (ties, operands outside its range, underflow, cancellation).
 """
 import numpy as np
 import pytest
@@ -45,6 +47,55 @@ def test_combine_matches_oracle(G, interp):
     torch.cuda.synchronize()
     assert lqt.lqt_get_status() == 0
     same(got, oracle.grid_combine(g, A, B), "combine")
+
+
+def _screen_case(kind, G, rng):
+    """Operands aimed at the FP32 screen of the kernel: exact ties, ties to the
+    last bits, magnitudes outside its range, values near the float underflow,
+    cancellation between huge operands."""
+    x = np.linspace(-6.0, 6.0, G)
+    if kind == "all_ties":
+        return np.full((G, G), 2.5), np.full((G, G), 1.0)
+    if kind == "last_bit_ties":
+        base = 3.0 + rng.integers(0, 3, (G, G)) * np.spacing(3.0)
+        return base, 1.0 + rng.integers(0, 2, (G, G)) * np.spacing(1.0)
+    if kind == "out_of_range":
+        A = (x[:, None] - x[None, :]) ** 2
+        A[G // 3, 0] = 1e31  # above 2^100: the tile takes the FP64 path
+        return A, (x[:, None] + 0.5 * x[None, :]) ** 2
+    if kind == "tiny":
+        return rng.standard_normal((G, G)) * 1e-38, rng.standard_normal((G, G)) * 1e-39
+    if kind == "cancellation":
+        A = rng.uniform(-1e29, 1e29, (G, G))
+        return A, -A.T + rng.standard_normal((G, G))
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["all_ties", "last_bit_ties", "out_of_range", "tiny", "cancellation"])
+@pytest.mark.parametrize("interp", [False, True])
+def test_combine_screen_edge_cases(kind, interp):
+    import paper_2212_11744_gb300 as lqt
+    G = 45
+    g = W.falling_body(G=G, T=1, interp=interp)
+    A, B = _screen_case(kind, G, np.random.default_rng(77))
+    got = lqt.lqt_grid_combine(g, dev(A), dev(B))
+    torch.cuda.synchronize()
+    lqt.lqt_get_status()
+    same(got, oracle.grid_combine(g, A, B), kind)
+
+
+def test_infinite_operands_take_the_fp64_path():
+    import paper_2212_11744_gb300 as lqt
+    G = 40
+    g = W.falling_body(G=G, T=1, interp=False)
+    x = g.grid()
+    A = (x[:, None] - x[None, :]) ** 2
+    A[:, -1] = np.inf  # never the minimum
+    B = (x[:, None] + 1.0) ** 2 + 0.0 * x[None, :]
+    got = lqt.lqt_grid_combine(g, dev(A), dev(B))
+    torch.cuda.synchronize()
+    assert lqt.lqt_get_status() == 0
+    same(got, oracle.grid_combine(g, A, B), "inf")
 
 
 @pytest.mark.parametrize("G,substeps", [(61, 10), (61, 1), (61, 3), (201, 10), (20, 10), (40, 10)])

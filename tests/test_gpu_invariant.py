@@ -93,3 +93,20 @@ def test_batched_invariant_build_matches_oracle(n):
         got = bt.problem_slice(out, b)
         for k in ("S", "v", "zeta", "x", "u"):
             assert relerr(got[k].cpu().numpy(), ref[k]) <= TOL, (b, k)
+
+
+def test_long_uniform_grid_is_accepted():
+    """A linspace over [0, 1310.72] with 2^16 sub-intervals: lengths differ by
+    up to 1.05e-11 relative through the rounding of t alone, which is not a
+    non-uniform grid.  The shared A, C, J are integrated with the first
+    sub-interval's length, the oracle's with each one's own, so they agree to
+    that relative spread (bound 1e-10), the rest as in the cases above."""
+    import paper_2212_11744_gb300 as lqt
+    p = W.batched_member(17, T=1 << 16, n=2)
+    p.t = W.uniform_grid(0.0, 0.02 * p.T, p.T)
+    ref = oracle.build_elements(p)
+    got = lqt.lqt_build_elements_invariant(lqt.DeviceProblem(p))
+    torch.cuda.synchronize()
+    assert lqt.lqt_get_status() == 0
+    for k in ("A", "b", "C", "eta", "J", "zeta"):
+        assert relerr(to_np(got[k]), ref[k]) <= 1e-10, k

@@ -169,8 +169,23 @@ def test_sequential_sweep_matches_oracle(name, make):
     check_solution(out, ref, label=name)
 
 
-def test_solve_host_matches_device():
-    p = W.point_mass_2d(T=777, K=4)
+HOST_CASES = [
+    ("point_mass_T777", lambda: W.point_mass_2d(T=777, K=4)),  # one piece
+    # chunked: coefficient copies overlapped with the builds of earlier chunks
+    ("point_mass_T2e17_plus_5", lambda: W.point_mass_2d(T=(1 << 17) + 5, K=4)),
+    ("general_n3_per_interval_T70001", lambda: W.general_time_varying(
+        3, 2, 2, T=70001, K=2, seed=61, tf=3.0, modes={"F": W.PER_INTERVAL, "L": W.PER_INTERVAL, "c": W.CONST,
+                                                     "H": W.CONST, "X": W.PER_INTERVAL, "U": W.PER_INTERVAL,
+                                                     "r": W.PER_INTERVAL})),
+    ("general_n2_per_stage_T65536", lambda: W.general_time_varying(2, 1, 2, T=65536, K=2, seed=62, tf=3.0)),
+]
+
+
+@pytest.mark.parametrize("name,make", HOST_CASES, ids=[c[0] for c in HOST_CASES])
+def test_solve_host_matches_device(name, make):
+    """lqt_solve_host (host buffers in, host buffers out) gives lqt_solve's
+    results bit for bit, also when it copies and builds in overlapped chunks."""
+    p = make()
     m = lqt()
     dp = m.DeviceProblem(p)
     dev = m.lqt_solve(dp)
