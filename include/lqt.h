@@ -399,8 +399,9 @@ typedef struct {
 } lqt_grid_problem;
 
 /* Workspace bytes: which = 0 for lqt_grid_block (2 G^2 doubles), 1 for
- * lqt_grid_values (G^2 ceil(log2(T+1)) + (T+1) G doubles).  0 when p is
- * invalid or `which` unknown. */
+ * lqt_grid_values (3 G^2 ceil(log2(T+1)) + 1 + (T+1) G doubles: the powers,
+ * their App. E curvatures and slopes, one value buffer).  0 when p is invalid
+ * or `which` unknown. */
 size_t lqt_grid_workspace_size(const lqt_grid_problem *p, int32_t which);
 
 /* The block's conditional value function Vblock (G x G, device) as described

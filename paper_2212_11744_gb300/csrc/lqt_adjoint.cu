@@ -707,26 +707,29 @@ __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const
 
 }  // namespace warp
 
-// Shared-memory doubles of one warp of rk4_adjoint_warp_kernel.
+// Shared-memory doubles of one warp of rk4_adjoint_warp_kernel: five element
+// buffers (the forward phase uses four, the reverse phase five, in turn),
+// B, Fb, Bb, Qb, the temporaries, and the per-sample q, rho adjoints.
 __host__ __device__ constexpr int rk4w_smem_doubles() {
-  return 11 * AS + 8 * AN * AN + 4 * AN + (2 * 8 + 1) * AN + (2 * 8 + 1) + 8;
+  return 5 * AS + 8 * AN * AN + 4 * AN + (2 * 8 + 1) * AN + (2 * 8 + 1) + 8;
 }
 
-__global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
+__global__ void __launch_bounds__(32, 15) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x;
   const int n = a.n, nn = n * n, fs = fe_size(n), K = a.K, M = a.M;
+  // forward phase: y (the state), ys (a stage input), ka (k1 + 2 k2 + 2 k3),
+  // kn (the stage just evaluated); reverse phase: y (a stage input), yb, kb
+  // (one stage's output adjoint), acc (its input adjoint), kbs (the step's
+  // output adjoint)
   double* y = sm;
-  double* k1 = y + AS;
-  double* k2 = k1 + AS;
-  double* k3 = k2 + AS;
-  double* y2 = k3 + AS;
-  double* y3 = y2 + AS;
-  double* y4 = y3 + AS;
-  double* yb = y4 + AS;
-  double* kb = yb + AS;   // one stage's output adjoint at a time
-  double* acc = kb + AS;  // a stage's input adjoint
-  double* kbs = acc + AS; // the step's h-weighted output adjoint
+  double* ys_ = y + AS;
+  double* ka = ys_ + AS;
+  double* kn = ka + AS;
+  double* yb = ys_;
+  double* kb = ka;
+  double* acc = kn;
+  double* kbs = kn + AS;
   double* B = kbs + AS;
   double* Fb = B + AN * AN;
   double* Bb = Fb + AN * AN;
@@ -770,42 +773,41 @@ __global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
       const double* q1 = qr_at(2 * i + 2);
       const double* q2 = qr_at(2 * i + 1);
       const double* q3 = qr_at(2 * i);
-      warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], k1, tmp);
+      warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], ka, tmp);  // k1
       for (int e = lane; e < fs; e += 32) {
         st[e] = y[e];
-        y2[e] = y[e] - 0.5 * h * k1[e];
-        st[fs + e] = y2[e];
+        ys_[e] = y[e] - 0.5 * h * ka[e];
+        st[fs + e] = ys_[e];
       }
       warp::sync();
-      warp::rhs_full(lane, n, y2, F, B, Q, q2, q2[n], k2, tmp);
+      warp::rhs_full(lane, n, ys_, F, B, Q, q2, q2[n], kn, tmp);  // k2
       for (int e = lane; e < fs; e += 32) {
-        y3[e] = y[e] - 0.5 * h * k2[e];
-        st[2 * fs + e] = y3[e];
+        ys_[e] = y[e] - 0.5 * h * kn[e];
+        st[2 * fs + e] = ys_[e];
+        ka[e] = ka[e] + 2.0 * kn[e];
       }
       warp::sync();
-      warp::rhs_full(lane, n, y3, F, B, Q, q2, q2[n], k3, tmp);
+      warp::rhs_full(lane, n, ys_, F, B, Q, q2, q2[n], kn, tmp);  // k3
       for (int e = lane; e < fs; e += 32) {
-        y4[e] = y[e] - h * k3[e];
-        st[3 * fs + e] = y4[e];
+        ys_[e] = y[e] - h * kn[e];
+        st[3 * fs + e] = ys_[e];
+        ka[e] = ka[e] + 2.0 * kn[e];
       }
       warp::sync();
-      warp::rhs_full(lane, n, y4, F, B, Q, q3, q3[n], y2, tmp);  // k4 into y2
-      for (int e = lane; e < fs; e += 32) y[e] = y[e] - (h / 6.0) * (k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + y2[e]);
+      warp::rhs_full(lane, n, ys_, F, B, Q, q3, q3[n], kn, tmp);  // k4
+      for (int e = lane; e < fs; e += 32) y[e] = y[e] - (h / 6.0) * (ka[e] + kn[e]);
       warp::sync();
     }
     // adjoint
     const double* eb = a.ebar + j * fs;
     for (int e = lane; e < fs; e += 32) yb[e] = eb[e];
     warp::sync();
+    auto load_stage = [&](const double* src) {
+      for (int e = lane; e < fs; e += 32) y[e] = src[e];
+      warp::sync();
+    };
     for (int i = 0; i < K; ++i) {
       const double* st = ysj + (int64_t)i * 4 * fs;
-      for (int e = lane; e < fs; e += 32) {
-        y[e] = st[e];
-        y2[e] = st[fs + e];
-        y3[e] = st[2 * fs + e];
-        y4[e] = st[3 * fs + e];
-      }
-      warp::sync();
       const int p1 = 2 * i + 2, p2 = 2 * i + 1, p3 = 2 * i;
       // y_new = y - h/6 (k1 + 2 k2 + 2 k3 + k4): stage output adjoints
       // kb4 = -h/6 yb, kb3 = -h/3 yb (+ -h acc4), kb2 = -h/3 yb (+ -h/2 acc3),
@@ -815,28 +817,28 @@ __global__ void __launch_bounds__(32) rk4_adjoint_warp_kernel(RK4AdjArgs a) {
         kb[e] = -(h / 6.0) * yb[e];
         acc[e] = 0.0;
       }
-      warp::sync();
-      warp::rhs_vjp(lane, n, y4, F, B, kb, acc, Fb, Bb, Qb, qb + p3 * n, rhob + p3, tmp);
+      load_stage(st + 3 * fs);
+      warp::rhs_vjp(lane, n, y, F, B, kb, acc, Fb, Bb, Qb, qb + p3 * n, rhob + p3, tmp);
       for (int e = lane; e < fs; e += 32) {
         yb[e] += acc[e];
         kb[e] = -(h / 3.0) * kbs[e] - h * acc[e];
         acc[e] = 0.0;
       }
-      warp::sync();
-      warp::rhs_vjp(lane, n, y3, F, B, kb, acc, Fb, Bb, Qb, qb + p2 * n, rhob + p2, tmp);
+      load_stage(st + 2 * fs);
+      warp::rhs_vjp(lane, n, y, F, B, kb, acc, Fb, Bb, Qb, qb + p2 * n, rhob + p2, tmp);
       for (int e = lane; e < fs; e += 32) {
         yb[e] += acc[e];
         kb[e] = -(h / 3.0) * kbs[e] - 0.5 * h * acc[e];
         acc[e] = 0.0;
       }
-      warp::sync();
-      warp::rhs_vjp(lane, n, y2, F, B, kb, acc, Fb, Bb, Qb, qb + p2 * n, rhob + p2, tmp);
+      load_stage(st + fs);
+      warp::rhs_vjp(lane, n, y, F, B, kb, acc, Fb, Bb, Qb, qb + p2 * n, rhob + p2, tmp);
       for (int e = lane; e < fs; e += 32) {
         yb[e] += acc[e];
         kb[e] = -(h / 6.0) * kbs[e] - 0.5 * h * acc[e];
         acc[e] = 0.0;
       }
-      warp::sync();
+      load_stage(st);
       warp::rhs_vjp(lane, n, y, F, B, kb, acc, Fb, Bb, Qb, qb + p1 * n, rhob + p1, tmp);
       for (int e = lane; e < fs; e += 32) yb[e] += acc[e];
       warp::sync();
@@ -1117,7 +1119,8 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   {
     const size_t smem = rk4w_smem_doubles() * sizeof(double);
     cudaFuncSetAttribute(rk4_adjoint_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t grid = T < 152 * 12 ? T : 152 * 12;
+    // 14 KB of shared memory per warp (+1 KB reserved per CTA): 15 warps per SM
+    const int64_t grid = T < 152 * 15 ? T : 152 * 15;
     rk4_adjoint_warp_kernel<<<(unsigned)grid, 32, smem, st>>>(ra);
   }
   count_launch();

@@ -69,20 +69,31 @@ __device__ __forceinline__ long long order_key(double v) {
   return b < 0 ? LLONG_MIN - b : b;
 }
 
-// App. E: the grid minimum `best` = g_k + f_k at index k lowered by
-// b^2 / (4a), a and b the curvature and slope sums of the quadratics through
-// (k-1, k, k+1) of g and of f; unchanged when a <= 0.
-__device__ __forceinline__ double refine(const GridArgs& a, double best, double gm, double g0, double gp, double fm,
-                                         double f0, double fp) {
+// App. E: the curvature a = (p + m - 2 c) / (2 dx^2) and slope
+// b = (p - m) / (2 dx) of the quadratic through (m, c, p) at (k-1, k, k+1).
+__device__ __forceinline__ double2 curvature(const GridArgs& a, double m, double c, double p) {
   const double den2 = __dmul_rn(2.0, __dmul_rn(a.dx, a.dx));
   const double den1 = __dmul_rn(2.0, a.dx);
-  const double ag = __ddiv_rn(__dsub_rn(__dadd_rn(gp, gm), __dmul_rn(2.0, g0)), den2);
-  const double bg = __ddiv_rn(__dsub_rn(gp, gm), den1);
-  const double af = __ddiv_rn(__dsub_rn(__dadd_rn(fp, fm), __dmul_rn(2.0, f0)), den2);
-  const double bf = __ddiv_rn(__dsub_rn(fp, fm), den1);
-  const double cv = __dadd_rn(ag, af), sl = __dadd_rn(bg, bf);
+  return make_double2(__ddiv_rn(__dsub_rn(__dadd_rn(p, m), __dmul_rn(2.0, c)), den2), __ddiv_rn(__dsub_rn(p, m), den1));
+}
+
+// App. E: the grid minimum `best` = g_k + f_k lowered by b^2 / (4a), with
+// a = a_g + a_f and b = b_g + b_f; unchanged when a <= 0.
+__device__ __forceinline__ double refine_with(double best, double2 g, double2 f) {
+  const double cv = __dadd_rn(g.x, f.x), sl = __dadd_rn(g.y, f.y);
   if (!(cv > 0.0)) return best;
   return __dsub_rn(best, __ddiv_rn(__dmul_rn(sl, sl), __dmul_rn(4.0, cv)));
+}
+
+// Curvature and slope of every power's rows at every interior k, as pairs
+// tab[l][i][k] (zero at k = 0 and G-1): they depend on (l, i, k) alone, so the
+// values levels read them instead of dividing again for every row of w.
+__global__ void grid_curv_kernel(GridArgs a, const double* __restrict__ pw, int L, double2* __restrict__ tab) {
+  const int64_t GG = (int64_t)a.G * a.G;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * GG) return;
+  const int k = (int)(e % a.G);
+  tab[e] = (k > 0 && k < a.G - 1) ? curvature(a, pw[e - 1], pw[e], pw[e + 1]) : make_double2(0.0, 0.0);
 }
 
 // C(i, j): from x_i to x_j in one step dt = tau / substeps of
@@ -282,7 +293,7 @@ __device__ __forceinline__ void fp64_scan(const Operands<kValues>& op, GridSmem&
 template <bool kValues>
 __global__ void __launch_bounds__(kGT* kGT, 4)
     grid_minplus_kernel(GridArgs a, const double* __restrict__ A, const double* Bm, double* Om, double* X0,
-                        double* X1, int l, int64_t ncols) {
+                        double* X1, int l, int64_t ncols, const double2* __restrict__ tab) {
   __shared__ GridSmem sm;
   const Operands<kValues> op{a, A, Bm, Om, X0, X1, l};
   const int G = a.G;
@@ -358,9 +369,10 @@ __global__ void __launch_bounds__(kGT* kGT, 4)
   if (!valid) return;
   const double* col = op.bcol(c);
   double res = best;
-  if (a.interp && bk > 0 && bk < G - 1)
-    res = refine(a, best, op.av(i, bk - 1), op.av(i, bk), op.av(i, bk + 1), op.bv(col, bk - 1), op.bv(col, bk),
-                 op.bv(col, bk + 1));
+  if (a.interp && bk > 0 && bk < G - 1) {
+    const double2 gc = tab ? tab[(int64_t)i * G + bk] : curvature(a, op.av(i, bk - 1), op.av(i, bk), op.av(i, bk + 1));
+    res = refine_with(best, gc, curvature(a, op.bv(col, bk - 1), op.bv(col, bk), op.bv(col, bk + 1)));
+  }
   if (kValues) value_column(a, l, c, X0, X1).out[i] = res;
   else Om[(int64_t)i * G + c] = res;
   if (!isfinite(res)) flag(kStatusNonFinite);
@@ -396,7 +408,7 @@ int64_t set_count(int64_t T, int l) {
 
 cudaError_t launch_combine(const GridArgs& a, const double* A, const double* B, double* out, cudaStream_t st) {
   const dim3 grid(cdiv_u(a.G, kGT), cdiv_u(a.G, kGT));
-  grid_minplus_kernel<false><<<grid, kGT * kGT, 0, st>>>(a, A, B, out, nullptr, nullptr, 0, a.G);
+  grid_minplus_kernel<false><<<grid, kGT * kGT, 0, st>>>(a, A, B, out, nullptr, nullptr, 0, a.G, nullptr);
   count_launch();
   return cudaGetLastError();
 }
@@ -406,7 +418,9 @@ cudaError_t launch_combine(const GridArgs& a, const double* A, const double* B, 
 size_t grid_workspace_bytes(const lqt_grid_problem& p, int which) {
   const size_t GG = (size_t)p.G * p.G;
   if (which == 0) return 2 * GG * sizeof(double);
-  return ((size_t)grid_levels(p.T) * GG + ((size_t)p.T + 1) * p.G) * sizeof(double);
+  // powers, one double of alignment slack, their (curvature, slope) pairs, the
+  // second buffer of the values
+  return ((size_t)grid_levels(p.T) * GG * 3 + 1 + ((size_t)p.T + 1) * p.G) * sizeof(double);
 }
 
 cudaError_t run_grid_block(const lqt_grid_problem& p, double* Vblock, char* ws, cudaStream_t st) {
@@ -438,18 +452,25 @@ cudaError_t run_grid_values(const lqt_grid_problem& p, const double* Vblock, dou
   const GridArgs a = grid_args(p);
   const size_t GG = (size_t)p.G * p.G;
   const int L = grid_levels(p.T);
-  double* pw = (double*)ws;          // P_0 .. P_{L-1}
-  double* X1 = pw + (size_t)L * GG;  // second buffer of the values (V is the first)
+  double* pw = (double*)ws;  // P_0 .. P_{L-1}
+  // their (curvature, slope) pairs, on a 16-byte boundary
+  double2* tab = (double2*)(((uintptr_t)(pw + (size_t)L * GG) + 15) & ~(uintptr_t)15);
+  double* X1 = (double*)(tab + (size_t)L * GG);  // second buffer of the values (V is the first)
   cudaError_t e = cudaMemcpyAsync(pw, Vblock, GG * sizeof(double), cudaMemcpyDeviceToDevice, st);
   for (int l = 1; l < L && e == cudaSuccess; ++l)
     e = launch_combine(a, pw + (l - 1) * GG, pw + (l - 1) * GG, pw + l * GG, st);
   if (e != cudaSuccess) return e;
+  if (p.interp) {
+    grid_curv_kernel<<<cdiv_u((int64_t)L * GG, 256), 256, 0, st>>>(a, pw, L, tab);
+    count_launch();
+  }
   grid_terminal_kernel<<<cdiv_u((p.T + 1) * p.G, 256), 256, 0, st>>>(a, V, X1);
   count_launch();
   for (int l = 0; l < L; ++l) {
     const int64_t nc = set_count(p.T, l);
     const dim3 grid(cdiv_u(nc, kGT), cdiv_u(p.G, kGT));
-    grid_minplus_kernel<true><<<grid, kGT * kGT, 0, st>>>(a, pw + l * GG, nullptr, nullptr, V, X1, l, nc);
+    grid_minplus_kernel<true><<<grid, kGT * kGT, 0, st>>>(a, pw + l * GG, nullptr, nullptr, V, X1, l, nc,
+                                                          p.interp ? tab + l * GG : nullptr);
     count_launch();
   }
   return cudaGetLastError();

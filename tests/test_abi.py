@@ -122,9 +122,10 @@ def test_grid_validation_on_host(lib):
     L = _abi.lib()
     g = W.falling_body(G=60, T=100)
     gs = m.grid_struct(g)
-    # block: 2 G^2 doubles; values: G^2 per power (7 powers for T = 100) + (T+1) G
+    # block: 2 G^2 doubles; values: 3 G^2 per power (7 powers for T = 100; the
+    # power and its curvature/slope pairs) + 1 + (T+1) G
     assert L.lqt_grid_workspace_size(ct.byref(gs), 0) == 2 * 60 * 60 * 8
-    assert L.lqt_grid_workspace_size(ct.byref(gs), 1) == (7 * 60 * 60 + 101 * 60) * 8
+    assert L.lqt_grid_workspace_size(ct.byref(gs), 1) == (3 * 7 * 60 * 60 + 1 + 101 * 60) * 8
     assert L.lqt_grid_workspace_size(ct.byref(gs), 2) == 0
     d = ct.c_void_p(256)
     need = L.lqt_grid_workspace_size(ct.byref(gs), 1)

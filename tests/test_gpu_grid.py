@@ -137,6 +137,22 @@ def test_values_match_oracle(name, kw):
         assert np.abs(got.cpu().numpy() - seq).max() <= 1e-12 * np.abs(seq).max()
 
 
+def test_values_with_a_workspace_off_16_byte_alignment():
+    """The workspace need only be 8-byte aligned: the table of curvature pairs
+    inside it is placed on a 16-byte boundary by the library."""
+    import paper_2212_11744_gb300 as lqt
+    g = W.falling_body(G=61, T=77)
+    Vb = oracle.grid_block(g)
+    need = lqt.lqt_grid_workspace_size(g, 1)
+    raw = torch.empty(need + 16, dtype=torch.uint8, device="cuda")
+    ws = raw[8:8 + need]
+    assert ws.data_ptr() % 16 == 8
+    got = lqt.lqt_grid_values(g, dev(Vb), ws=ws)
+    torch.cuda.synchronize()
+    assert lqt.lqt_get_status() == 0
+    same(got, oracle.grid_values(g, Vb), "values")
+
+
 def test_full_path_at_paper_size():
     """Block function and values on the GPU alone, the largest configuration of
     the paper's nonlinear experiment (grid of 60 points, 10^4 blocks of 1/10
