@@ -531,21 +531,25 @@ __device__ __forceinline__ void mmt(int lane, int n, const double* a, const doub
   }
   sync();
 }
-__device__ __forceinline__ void mv(int lane, int n, const double* a, const double* x, double* y) {
-  if (lane < n) {
-    double s = 0.0;
-    for (int l = 0; l < n; ++l) s = fma(a[lane * n + l], x[l], s);
-    y[lane] = s;
-  }
+// y = a x, y = a^T x (n <= 8): four lanes per output, each summing every
+// fourth column, then two butterfly steps, so that the warp's FP64
+// instructions run with all lanes rather than n of them.
+template <bool kTrans>
+__device__ __forceinline__ void mv4(int lane, int n, const double* a, const double* x, double* y) {
+  const int i = lane >> 2, q = lane & 3;
+  double s = 0.0;
+  if (i < n)
+    for (int l = q; l < n; l += 4) s = fma(kTrans ? a[l * n + i] : a[i * n + l], x[l], s);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (i < n && q == 0) y[i] = s;
   sync();
 }
+__device__ __forceinline__ void mv(int lane, int n, const double* a, const double* x, double* y) {
+  mv4<false>(lane, n, a, x, y);
+}
 __device__ __forceinline__ void mtv(int lane, int n, const double* a, const double* x, double* y) {
-  if (lane < n) {
-    double s = 0.0;
-    for (int l = 0; l < n; ++l) s = fma(a[l * n + lane], x[l], s);
-    y[lane] = s;
-  }
-  sync();
+  mv4<true>(lane, n, a, x, y);
 }
 // a <- (a + a^T) / 2  (n <= 8: at most two entries per lane; every lane runs
 // the same iterations so that the warp barrier is reached by all)
@@ -576,46 +580,7 @@ struct Tmp {
   double *t1, *t2, *t3, *JG, *beta, *betab, *v1, *v2;
 };
 
-// k = f(y), lanes over entries.
-__device__ void rhs_full(int lane, int n, const double* y, const double* F, const double* B, const double* Q,
-                         const double* q, double rho, double* k, const Tmp& t) {
-  const int nn = n * n;
-  FE Y = fe_view(n, const_cast<double*>(y)), K = fe_view(n, k);
-  mv(lane, n, B, Y.eta, t.beta);
-  mm(lane, n, B, Y.J, t.t1);                                   // G
-  for (int e = lane; e < nn; e += 32) t.t2[e] = t.t1[e] - F[e];  // G - F
-  sync();
-  mm(lane, n, Y.A, t.t2, K.A);
-  if (lane < n) {
-    double s = 0.0;
-    for (int l = 0; l < n; ++l) s = fma(Y.A[lane * n + l], t.beta[l], s);
-    K.b[lane] = -s;
-  }
-  mm(lane, n, Y.A, B, t.t2);
-  mmt(lane, n, t.t2, Y.A, K.C);
-  for (int e = lane; e < nn; e += 32) K.C[e] = -K.C[e];
-  sync();
-  symm(lane, n, K.C);
-  mtv(lane, n, F, Y.eta, t.v1);
-  mv(lane, n, Y.J, t.beta, t.v2);
-  if (lane < n) K.eta[lane] = -q[lane] - t.v1[lane] + t.v2[lane];
-  mm(lane, n, Y.J, F, t.t2);  // JF
-  mm(lane, n, Y.J, t.t1, t.JG);
-  for (int e = lane; e < nn; e += 32) {
-    const int i = e / n, c = e % n;
-    K.J[e] = -Q[e] - t.t2[i * n + c] - t.t2[c * n + i] + t.JG[e];
-  }
-  sync();
-  symm(lane, n, K.J);
-  if (lane == 0) {
-    double z = -0.5 * rho;
-    for (int i = 0; i < n; ++i) z += 0.5 * Y.eta[i] * t.beta[i];
-    *K.z = z;
-  }
-  sync();
-}
-
-// Vector-Jacobian product of rhs_full at y with output adjoint kb (its C, J
+// Vector-Jacobian product of the full-matrix right-hand side at y with output adjoint kb (its C, J
 // parts symmetrised first), accumulated into yb and the coefficient adjoints;
 // lanes over entries: Fb, Bb, Qb accumulate entry-wise (each lane owns the same
 // entries throughout), qb, rhob by lanes < n and lane 0.
@@ -708,8 +673,7 @@ __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const
 }  // namespace warp
 
 // Shared-memory doubles of one warp of rk4_adjoint_warp_kernel: five element
-// buffers (the forward phase uses four, the reverse phase five, in turn),
-// B, Fb, Bb, Qb, the temporaries, and the per-sample q, rho adjoints.
+// buffers, B, Fb, Bb, Qb, the temporaries, and the per-sample q, rho adjoints.
 __host__ __device__ constexpr int rk4w_smem_doubles() {
   return 5 * AS + 8 * AN * AN + 4 * AN + (2 * 8 + 1) * AN + (2 * 8 + 1) + 8;
 }
@@ -718,18 +682,13 @@ __global__ void __launch_bounds__(32, 15) rk4_adjoint_warp_kernel(RK4AdjArgs a) 
   extern __shared__ double sm[];
   const int lane = threadIdx.x;
   const int n = a.n, nn = n * n, fs = fe_size(n), K = a.K, M = a.M;
-  // forward phase: y (the state), ys (a stage input), ka (k1 + 2 k2 + 2 k3),
-  // kn (the stage just evaluated); reverse phase: y (a stage input), yb, kb
-  // (one stage's output adjoint), acc (its input adjoint), kbs (the step's
-  // output adjoint)
+  // y (a stage input), yb (the state adjoint), kb (one stage's output
+  // adjoint), acc (its input adjoint), kbs (the step's output adjoint)
   double* y = sm;
-  double* ys_ = y + AS;
-  double* ka = ys_ + AS;
-  double* kn = ka + AS;
-  double* yb = ys_;
-  double* kb = ka;
-  double* acc = kn;
-  double* kbs = kn + AS;
+  double* yb = y + AS;
+  double* kb = yb + AS;
+  double* acc = kb + AS;
+  double* kbs = acc + AS;
   double* B = kbs + AS;
   double* Fb = B + AN * AN;
   double* Bb = Fb + AN * AN;
@@ -761,43 +720,10 @@ __global__ void __launch_bounds__(32, 15) rk4_adjoint_warp_kernel(RK4AdjArgs a) 
     }
     for (int e = lane; e < (2 * K + 1) * n; e += 32) qb[e] = 0.0;
     for (int e = lane; e <= 2 * K; e += 32) rhob[e] = 0.0;
-    for (int e = lane; e < fs; e += 32) y[e] = (e < nn && e % (n + 1) == 0) ? 1.0 : 0.0;
     warp::sync();
-    auto qr_at = [&](int p) { return a.cf.qr.ptr + sample_index(a.cf.qr.mode, j, p, K) * (n + 1); };
-    // the four stage inputs of every step, stored by the forward pass for the
-    // reverse sweep (instead of recomputing them there)
-    double* ysj = a.ys + j * (int64_t)K * 4 * fs;
-    // forward
-    for (int i = K - 1; i >= 0; --i) {
-      double* st = ysj + (int64_t)i * 4 * fs;
-      const double* q1 = qr_at(2 * i + 2);
-      const double* q2 = qr_at(2 * i + 1);
-      const double* q3 = qr_at(2 * i);
-      warp::rhs_full(lane, n, y, F, B, Q, q1, q1[n], ka, tmp);  // k1
-      for (int e = lane; e < fs; e += 32) {
-        st[e] = y[e];
-        ys_[e] = y[e] - 0.5 * h * ka[e];
-        st[fs + e] = ys_[e];
-      }
-      warp::sync();
-      warp::rhs_full(lane, n, ys_, F, B, Q, q2, q2[n], kn, tmp);  // k2
-      for (int e = lane; e < fs; e += 32) {
-        ys_[e] = y[e] - 0.5 * h * kn[e];
-        st[2 * fs + e] = ys_[e];
-        ka[e] = ka[e] + 2.0 * kn[e];
-      }
-      warp::sync();
-      warp::rhs_full(lane, n, ys_, F, B, Q, q2, q2[n], kn, tmp);  // k3
-      for (int e = lane; e < fs; e += 32) {
-        ys_[e] = y[e] - h * kn[e];
-        st[3 * fs + e] = ys_[e];
-        ka[e] = ka[e] + 2.0 * kn[e];
-      }
-      warp::sync();
-      warp::rhs_full(lane, n, ys_, F, B, Q, q3, q3[n], kn, tmp);  // k4
-      for (int e = lane; e < fs; e += 32) y[e] = y[e] - (h / 6.0) * (ka[e] + kn[e]);
-      warp::sync();
-    }
+    // the four stage inputs of every RK4 step, written by this backward pass's
+    // element build (build_stages_kernel)
+    const double* ysj = a.ys + j * (int64_t)K * 4 * fs;
     // adjoint
     const double* eb = a.ebar + j * fs;
     for (int e = lane; e < fs; e += 32) yb[e] = eb[e];
@@ -1073,7 +999,8 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   cudaError_t e = launch_prepare_coefs(p, L, ws + b.coef, cf, st);
   if (e != cudaSuccess) return e;
   ElemPtrs el = carve_elements_at(p, ws + b.elems);
-  e = launch_build(p, L, cf, el, st, nullptr);
+  // the elements, and the RK4 stage inputs for the discrete adjoint (step 5)
+  e = launch_build_with_stages(p, L, cf, el, (double*)(ws + b.ys), st);
   if (e != cudaSuccess) return e;
   double* maps = (double*)(ws + b.maps);
   e = launch_maps_from_values(p, el, S, v, maps, st);

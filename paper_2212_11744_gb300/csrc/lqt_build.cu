@@ -473,11 +473,37 @@ __device__ __forceinline__ const double* coef_at(const Coef& c, int64_t j, int32
   return c.ptr + sample_index(c.mode, j, p, K) * stride;
 }
 
+// Element y in the full layout (A, b, C, eta, J with C and J written in full,
+// zeta): 3 N^2 + 2 N + 1 doubles at dst.
+template <int N>
+__device__ __forceinline__ void store_full(const Elem<N>& y, double* dst) {
+  double* o = dst;
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) *o++ = y.A[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) *o++ = y.b[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int c = 0; c < N; ++c) *o++ = y.C[sidx<N>(i, c)];
+#pragma unroll
+  for (int i = 0; i < N; ++i) *o++ = y.eta[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int c = 0; c < N; ++c) *o++ = y.J[sidx<N>(i, c)];
+  *o = y.zeta;
+}
+
 // K classical RK4 steps of the backward conditional HJB ODEs for sub-interval
 // j, from the boundary A = I, b = C = eta = J = 0, zeta = 0 at s = t_{j+1}
-// down to s = t_j (Sec. IV-B, eq. abcej_boundary).
-template <int N, int M>
-__device__ __forceinline__ void build_one(const Coefs& cf, const double* t, int64_t j, int32_t K, Elem<N>& y) {
+// down to s = t_j (Sec. IV-B, eq. abcej_boundary).  With kStages the four
+// stage inputs of every step go to stages[i][0..3] (full layout), for the
+// discrete adjoint's reverse sweep.
+template <int N, int M, bool kStages = false>
+__device__ __forceinline__ void build_one(const Coefs& cf, const double* t, int64_t j, int32_t K, Elem<N>& y,
+                                          double* stages = nullptr) {
+  constexpr int FS = 3 * N * N + 2 * N + 1;
   const double h = (t[j + 1] - t[j]) / K;
   Elem<N> yn, yt, k;
 #pragma unroll
@@ -509,15 +535,20 @@ __device__ __forceinline__ void build_one(const Coefs& cf, const double* t, int6
       Q[q] = coef_at<N>(cf.Q, j, ps[q], K, N * N);
       qr[q] = coef_at<N>(cf.qr, j, ps[q], K, N + 1);
     }
+    double* st = kStages ? stages + (int64_t)i * 4 * FS : nullptr;
+    if constexpr (kStages) store_full<N>(y, st);
     element_rhs<N, M>(y, F[0], c[0], Lt[0], Q[0], qr[0], k);
     axpy_to(yn, y, -h / 6.0, k);
     axpy_to(yt, y, -0.5 * h, k);
+    if constexpr (kStages) store_full<N>(yt, st + FS);
     element_rhs<N, M>(yt, F[1], c[1], Lt[1], Q[1], qr[1], k);
     axpy_to(yn, yn, -h / 3.0, k);
     axpy_to(yt, y, -0.5 * h, k);
+    if constexpr (kStages) store_full<N>(yt, st + 2 * FS);
     element_rhs<N, M>(yt, F[1], c[1], Lt[1], Q[1], qr[1], k);
     axpy_to(yn, yn, -h / 3.0, k);
     axpy_to(yt, y, -h, k);
+    if constexpr (kStages) store_full<N>(yt, st + 3 * FS);
     element_rhs<N, M>(yt, F[2], c[2], Lt[2], Q[2], qr[2], k);
     axpy_to(y, yn, -h / 6.0, k);
   }
@@ -529,6 +560,18 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
   if (j >= a.T) return;
   Elem<N> y;
   build_one<N, M>(a.cf, a.t, j, a.K, y);
+  store_public<N>(a.out, j, y);
+}
+
+// The same, also writing every RK4 stage input of sub-interval j to
+// stages + j K 4 (3N^2 + 2N + 1) (full layout, step i = K-1 .. 0 at slot i).
+template <int N, int M>
+__global__ void __launch_bounds__(128) build_stages_kernel(BuildArgs a, double* stages) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.T) return;
+  constexpr int FS = 3 * N * N + 2 * N + 1;
+  Elem<N> y;
+  build_one<N, M, true>(a.cf, a.t, j, a.K, y, stages + j * (int64_t)a.K * 4 * FS);
   store_public<N>(a.out, j, y);
 }
 
@@ -735,23 +778,45 @@ cudaError_t batch_build(const BatchDev& bd, const ElemPtrs& el, char* team_scrat
 }
 
 template <int N, int M>
-static void launch_build_nm(const BuildArgs& a, cudaStream_t st) {
+static void launch_build_nm(const BuildArgs& a, cudaStream_t st, double* stages) {
   const int threads = 128;
   const int64_t blocks = (a.T + threads - 1) / threads;
-  build_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a);
+  if (stages)
+    build_stages_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a, stages);
+  else
+    build_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a);
   count_launch();
 }
 
 template <int N>
-static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st) {
+static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st, double* stages = nullptr) {
   switch (M) {
-    case 1: launch_build_nm<N, 1>(a, st); break;
-    case 2: if constexpr (N >= 2) { launch_build_nm<N, 2>(a, st); break; } else return cudaErrorInvalidValue;
-    case 4: if constexpr (N >= 3) { launch_build_nm<N, 4>(a, st); break; } else return cudaErrorInvalidValue;
-    case 8: if constexpr (N >= 8) { launch_build_nm<N, 8>(a, st); break; } else return cudaErrorInvalidValue;
+    case 1: launch_build_nm<N, 1>(a, st, stages); break;
+    case 2: if constexpr (N >= 2) { launch_build_nm<N, 2>(a, st, stages); break; } else return cudaErrorInvalidValue;
+    case 4: if constexpr (N >= 3) { launch_build_nm<N, 4>(a, st, stages); break; } else return cudaErrorInvalidValue;
+    case 8: if constexpr (N >= 8) { launch_build_nm<N, 8>(a, st, stages); break; } else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   return cudaSuccess;
+}
+
+// Elements 0..T (terminal included) of p, n <= 8, with every RK4 stage input
+// of sub-interval j at stages + j K 4 (3n^2 + 2n + 1) (full layout).
+cudaError_t launch_build_with_stages(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                                     double* stages, cudaStream_t st) {
+  BuildArgs a;
+  a.T = p.T; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
+  cudaError_t e;
+  switch (p.n) {
+    case 1: e = launch_build_n<1>(a, lay.M, st, stages); break;
+    case 2: e = launch_build_n<2>(a, lay.M, st, stages); break;
+    case 3: e = launch_build_n<3>(a, lay.M, st, stages); break;
+    case 4: e = launch_build_n<4>(a, lay.M, st, stages); break;
+    case 8: e = launch_build_n<8>(a, lay.M, st, stages); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return launch_terminal_element(p, out, st);
 }
 
 // Elements 0..T-1 of p alone (no terminal element), n <= 8.

@@ -100,6 +100,8 @@ cudaError_t launch_prepare_into(const lqt_problem& p, const Layout& lay, double*
 Coefs coefs_view(const lqt_problem& p, const Layout& lay, double* Lt, double* Q, double* qr, double* Ku);
 cudaError_t launch_build_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                                cudaStream_t st);
+cudaError_t launch_build_with_stages(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                                     double* stages, cudaStream_t st);
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                          cudaStream_t s, double* team_scratch = nullptr);
 // n = 16, 64 (team kernels, lqt_team.cu)
