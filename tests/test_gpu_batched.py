@@ -96,3 +96,30 @@ def test_autotuner_picks_a_candidate():
     best = bt.autotune(candidates=(0, 4, 16), reps=2)
     assert best in (0, 4, 16)
     assert Batch.tuning_table()[(4, 3, bt.total, 0)][0] == best
+
+
+@pytest.mark.slow
+def test_full_batch_sampled_problems_against_oracle():
+    """The whole 4096-problem batch of the benchmark (n in {2,4,8,16},
+    T in [256, 8192]), solved per state dimension with the autotuned chunk as
+    the benchmark runs it; for each n, the problems with the shortest and the
+    longest horizon and one more (seeded) against the oracle, every output."""
+    from paper_2212_11744_gb300.batch import Batch
+    probs = [W.batched_member(b) for b in range(4096)]
+    byn = {}
+    for b, p in enumerate(probs):
+        byn.setdefault(p.n, []).append(b)
+    rng = np.random.default_rng(4096)
+    for n, idx in sorted(byn.items()):
+        bt = Batch([probs[b] for b in idx])
+        bt.autotune(candidates=(0, 8, 32), reps=1)
+        out = bt.solve()
+        torch.cuda.synchronize()
+        Ts = [probs[b].T for b in idx]
+        picks = {int(np.argmin(Ts)), int(np.argmax(Ts)), int(rng.integers(len(idx)))}
+        for i in sorted(picks):
+            p = probs[idx[i]]
+            ref = oracle.solve(p)
+            got = bt.problem_slice(out, i)
+            for k in ("S", "v", "zeta", "x", "u"):
+                assert rel(got[k].cpu().numpy(), ref[k]) <= TOL, (n, idx[i], p.T, k)

@@ -235,3 +235,37 @@ def test_point_mass_full_size_against_oracle():
     assert m.lqt_get_status() == 0
     ref = oracle.solve(p)
     check_solution(out, ref, label="point_mass_2^20")
+
+
+@pytest.mark.slow
+def test_large_state_full_size_local_checks():
+    """The n = 64, m = 16 workload at its full size, T = 2^16, K = 2, solved in
+    FP64 as the benchmark runs it.  The oracle cannot fold 2^16 elements of
+    n = 64 in seconds, so at sampled boundaries k the GPU's outputs are checked
+    through relations that hold at any size, with the oracle's own element k:
+    (S, v, zeta)_k = element_k (x) (S, v, zeta)_{k+1} (the oracle's
+    combination, Lemma LQT_combination, with a value as the right operand),
+    x_{k+1} = (I + C_k S_{k+1})^-1 (A_k x_k + b_k + C_k v_{k+1}) (Method 2 over
+    one sub-interval) and u_k = U^-1 L^T (v_k - S_k x_k)."""
+    p = W.large_state_n64(T=1 << 16)
+    m = lqt()
+    out = m.lqt_solve(m.DeviceProblem(p))
+    torch.cuda.synchronize()
+    assert m.lqt_get_status() == 0
+    S, v, z, x, u = (to_np(out[k]) for k in ("S", "v", "zeta", "x", "u"))
+    n, T = p.n, p.T
+    term = oracle.build_elements(p, T, T + 1)
+    assert relerr(S[T], term["J"][0]) <= TOL and relerr(v[T], term["eta"][0]) <= TOL
+    L = p.L.values[0]
+    U = p.U.values[0]
+    for k in (0, 1, 4097, 31_000, T // 2 + 3, T - 2, T - 1):
+        e = {kk: vv[0] for kk, vv in oracle.build_elements(p, k, k + 1).items()}
+        val = {"A": np.zeros((n, n)), "b": np.zeros(n), "C": np.zeros((n, n)), "eta": v[k + 1], "J": S[k + 1],
+               "zeta": z[k + 1]}
+        c = oracle.combine(n, e, val)
+        assert relerr(S[k], c["J"]) <= TOL, k
+        assert relerr(v[k], c["eta"]) <= TOL, k
+        assert abs(z[k] - float(c["zeta"])) <= TOL * max(1.0, abs(float(c["zeta"]))), k
+        xn = np.linalg.solve(np.eye(n) + e["C"] @ S[k + 1], e["A"] @ x[k] + e["b"] + e["C"] @ v[k + 1])
+        assert relerr(x[k + 1], xn) <= TOL, k
+        assert relerr(u[k], np.linalg.solve(U, L.T @ (v[k] - S[k] @ x[k]))) <= TOL, k
