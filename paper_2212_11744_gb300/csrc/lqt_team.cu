@@ -24,6 +24,10 @@ struct TeamCfg<16> {
   static constexpr int TEAM = 32;
   static constexpr bool SMEM = true;
   static constexpr int SLOTS = 152 * 8;
+  // the build: 21.3 KB of shared memory per warp (one full record and three
+  // flow records) and at most 204 registers: 10 warps per SM
+  static constexpr int BUILD_MIN = 10;
+  static constexpr int BUILD_SLOTS = 152 * 10;
 };
 // n <= 8: the thread-per-element kernels do level 0 of the scans; these
 // warp-per-combination instances run the pairwise upper levels.
@@ -32,6 +36,8 @@ struct TeamCfgSmall {
   static constexpr int TEAM = 32;
   static constexpr bool SMEM = true;
   static constexpr int SLOTS = 152 * 8;
+  static constexpr int BUILD_MIN = 1;
+  static constexpr int BUILD_SLOTS = SLOTS;
 };
 template <>
 struct TeamCfg<1> : TeamCfgSmall<1> {};
@@ -48,11 +54,13 @@ struct TeamCfg<64> {
   static constexpr int TEAM = 256;
   static constexpr bool SMEM = false;
   static constexpr int SLOTS = 152;
+  static constexpr int BUILD_MIN = 1;
+  static constexpr int BUILD_SLOTS = SLOTS;  // one global scratch slot per CTA
 };
 
 // Doubles of per-slot scratch of each kernel.
 template <int N, int M>
-constexpr int build_slot_doubles() { return 4 * Rec<N>::SIZE + 2 * N * M + M + 8; }
+constexpr int build_slot_doubles() { return Rec<N>::SIZE + 3 * Rec<N>::FLOW + 2 * N * M + M + 8; }
 template <int N>
 constexpr int reduce_slot_doubles() { return 2 * Rec<N>::SIZE + team::combine_scratch_doubles<N>() + 8; }
 template <int N>
@@ -103,7 +111,7 @@ template <int N, int M>
 __device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64_t j, int32_t K, double* yb,
                                double* ynb, double* ytb, double* kb, double* AL, double* P, double* w) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
-  const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
+  const Rec<N> y = Rec<N>::packed(yb), yn = Rec<N>::flow(ynb), yt = Rec<N>::flow(ytb), k = Rec<N>::flow(kb);
   const double h = (t[j + 1] - t[j]) / K;
   for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
   team::sync<TEAM>();
@@ -117,31 +125,33 @@ __device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64
       Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], K) * N * N;
       qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], K) * (N + 1);
     }
-    team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w);
-    team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
-    team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
-    team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
-    team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w);
-    team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
-    team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
-    team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w);
-    team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
+    // (A, eta, J) by classical RK4 through yn and yt; b, C, zeta accumulated
+    // into y by the right-hand side
+    team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w, -h / 6.0, y);
+    team::axpy_flow<N, TEAM>(lane, yn, y, -h / 6.0, k);
+    team::axpy_flow<N, TEAM>(lane, yt, y, -0.5 * h, k);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w, -h / 3.0, y);
+    team::axpy_flow<N, TEAM>(lane, yn, yn, -h / 3.0, k);
+    team::axpy_flow<N, TEAM>(lane, yt, y, -0.5 * h, k);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w, -h / 3.0, y);
+    team::axpy_flow<N, TEAM>(lane, yn, yn, -h / 3.0, k);
+    team::axpy_flow<N, TEAM>(lane, yt, y, -h, k);
+    team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w, -h / 6.0, y);
+    team::axpy_flow<N, TEAM>(lane, y, yn, -h / 6.0, k);
   }
 }
 
 template <int N, int M>
-__global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_kernel(TeamBuildArgs a) {
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::BUILD_MIN) build_team_kernel(TeamBuildArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = build_slot_doubles<N, M>();
   const int lane = threadIdx.x;
   double* base = slot_base<N>(a.gscratch, SD);
   double* yb = base;
   double* ynb = yb + Rec<N>::SIZE;
-  double* ytb = ynb + Rec<N>::SIZE;
-  double* kb = ytb + Rec<N>::SIZE;
-  double* AL = kb + Rec<N>::SIZE;
+  double* ytb = ynb + Rec<N>::FLOW;
+  double* kb = ytb + Rec<N>::FLOW;
+  double* AL = kb + Rec<N>::FLOW;
   double* P = AL + N * M;
   double* w = P + N * M;
   for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
@@ -154,17 +164,17 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_kernel(TeamBuildA
 
 // Batches: one team per boundary of the concatenation (element or terminal).
 template <int N, int M>
-__global__ void __launch_bounds__(TeamCfg<N>::TEAM) batch_build_team_kernel(BatchDev bd, ElemPtrs out,
-                                                                           double* gscratch) {
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::BUILD_MIN)
+    batch_build_team_kernel(BatchDev bd, ElemPtrs out, double* gscratch) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = build_slot_doubles<N, M>();
   const int lane = threadIdx.x;
   double* base = slot_base<N>(gscratch, SD);
   double* yb = base;
   double* ynb = yb + Rec<N>::SIZE;
-  double* ytb = ynb + Rec<N>::SIZE;
-  double* kb = ytb + Rec<N>::SIZE;
-  double* AL = kb + Rec<N>::SIZE;
+  double* ytb = ynb + Rec<N>::FLOW;
+  double* kb = ytb + Rec<N>::FLOW;
+  double* AL = kb + Rec<N>::FLOW;
   double* P = AL + N * M;
   double* w = P + N * M;
   for (int64_t g = blockIdx.x; g < bd.total; g += gridDim.x) {
@@ -523,16 +533,16 @@ static TeamPlan<N> team_plan(int64_t T, bool with_traj) {
 }
 
 template <int N>
-static unsigned team_grid(int64_t work) {
-  const int64_t s = TeamCfg<N>::SLOTS;
+static unsigned team_grid(int64_t work, int64_t s = TeamCfg<N>::SLOTS) {
   return (unsigned)(work < s ? (work > 0 ? work : 1) : s);
 }
 
 template <int N, class Kern, class Args>
-static void team_launch(Kern k, int64_t work, size_t smem_doubles, const Args& a, cudaStream_t st) {
+static void team_launch(Kern k, int64_t work, size_t smem_doubles, const Args& a, cudaStream_t st,
+                        int64_t slots = TeamCfg<N>::SLOTS) {
   const size_t smem = TeamCfg<N>::SMEM ? smem_doubles * sizeof(double) : 0;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<team_grid<N>(work), TeamCfg<N>::TEAM, smem, st>>>(a);
+  k<<<team_grid<N>(work, slots), TeamCfg<N>::TEAM, smem, st>>>(a);
   count_launch();
 }
 
@@ -540,7 +550,7 @@ template <int N, int M>
 static cudaError_t team_build_nm(const lqt_problem& p, const Coefs& cf, const ElemPtrs& out, double* gscratch,
                                  cudaStream_t st) {
   TeamBuildArgs a{p.T, p.K, p.t, cf, out, gscratch};
-  team_launch<N>(build_team_kernel<N, M>, p.T, build_slot_doubles<N, M>(), a, st);
+  team_launch<N>(build_team_kernel<N, M>, p.T, build_slot_doubles<N, M>(), a, st, TeamCfg<N>::BUILD_SLOTS);
   return cudaGetLastError();
 }
 
@@ -723,7 +733,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) inv_master_team_kernel(InvTe
     double* w = P + N * M;
     double* JF = w + M;
     double* zq = JF + N * N;  // N + 1 zeros: q = 0, rho = 0
-    const Rec<N> y = Rec<N>::packed(yb), yt = Rec<N>::packed(ytb), k = Rec<N>::packed(kb);
+    const Rec<N> y = Rec<N>::packed(yb), yn = Rec<N>::flow(ynb), yt = Rec<N>::flow(ytb), k = Rec<N>::flow(kb);
     for (int e = lane; e < SZ; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
     for (int e = lane; e <= N; e += TEAM) zq[e] = 0.0;
     team::sync<TEAM>();
@@ -743,21 +753,21 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) inv_master_team_kernel(InvTe
     };
     for (int32_t i = K - 1; i >= 0; --i) {
       double* rec = table + 4 * (int64_t)i * SD;
-      team::rhs<N, M, TEAM>(lane, y, k, F, nullptr, Lt, Q, zq, AL, P, w);
+      team::rhs<N, M, TEAM>(lane, y, k, F, nullptr, Lt, Q, zq, AL, P, w, -h / 6.0, y);
       record(rec, y);
-      team::axpy<N, TEAM>(lane, ynb, yb, -h / 6.0, kb);
-      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w);
+      team::axpy_flow<N, TEAM>(lane, yn, y, -h / 6.0, k);
+      team::axpy_flow<N, TEAM>(lane, yt, y, -0.5 * h, k);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, -h / 3.0, y);
       record(rec + SD, yt);
-      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
-      team::axpy<N, TEAM>(lane, ytb, yb, -0.5 * h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w);
+      team::axpy_flow<N, TEAM>(lane, yn, yn, -h / 3.0, k);
+      team::axpy_flow<N, TEAM>(lane, yt, y, -0.5 * h, k);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, -h / 3.0, y);
       record(rec + 2 * SD, yt);
-      team::axpy<N, TEAM>(lane, ynb, ynb, -h / 3.0, kb);
-      team::axpy<N, TEAM>(lane, ytb, yb, -h, kb);
-      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w);
+      team::axpy_flow<N, TEAM>(lane, yn, yn, -h / 3.0, k);
+      team::axpy_flow<N, TEAM>(lane, yt, y, -h, k);
+      team::rhs<N, M, TEAM>(lane, yt, k, F, nullptr, Lt, Q, zq, AL, P, w, -h / 6.0, y);
       record(rec + 3 * SD, yt);
-      team::axpy<N, TEAM>(lane, yb, ynb, -h / 6.0, kb);
+      team::axpy_flow<N, TEAM>(lane, y, yn, -h / 6.0, k);
     }
     for (int e = lane; e < N * N; e += TEAM) {
       fin[e] = y.A()[e];
@@ -885,7 +895,8 @@ cudaError_t team_concat_scan(int32_t n, int64_t Tcat, const ElemPtrs& el, double
 template <int N, int M>
 static void batch_build_team_nm(const BatchDev& bd, const ElemPtrs& el, double* gs, cudaStream_t st) {
   const size_t smem = TeamCfg<N>::SMEM ? build_slot_doubles<N, M>() * sizeof(double) : 0;
-  batch_build_team_kernel<N, M><<<team_grid<N>(bd.total), TeamCfg<N>::TEAM, smem, st>>>(bd, el, gs);
+  batch_build_team_kernel<N, M><<<team_grid<N>(bd.total, TeamCfg<N>::BUILD_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(
+      bd, el, gs);
   count_launch();
 }
 

@@ -117,6 +117,12 @@ struct Rec {
   __device__ __forceinline__ static Rec packed(double* p) {
     return Rec{p, p + N * N, p + N * N + N, p + 2 * N * N + N, p + 2 * N * N + 2 * N, p + 3 * N * N + 2 * N};
   }
+  // the fields that drive the element flow (A, eta, J) alone, FLOW doubles at
+  // p: the RK4 stage buffers of the build (b, C, zeta are quadratures)
+  static constexpr int FLOW = 2 * N * N + N;
+  __device__ __forceinline__ static Rec flow(double* p) {
+    return Rec{p, nullptr, nullptr, p + N * N, p + N * N + N, nullptr};
+  }
   // element k of the public arrays
   __device__ __forceinline__ static Rec pub(const ElemPtrs& el, int64_t k, double* zeta_fallback) {
     return Rec{el.A + k * N * N, el.b + k * N, el.C + k * N * N, el.eta + k * N, el.J + k * N * N,
@@ -127,14 +133,18 @@ struct Rec {
 // element build right-hand side (factor form, see build_kernel)
 // ---------------------------------------------------------------------------
 
-// k = f(y); scratch: AL, P (N x M), w (M).  Plain loops, one output per
-// thread at a time, with the symmetric C, J formed on their upper triangles:
-// measured faster here than the register-blocked team products (the products
-// are thin, inner length M, and the triangles halve the C and J work).
+// k = f(y) for the flow fields (A, eta, J); the quadrature fields' rates
+// (db, dC, dzeta: nothing reads b, C or zeta) are added, times the RK4 weight
+// sq, straight into qacc's b, C, zeta, in the order the four-stage sum takes
+// them.  y and k may be flow records.  Scratch: AL, P (N x M), w (M).  Plain
+// loops, one output per thread at a time, with the symmetric C, J formed on
+// their upper triangles: measured faster here than the register-blocked team
+// products (the products are thin, inner length M, and the triangles halve the
+// C and J work).
 template <int N, int M, int TEAM>
 __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
                     const double* __restrict__ Lt, const double* __restrict__ Q, const double* __restrict__ qr,
-                    double* AL, double* P, double* w) {
+                    double* AL, double* P, double* w, double sq, Rec<N> qacc) {
   const double* A = y.A();
   const double* J = y.J();
   const double* eta = y.eta();
@@ -177,7 +187,7 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
         s = fma(-A[t * N + l], c[l], s);
         se = fma(J[t * N + l], c[l], se);
       }
-    k.b()[t] = s;
+    qacc.b()[t] = fma(sq, s, qacc.b()[t]);
     k.eta()[t] = se;
   }
   // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored)
@@ -193,8 +203,9 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
       sj = fma(-J[i * N + l], F[l * N + j], sj);
       sj = fma(-J[j * N + l], F[l * N + i], sj);
     }
-    k.C()[i * N + j] = sc;
-    k.C()[j * N + i] = sc;
+    const double cn = fma(sq, sc, qacc.C()[i * N + j]);
+    qacc.C()[i * N + j] = cn;
+    qacc.C()[j * N + i] = cn;
     k.J()[i * N + j] = sj;
     k.J()[j * N + i] = sj;
   }
@@ -203,17 +214,22 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
     for (int a = 0; a < M; ++a) z = fma(0.5 * w[a], w[a], z);
     if (c)
       for (int l = 0; l < N; ++l) z = fma(eta[l], c[l], z);
-    *k.zeta() = z;
+    *qacc.zeta() = fma(sq, z, *qacc.zeta());
   }
   sync<TEAM>();
 }
 
-// out = base + s * k over a packed record (out may alias base).
+// out = base + s * k over the flow fields A, eta, J (out may alias base).
 template <int N, int TEAM>
-__device__ __forceinline__ void axpy(int lane, double* out, const double* base, double s, const double* k) {
-  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) out[e] = fma(s, k[e], base[e]);
+__device__ __forceinline__ void axpy_flow(int lane, Rec<N> out, Rec<N> base, double s, Rec<N> k) {
+  for (int e = lane; e < N * N; e += TEAM) {
+    out.A()[e] = fma(s, k.A()[e], base.A()[e]);
+    out.J()[e] = fma(s, k.J()[e], base.J()[e]);
+  }
+  for (int e = lane; e < N; e += TEAM) out.eta()[e] = fma(s, k.eta()[e], base.eta()[e]);
   sync<TEAM>();
 }
+
 
 // copy a record (any layout) to another
 template <int N, int TEAM>
