@@ -28,6 +28,9 @@ struct TeamCfg<16> {
   // flow records) and at most 204 registers: 10 warps per SM
   static constexpr int BUILD_MIN = 10;
   static constexpr int BUILD_SLOTS = 152 * 10;
+  // the scan's combinations: <= 21.7 KB and <= 146 registers per warp
+  static constexpr int SCAN_MIN = 10;
+  static constexpr int SCAN_SLOTS = 152 * 10;
 };
 // n <= 8: the thread-per-element kernels do level 0 of the scans; these
 // warp-per-combination instances run the pairwise upper levels.
@@ -38,6 +41,8 @@ struct TeamCfgSmall {
   static constexpr int SLOTS = 152 * 8;
   static constexpr int BUILD_MIN = 1;
   static constexpr int BUILD_SLOTS = SLOTS;
+  static constexpr int SCAN_MIN = 1;
+  static constexpr int SCAN_SLOTS = SLOTS;
 };
 template <>
 struct TeamCfg<1> : TeamCfgSmall<1> {};
@@ -56,6 +61,8 @@ struct TeamCfg<64> {
   static constexpr int SLOTS = 152;
   static constexpr int BUILD_MIN = 1;
   static constexpr int BUILD_SLOTS = SLOTS;  // one global scratch slot per CTA
+  static constexpr int SCAN_MIN = 1;
+  static constexpr int SCAN_SLOTS = SLOTS;
 };
 
 // Doubles of per-slot scratch of each kernel.
@@ -242,7 +249,7 @@ __device__ __forceinline__ Rec<N> level_elem(const TeamScanArgs& a, int64_t k, d
 }
 
 template <int N, typename GT = double>
-__global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_team_kernel(TeamScanArgs a) {
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce_team_kernel(TeamScanArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = reduce_slot_doubles<N>();
   __shared__ double fs[TEAM];
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) reduce_team_kernel(TeamScanA
 }
 
 template <int N, bool Level0, typename GT = double>
-__global__ void __launch_bounds__(TeamCfg<N>::TEAM) down_team_kernel(TeamScanArgs a) {
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_team_kernel(TeamScanArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = down_slot_doubles<N>();
   constexpr int VS = team::val_doubles<N>();
@@ -569,7 +576,7 @@ static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemP
       TeamScanArgs a{};
       a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
       a.agg = (double*)(ws + pl.off_agg[l]); a.T = p.T; a.gscratch = gs;
-      team_launch<N>(reduce_team_kernel<N, GT>, pl.cnt[l], reduce_slot_doubles<N>(), a, st);
+      team_launch<N>(reduce_team_kernel<N, GT>, pl.cnt[l], reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
       c = pl.cnt[l];
       G = 2;
     }
@@ -588,10 +595,10 @@ static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemP
         a.S = S; a.v = v; a.zeta = zeta;
         a.maps = do_traj ? maps0 : nullptr;
         a.comp = do_traj ? comp1 : nullptr;
-        team_launch<N>(down_team_kernel<N, true, GT>, groups, down_slot_doubles<N>(), a, st);
+        team_launch<N>(down_team_kernel<N, true, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
       } else {
         a.vals = (double*)(ws + pl.off_val[l - 1]);
-        team_launch<N>(down_team_kernel<N, false, GT>, groups, down_slot_doubles<N>(), a, st);
+        team_launch<N>(down_team_kernel<N, false, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
       }
     }
   } else if (do_traj) {
@@ -823,7 +830,7 @@ static cudaError_t team_concat(int64_t Tcat, const ElemPtrs& el, double* S, doub
     TeamScanArgs a{};
     a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
     a.agg = (double*)(ws + pl.off_agg[l]); a.T = Tcat; a.gscratch = gs;
-    team_launch<N>(reduce_team_kernel<N>, pl.cnt[l], reduce_slot_doubles<N>(), a, st);
+    team_launch<N>(reduce_team_kernel<N>, pl.cnt[l], reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
     c = pl.cnt[l];
     G = 2;
   }
@@ -840,10 +847,10 @@ static cudaError_t team_concat(int64_t Tcat, const ElemPtrs& el, double* S, doub
     const int64_t groups = tdiv(a.cnt, a.G);
     if (l == 0) {
       a.S = S; a.v = v; a.zeta = zeta; a.maps = maps0; a.comp = nullptr;
-      team_launch<N>(down_team_kernel<N, true>, groups, down_slot_doubles<N>(), a, st);
+      team_launch<N>(down_team_kernel<N, true>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
     } else {
       a.vals = (double*)(ws + pl.off_val[l - 1]);
-      team_launch<N>(down_team_kernel<N, false>, groups, down_slot_doubles<N>(), a, st);
+      team_launch<N>(down_team_kernel<N, false>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
     }
   }
   launch_boundary_patch(N, maps0, patch, st);
