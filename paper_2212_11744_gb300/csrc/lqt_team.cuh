@@ -250,8 +250,8 @@ __device__ __forceinline__ void copy_rec(int lane, Rec<N> dst, Rec<N> src) {
 // caller's buffers.  piv_scratch: 2 * TEAM doubles + TEAM ints of scratch.
 // ---------------------------------------------------------------------------
 
-template <int N, int TEAM>
-__device__ void lu_solve(int lane, double* W, double* R, int Q, double* fscratch, int* iscratch) {
+template <int N, int TEAM, int Q>
+__device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* iscratch) {
   for (int k = 0; k < N; ++k) {
     // arg max |W[i][k]|, i >= k (lowest index on ties)
     double best = -1.0;
@@ -300,16 +300,35 @@ __device__ void lu_solve(int lane, double* W, double* R, int Q, double* fscratch
     // multipliers into column k (below the diagonal)
     for (int i = k + 1 + lane; i < N; i += TEAM) W[i * N + k] *= inv;
     sync<TEAM>();
-    const int rows = N - k - 1, cols = N - k - 1 + Q;
-    for (int e = lane; e < rows * cols; e += TEAM) {
-      const int i = k + 1 + e / cols, c = e % cols;
-      const double f = W[i * N + k];
-      if (c < N - k - 1) {
-        const int j = k + 1 + c;
-        W[i * N + j] = fma(-f, W[k * N + j], W[i * N + j]);
-      } else {
-        const int j = c - (N - k - 1);
-        R[i * Q + j] = fma(-f, R[k * Q + j], R[i * Q + j]);
+    // rank-1 update of the trailing rows
+    const int wc = N - k - 1, cols = wc + Q;
+    if constexpr (TEAM <= 32) {
+      // a warp: one row at a time, the lanes over its columns (no division by
+      // the step-dependent row length in the warp's instruction stream)
+      for (int i = k + 1; i < N; ++i) {
+        const double f = W[i * N + k];
+        for (int c = lane; c < cols; c += TEAM) {
+          if (c < wc) {
+            const int j = k + 1 + c;
+            W[i * N + j] = fma(-f, W[k * N + j], W[i * N + j]);
+          } else {
+            const int j = c - wc;
+            R[i * Q + j] = fma(-f, R[k * Q + j], R[i * Q + j]);
+          }
+        }
+      }
+    } else {
+      // a CTA: the threads over all (row, column) entries of the update
+      for (int e = lane; e < wc * cols; e += TEAM) {
+        const int i = k + 1 + e / cols, c = e % cols;
+        const double f = W[i * N + k];
+        if (c < wc) {
+          const int j = k + 1 + c;
+          W[i * N + j] = fma(-f, W[k * N + j], W[i * N + j]);
+        } else {
+          const int j = c - wc;
+          R[i * Q + j] = fma(-f, R[k * Q + j], R[i * Q + j]);
+        }
       }
     }
     sync<TEAM>();
@@ -388,7 +407,7 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
     R[i * Q + 2 * N] = (double)g;
   }
   sync<TEAM>();
-  lu_solve<N, TEAM>(lane, W, R, Q, fs, is);
+  lu_solve<N, TEAM, Q>(lane, W, R, fs, is);
   // R = [K1 | MC1 | z0]
   for (int i = lane; i < N; i += TEAM) z0[i] = R[i * Q + 2 * N];
   sync<TEAM>();
@@ -489,7 +508,7 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
     R[i * Q + N] = (double)g;
   }
   sync<TEAM>();
-  lu_solve<N, TEAM>(lane, W, R, Q, fs, is);
+  lu_solve<N, TEAM, Q>(lane, W, R, fs, is);
   for (int t = lane; t < N * N + N; t += TEAM) {
     if (t < N * N) Psi[t] = R[(t / N) * Q + (t % N)];
     else alpha[t - N * N] = R[(t - N * N) * Q + N];
