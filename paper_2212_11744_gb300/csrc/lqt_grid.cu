@@ -17,7 +17,7 @@
 //            launch.  After the last bit w_k = V(., t_k).
 //
 // Both products are one kernel: a 16 x 16 tile of outputs per CTA, one output
-// per thread, the reduction index in steps of 32 staged in shared memory.  The
+// per thread, the reduction index in steps of 64 staged in shared memory.  The
 // minimum is defined on FP64 sums, ascending k, strict improvement only (the
 // lowest index wins a tie).  GB300 retires FP64 adds at 1/64 of its FP32
 // rate, so every candidate is first screened in FP32 (a bracket around its
@@ -57,7 +57,7 @@ GridArgs grid_args(const lqt_grid_problem& p) {
 }
 
 constexpr int kGT = 16;  // output tile edge
-constexpr int kGK = 32;  // reduction step staged in shared memory
+constexpr int kGK = 64;  // reduction step staged in shared memory (a grid of <= 64 points: one tile)
 
 __device__ __forceinline__ double grid_x(const GridArgs& a, int i) { return __dadd_rn(a.x_min, __dmul_rn((double)i, a.dx)); }
 
@@ -191,7 +191,7 @@ union GridSmem {
   struct {
     float A[kGT][kGK + 2];
     float Bt[kGT][kGK + 2];  // B transposed: one row of k per output column
-  } f;  // screen; rows of 34 floats keep float2 reads aligned and conflict-free
+  } f;  // screen; rows of 66 floats keep float2 reads aligned and conflict-free
 };
 
 __device__ __forceinline__ float screen_hi(float a, float b) {
@@ -334,8 +334,10 @@ __global__ void __launch_bounds__(kGT* kGT, 4)
     unsigned long long pk = 0;
     int ns = 0;
     for (int k0 = 0; k0 < G; k0 += kGK) {
-      stage_float(op, sm, t, i0, c0, ncols, k0);
-      __syncthreads();
+      if (G > kGK) {  // one tile: pass 1's staging is still in place
+        stage_float(op, sm, t, i0, c0, ncols, k0);
+        __syncthreads();
+      }
       const int kend = G - k0 < kGK ? G - k0 : kGK;
       for (int kk = 0; kk < kend; kk += 2) {
         const float2 a2 = *reinterpret_cast<const float2*>(&sm.f.A[r_loc][kk]);
