@@ -26,8 +26,8 @@
 //     Cbar += -Lambda Sbar Lambda^T + sym(Lambda vbar l^T) - zetabar l l^T / 2.
 //  5. element build: discrete adjoint of the K classical RK4 steps of the
 //     backward conditional HJB ODEs (Theorem Backward_HJB_LQT), per
-//     sub-interval, forward stages recomputed (checkpoint = the sub-interval
-//     start), giving Fbar, Bbar (B = L U^-1 L^T), Qbar, qbar, rhobar, then
+//     sub-interval, about the stage inputs that this pass's element build
+//     recomputed and stored, giving Fbar, Bbar (B = L U^-1 L^T), Qbar, qbar, rhobar, then
 //     Xbar, rbar (Q = X, q = X r, rho = r'Xr for H = I) and, after the
 //     reduction over sub-intervals, Lbar = (Bbar + Bbar^T) L U^-1 and
 //     Ubar = -U^-1 L^T Bbar L U^-1.
@@ -475,7 +475,8 @@ __global__ void elem_adjoint_kernel(ElemAdjArgs a) {
 //   G = B J, beta = B eta
 //   dA = A G - A F, db = -A beta, dC = sym(-A B A^T), deta = -q - F^T eta + J beta,
 //   dJ = sym(-Q - J F - F^T J + J G), dz = -rho/2 + eta^T beta / 2
-// and its vector-Jacobian product; one warp per sub-interval (below).
+// whose vector-Jacobian product the reverse sweep evaluates at every stored
+// stage input; one warp per sub-interval (below).
 
 struct RK4AdjArgs {
   int n, K, M;
