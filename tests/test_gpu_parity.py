@@ -269,3 +269,31 @@ def test_large_state_full_size_local_checks():
         xn = np.linalg.solve(np.eye(n) + e["C"] @ S[k + 1], e["A"] @ x[k] + e["b"] + e["C"] @ v[k + 1])
         assert relerr(x[k + 1], xn) <= TOL, k
         assert relerr(u[k], np.linalg.solve(U, L.T @ (v[k] - S[k] @ x[k]))) <= TOL, k
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("T", [1 << 10, 1 << 14])
+def test_parallel_solve_beats_the_sequential_sweep(T):
+    """The point-mass workload at T = 2^10 and 2^14 (K = 4): the parallel solve
+    (lqt_solve) takes less time than the one-thread sequential GPU sweep
+    (lqt_solve_sequential, the paper's sequential method) on the same grid,
+    both timed with CUDA events after a warm-up."""
+    m = lqt()
+    dp = m.DeviceProblem(W.point_mass_2d(T=T, K=4))
+    par = m.lqt_solve(dp)
+    seq = m.lqt_solve_sequential(dp)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    t_par = min(timed(lambda: m.lqt_solve(dp, out=par)) for _ in range(3))
+    t_seq = timed(lambda: m.lqt_solve_sequential(dp, out=seq))
+    assert m.lqt_get_status() == 0
+    print(f"T={T}: parallel {t_par:.3f} ms, sequential {t_seq:.1f} ms")
+    assert t_par < t_seq, (t_par, t_seq)
