@@ -384,11 +384,27 @@ def measure_rows(T_headline):
                 "ms_forward": fms, "ms_backward": bms}
 
     def small():
+        """The double integrator (T = 1024, K = 10): at this size a solve is
+        ~60 dependent short launches, so it is also timed captured in one CUDA
+        graph (the calls allocate nothing and never synchronise)."""
         p = W.double_integrator()
         dp = lqt.DeviceProblem(p)
-        o = lqt.lqt_solve(dp)
-        ms = _events_ms(lambda: lqt.lqt_solve(dp, out=o), 20)
-        return {"workload": "double integrator n=2, T=1024, K=10", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms}
+        ws = torch.empty(lqt.lqt_workspace_size(dp, lqt.LQT_WS_SOLVE), dtype=torch.uint8, device="cuda")
+        o = lqt.lqt_solve(dp, ws=ws)
+        ms = _events_ms(lambda: lqt.lqt_solve(dp, out=o, ws=ws), 20)
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            lqt.lqt_solve(dp, out=o, ws=ws)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=st):
+                lqt.lqt_solve(dp, out=o, ws=ws)
+        torch.cuda.synchronize()
+        graph.replay()
+        ms_graph = _events_ms(graph.replay, 20)
+        return {"workload": "double integrator n=2, T=1024, K=10", "value": p.T / (ms_graph * 1e-3), "unit": UNIT,
+                "ms_graph": ms_graph, "ms_stream_launches": ms, "value_stream_launches": p.T / (ms * 1e-3),
+                "status": lqt.lqt_get_status()}
 
     def densify():
         p = W.point_mass_2d(T=T_headline, K=K_STEPS)
