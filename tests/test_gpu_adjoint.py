@@ -96,7 +96,7 @@ def test_backward_matches_oracle_reverse_mode(name, make):
 
 
 def test_autograd_function_cost_and_terminal_state():
-    """The config-4 style loss through LQTSolve.apply: total optimal cost plus
+    """The differentiable workload's loss through LQTSolve.apply: total optimal cost plus
     |x(t_f) - x_target|^2, gradients against the oracle's reverse mode."""
     from paper_2212_11744_gb300.autograd import LQTSolve
     p = W.differentiable_n8(T=128)
@@ -119,7 +119,7 @@ def test_autograd_function_cost_and_terminal_state():
 
 
 @pytest.mark.slow
-def test_config4_gradients_full_size_fd_and_reverse_mode():
+def test_differentiable_n8_full_size_gradients_fd_and_reverse_mode():
     """n = 8, T = 2^14: loss = cost + |x_T - x_target|^2 with Xf tied to X,
     parameters diag(X), diag(U), r (T x 8) and F.  The GPU gradient's
     directional derivatives along 32 seeded random directions against central

@@ -411,9 +411,9 @@ def test_time_varying_against_adaptive_reference(modes):
 
 
 def test_scan_and_sequential_agree_at_every_boundary():
-    """The spec invariant: the parallel (scan) route and the sequential
-    Riccati sweep agree at every t_i, to discretisation error that vanishes at
-    order 4 (config-2-like point mass, short horizon)."""
+    """The parallel (scan) route and the sequential Riccati sweep agree at
+    every t_i, to discretisation error that vanishes at order 4 (the 2-D point
+    mass on a short horizon)."""
     base = W.point_mass_2d(T=32, K=4)
     base.t = W.uniform_grid(0.0, 4.0, 32)
     errs = []
