@@ -331,7 +331,12 @@ lqt_status lqt_solve_batched(const lqt_batch *b, const lqt_tuning *tune, double 
  * outputs.  Copies the inputs to the caller's device workspace (its size from
  * lqt_workspace_size(p, LQT_WS_SOLVE) + lqt_host_staging_size(p)), runs
  * lqt_solve on `stream`, copies the outputs back and synchronises the stream.
- * Host buffers should be pinned for full copy speed. */
+ * For n <= 8 and T >= 2^16 the sampled coefficients are copied in up to 16
+ * chunks on a stream of the call's own, each chunk's derived coefficients and
+ * elements built on `stream` as soon as it (and the next chunk, which holds its
+ * last sample) has arrived; the results are lqt_solve's, bit for bit.  Host
+ * buffers should be pinned for full copy speed (pageable ones work, with
+ * copies that complete before they return). */
 size_t lqt_host_staging_size(const lqt_problem *p);
 lqt_status lqt_solve_host(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
                           double *u, double *cost, void *ws, size_t ws_bytes, void *stream);

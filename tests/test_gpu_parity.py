@@ -198,6 +198,22 @@ def test_solve_host_matches_device(name, make):
         assert np.array_equal(to_np(dev[k]), host[k].numpy()), k
 
 
+def test_solve_host_with_pageable_buffers():
+    """The chunked host path with pageable (not pinned) host inputs and
+    outputs: the copies then complete before the calls return, the results are
+    still lqt_solve's bit for bit."""
+    p = W.point_mass_2d(T=(1 << 16) + 7, K=4)
+    m = lqt()
+    dev = m.lqt_solve(m.DeviceProblem(p))
+    hp = m.HostProblem(p, pinned=False)
+    need = m.lqt_workspace_size(hp, m.LQT_WS_SOLVE) + m.lqt_host_staging_size(hp)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    host = m.lqt_solve_host(hp, ws, out=m.host_solution(hp, pinned=False))
+    torch.cuda.synchronize()
+    for k in ("S", "v", "zeta", "x", "u", "cost"):
+        assert np.array_equal(to_np(dev[k]), host[k].numpy()), k
+
+
 def test_nonfinite_input_sets_status():
     p = W.point_mass_2d(T=64, K=4)
     p.r.values[100, 0] = np.nan
