@@ -486,20 +486,23 @@ __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V,
   constexpr int Q = N + 1;
   double W[N * N];
   double R[N * Q];
+  // W = I + C S2 and b + C v2 in FP64 whatever G is: they define the
+  // one-sub-interval map (Psi, alpha) that the state scan composes T times,
+  // where FP32 rounding would accumulate
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      G s = (i == j) ? G(1) : G(0);
+      double s = (i == j) ? 1.0 : 0.0;
 #pragma unroll
-      for (int l = 0; l < N; ++l) s = fma(gf<G>(e.C[sidx<N>(i, l)]), gf<G>(V.S[sidx<N>(l, j)]), s);
-      W[i * N + j] = (double)s;
+      for (int l = 0; l < N; ++l) s = fma(e.C[sidx<N>(i, l)], V.S[sidx<N>(l, j)], s);
+      W[i * N + j] = s;
       R[i * Q + j] = e.A[i * N + j];
     }
-    G s = gf<G>(e.b[i]);
+    double s = e.b[i];
 #pragma unroll
-    for (int l = 0; l < N; ++l) s = fma(gf<G>(e.C[sidx<N>(i, l)]), gf<G>(V.v[l]), s);
-    R[i * Q + N] = (double)s;
+    for (int l = 0; l < N; ++l) s = fma(e.C[sidx<N>(i, l)], V.v[l], s);
+    R[i * Q + N] = s;
   }
   lu_solve<N, Q>(W, R);
 #pragma unroll

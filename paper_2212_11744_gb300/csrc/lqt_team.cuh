@@ -498,14 +498,17 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
   double* wv = l0 + N;
   const double* A = e.A();
   const double* C = e.C();
-  // W = I + C S2 ; R = [A | b + C v2]
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return C[i * N + l]; }, [&](int l, int j) { return S2[l * N + j]; },
-                         [&](int i, int j, G v) { W[i * N + j] = (double)v + (i == j ? 1.0 : 0.0); });
+  // W = I + C S2 ; R = [A | b + C v2], in FP64 whatever G is: they define
+  // the one-sub-interval map (Psi, alpha) that the state scan composes T
+  // times, where FP32 rounding would accumulate
+  gemm<N, N, N, TEAM, double>(lane, [&](int i, int l) { return C[i * N + l]; },
+                              [&](int l, int j) { return S2[l * N + j]; },
+                              [&](int i, int j, double v) { W[i * N + j] = v + (i == j ? 1.0 : 0.0); });
   for (int t = lane; t < N * N; t += TEAM) R[(t / N) * Q + (t % N)] = A[t];
   for (int i = lane; i < N; i += TEAM) {
-    G g = (G)(e.b()[i]);
-    for (int l = 0; l < N; ++l) g = fma((G)(C[i * N + l]), (G)(v2[l]), g);
-    R[i * Q + N] = (double)g;
+    double g = e.b()[i];
+    for (int l = 0; l < N; ++l) g = fma(C[i * N + l], v2[l], g);
+    R[i * Q + N] = g;
   }
   sync<TEAM>();
   lu_solve<N, TEAM, Q>(lane, W, R, fs, is);
