@@ -238,6 +238,73 @@ def cpu_baseline_grid(g):
             "sample": f"the whole G = {g.G}, T = {g.T} problem, {dt:.2f} s"}
 
 
+def _oracle_timed(fn, units: float, unit: str, sample: str) -> dict:
+    t0 = time.perf_counter()
+    fn()
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": unit, "cores": 1, "kind": "oracle", "sample": f"{sample}, {dt:.2f} s"}
+
+
+def cpu_baseline_batch(max_seconds: float = 6.0) -> dict:
+    """The oracle on the first problems of the 4096-problem batch (mixed n and
+    T, in the batch's order), one after the other, until about max_seconds."""
+    import oracle
+    import workloads as W
+    t0 = time.perf_counter()
+    done, subs = 0, 0
+    while time.perf_counter() - t0 < max_seconds and done < 4096:
+        p = W.batched_member(done)
+        oracle.solve(p)
+        subs += p.T
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": subs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first {done} problems of the batch ({subs} sub-intervals), {dt:.2f} s"}
+
+
+def cpu_baseline_adjoint(Ts: int = 256) -> dict:
+    """The oracle's reverse mode (torch CPU autograd through its restatement)
+    on the first Ts sub-intervals of the differentiable n = 8 workload,
+    forward + backward."""
+    import torch
+
+    from oracle import lqt_torch as LT
+    import workloads as W
+    p = W.truncate(W.differentiable_n8(), Ts)
+
+    def run():
+        t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64).requires_grad_()
+        F, L, X, U, r, Xf, x0 = (t(p.F.values), t(p.L.values), t(p.X.values), t(p.U.values), t(p.r.values),
+                                 t(p.Xf), t(p.x0))
+        rf = t(p.rf) if p.rf is not None else None
+        o = LT.solve(p, F, L, X, U, r, Xf, rf, x0)
+        loss = o["cost"] + ((o["x"][-1] - torch.tensor(p.extra["x_target"])) ** 2).sum()
+        loss.backward()
+
+    return _oracle_timed(run, Ts, UNIT + " (forward + backward)",
+                         f"the first {Ts} of the {1 << 14} sub-intervals, reverse mode")
+
+
+def cpu_baseline_densify(Ts: int = 1 << 14) -> dict:
+    import oracle
+    import workloads as W
+    p = W.truncate(W.point_mass_2d(T=T_DEFAULT, K=K_STEPS), Ts)
+    return _oracle_timed(lambda: oracle.densify(p, oracle.solve(p)), Ts * p.K, "sub-steps/s (solve + densify)",
+                         f"the first {Ts} sub-intervals of the point mass")
+
+
+def cpu_baseline_method2(Ts: int = 1 << 14) -> dict:
+    import oracle
+    import workloads as W
+    p = W.truncate(W.point_mass_2d(T=T_DEFAULT, K=K_STEPS), Ts)
+
+    def run():
+        sol = oracle.solve(p)
+        oracle.trajectory_method2(p, sol["S"], sol["v"])
+
+    return _oracle_timed(run, Ts, UNIT, f"the first {Ts} sub-intervals of the point mass (values, then Method 2)")
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
@@ -342,7 +409,8 @@ def measure_rows(T_headline):
                             "of four batched solves (one per n)",
                 "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "sub_intervals": total,
                 "per_n_ms": per, "per_n_count": {str(n): bt.B for n, bt in bts.items()},
-                "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": st}
+                "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": st,
+                "cpu_baseline": cpu_baseline_batch()}
 
     def mixed():
         out = {}
@@ -367,6 +435,7 @@ def measure_rows(T_headline):
                                         "f64_value": p.T / (ms64 * 1e-3),
                                         "rel_err_vs_f64": {k: _relmax(b[k], a[k]) for k in ("S", "v", "zeta", "x")}}
         out["note"] = "errors against the FP64 oracle are asserted <= 1e-4 in tests/test_gpu_mixed.py"
+        out["cpu_baseline"] = cpu_baseline_sample(W.truncate(W.point_mass_2d(T=T_headline, K=K_STEPS), 1 << 17))
         return out
 
     def adjoint():
@@ -381,7 +450,7 @@ def measure_rows(T_headline):
         bms = _events_ms(lambda: lqt.lqt_backward(dp, fwd, gx=gx, g_cost=1.0, ws=ws), 3)
         return {"workload": "n=8, m=4, T=2^14, K=4; loss = cost + |x_T - x_target|^2; gradients w.r.t. F, L, X, U, "
                             "r, Xf, x0", "value": p.T / ((fms + bms) * 1e-3), "unit": UNIT + " (forward + backward)",
-                "ms_forward": fms, "ms_backward": bms}
+                "ms_forward": fms, "ms_backward": bms, "cpu_baseline": cpu_baseline_adjoint()}
 
     def small():
         """The double integrator (T = 1024, K = 10): at this size a solve is
@@ -404,7 +473,7 @@ def measure_rows(T_headline):
         ms_graph = _events_ms(graph.replay, 20)
         return {"workload": "double integrator n=2, T=1024, K=10", "value": p.T / (ms_graph * 1e-3), "unit": UNIT,
                 "ms_graph": ms_graph, "ms_stream_launches": ms, "value_stream_launches": p.T / (ms * 1e-3),
-                "status": lqt.lqt_get_status()}
+                "status": lqt.lqt_get_status(), "cpu_baseline": cpu_baseline_sample(p)}
 
     def densify():
         p = W.point_mass_2d(T=T_headline, K=K_STEPS)
@@ -418,7 +487,8 @@ def measure_rows(T_headline):
         fine = p.T * p.K
         return {"workload": "point mass T=2^20, K=4: solution at all 4 194 305 RK4 sub-steps from the boundary "
                             "solution", "value": fine / ((sms + dms) * 1e-3), "unit": "sub-steps/s (solve + densify)",
-                "ms_densify": dms, "ms_solve": sms, "status": lqt.lqt_get_status()}
+                "ms_densify": dms, "ms_solve": sms, "status": lqt.lqt_get_status(),
+                "cpu_baseline": cpu_baseline_densify()}
 
     def method2():
         p = W.point_mass_2d(T=T_headline, K=K_STEPS)
@@ -430,7 +500,7 @@ def measure_rows(T_headline):
         return {"workload": "point mass T=2^20, K=4: values by the suffix scan, states by Method 2 (forward-ODE "
                             "elements, prefix scan)", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms,
                 "rel_diff_vs_method1": {k: _relmax(m2[k], m1[k]) for k in ("x", "u")},
-                "status": lqt.lqt_get_status()}
+                "status": lqt.lqt_get_status(), "cpu_baseline": cpu_baseline_method2()}
 
     def invariant():
         """The 4096-problem batch and the n = 64 problem with the time-invariant
@@ -463,7 +533,8 @@ def measure_rows(T_headline):
         total = int(sum(p.T for p in probs))
         res = {"workload": "the 4096-problem batch (as a4) with the time-invariant element build",
                "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "per_n_ms": per,
-               "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": lqt.lqt_get_status()}
+               "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": lqt.lqt_get_status(),
+               "cpu_baseline": "as a4 (the oracle's general element build is the reference of this build)"}
         del bts, outs, g
         p = W.large_state_n64(T=1 << 16)
         dp = lqt.DeviceProblem(p)
