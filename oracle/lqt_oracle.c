@@ -24,6 +24,11 @@
  *      t_f, then a forward RK4 of the closed-loop ODE (eq.
  *      optimal_trajectory_ODE_LQT) with the control law eq. LQT_optimal_control.
  *
+ * and, further down, the within-block densification (Sec. IV-E, Sec. VI-A),
+ * Method 2 with forward-ODE elements (Sec. IV-C, Theorem Forward_HJB_LQT;
+ * Sec. IV-E) and the grid method for the nonlinear scalar example (Sec. VI-B,
+ * App. E), each with its own header comment.
+ *
  * Readings where the paper is silent (each is listed in the design notes):
  *  - zeta (the state-free part of V, eq. V_quadratic_LQT) is carried along:
  *    element ODE d zeta/ds = -1/2 r'Xr + 1/2 eta'B eta + eta'c, terminal
