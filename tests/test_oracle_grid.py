@@ -46,6 +46,34 @@ def test_interpolated_minimum_is_exact_for_quadratics():
         assert np.abs(got - exact).max() <= 1e-12 * max(1.0, abs(exact))
 
 
+def test_ties_take_the_lowest_index():
+    """Two grid minimisers with exactly equal sums, each the middle of three
+    points on its own parabola: the refined minimum is that of the parabola
+    at the lower index (the reading for ties), known in closed form
+    c - a delta^2 for the parabola a (x - x_k - delta)^2 + c - a delta^2."""
+    g = W.falling_body(G=41, T=1)
+    dx, G = g.dx, g.G
+    c = 1.25
+
+    def parabola_points(a, delta):
+        return [c + a * ((s * dx - delta) ** 2 - delta ** 2) for s in (-1, 0, 1)]
+
+    k1, k2 = 12, 29
+    a1, d1 = 2.0, 0.3 * dx
+    a2, d2 = 0.5, -0.4 * dx
+    row = np.full(G, 50.0)
+    row[k1 - 1:k1 + 2] = parabola_points(a1, d1)
+    row[k2 - 1:k2 + 2] = parabola_points(a2, d2)
+    assert row[k1] == row[k2] == c and row.min() == c
+    M = np.tile(row, (G, 1))
+    got = oracle.grid_apply(g, M, np.zeros(G))
+    expect = c - a1 * d1 ** 2
+    assert np.abs(got - expect).max() <= 1e-12, (got[0], expect, c - a2 * d2 ** 2)
+    # reversed rows put the other parabola at the lower index
+    got_rev = oracle.grid_apply(g, M[:, ::-1].copy(), np.zeros(G))
+    assert np.abs(got_rev - (c - a2 * d2 ** 2)).max() <= 1e-12
+
+
 def test_plain_combination_is_min_plus_and_associative():
     g = W.falling_body(G=13, T=1, interp=False)
     rng = np.random.default_rng(4)

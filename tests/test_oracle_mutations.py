@@ -109,6 +109,8 @@ MUTATIONS = [
     ("grid: terminal factor", "phi[i] = 0.5 * P->qf * x * x;", "phi[i] = P->qf * x * x;", 0),
     ("grid: block substeps", "for (int m = 1; m < P->substeps; ++m) {", "for (int m = 2; m < P->substeps; ++m) {", 0),
     ("grid: doubling skips a power", "if (e & (1L << l)) {", "if (l > 0 && (e & (1L << l))) {", 0),
+    ("grid: ties to the highest index", "if (v < best) { best = v; bi = j; }", "if (v <= best) { best = v; bi = j; }",
+     0),
     # shared small linear algebra
     ("mtm: operand not transposed", "for (int l = 0; l < k; ++l) s += a[l * p + i] * b[l * q + j];",
      "for (int l = 0; l < k; ++l) s += a[i * k + l] * b[l * q + j];", 0),
