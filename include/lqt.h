@@ -37,8 +37,14 @@
  *  - FP64 throughout.
  *  - Errors: invalid arguments are rejected on the host before any launch and
  *    returned directly.  Numerical trouble found on the device (a non-finite
- *    value in an output, a zero pivot) is recorded in a per-device status word
- *    read and cleared by lqt_get_status().
+ *    value in an output; a singular system) is recorded in a per-device status
+ *    word read and cleared by lqt_get_status().  A system W x = r of a
+ *    combination (W = I + C J, App. B: eigenvalues >= 1 for PSD C, J) or of a
+ *    control law counts as singular when an LU pivot's magnitude is at most
+ *    2^-40 (about 9.1e-13) times the largest magnitude of its row in the
+ *    original W: its condition number is then beyond ~1e12 and FP64 no longer
+ *    carries the digits of a 1e-9 result.  A non-positive Cholesky pivot of
+ *    U counts too.
  *  - Supported state dimensions n: 1, 2, 3, 4, 8 (one thread per element),
  *    16 and 64 (a warp / a CTA per element).  Other n return
  *    LQT_EUNSUPPORTED.  m <= 16, nr <= 64.
@@ -58,7 +64,8 @@ typedef enum {
   LQT_EINVAL = 1,       /* bad dimension, NULL pointer, bad sampling mode       */
   LQT_EWORKSPACE = 2,   /* workspace NULL or smaller than lqt_workspace_size()   */
   LQT_ENONFINITE = 3,   /* device found a NaN/Inf in an output                   */
-  LQT_ESINGULAR = 4,    /* device found a zero pivot (U or I + C J singular)     */
+  LQT_ESINGULAR = 4,    /* device found a (numerically) singular system: see
+                           "Errors" above                                          */
   LQT_ETIMEOUT = 5,     /* lqt_get_status() deadline passed before the stream     */
   LQT_ECUDA = 6,        /* a CUDA runtime call failed                             */
   LQT_EUNSUPPORTED = 7  /* dimension not compiled in                              */
@@ -351,7 +358,9 @@ lqt_status lqt_solve_host(const lqt_problem *p, const double *x0, double *S, dou
  * until the process exits.
  *  - Problems whose scan needs more scratch than that (see
  *    lqt_workspace_size(p, LQT_WS_VALUE)) return LQT_EWORKSPACE before any
- *    launch.  For n = 4 this admits T up to 2^19.
+ *    launch.  The largest T admitted, by state dimension: n = 1: 7 454 719;
+ *    n = 2: 2 795 391; n = 3: 44 607; n = 4: 26 877; n = 8: 7 429;
+ *    n = 16: 1 951; n = 64: none (every n = 64 problem is rejected).
  *  - The first call on a device looks up the array's device address (with that
  *    device current) and caches it: make that first call before any stream
  *    capture.
@@ -436,6 +445,20 @@ lqt_status lqt_grid_values(const lqt_grid_problem *p, const double *Vblock, doub
  * reads and clears the current device's status word.  Returns LQT_OK,
  * LQT_ENONFINITE, LQT_ESINGULAR, LQT_ETIMEOUT or LQT_ECUDA. */
 lqt_status lqt_get_status(void *stream, int32_t timeout_ms);
+
+/* Throughput probe of the FMA pipes, a measurement aid with no counterpart in
+ * the paper: the roofline denominator of this library's FP64-bound kernels
+ * (Sec. IV-A and IV-B give their work; the chip's FP64 rate bounds it), taken
+ * on the device they run on.  Launches `blocks` CTAs of `threads` threads
+ * (a multiple of 32, <= 1024); every thread whose lane index is below
+ * `active_lanes` (1..32) runs 8 independent chains x <- x a + b for `iters`
+ * rounds; precision 0 = FP64 (DFMA), 1 = FP32 (FFMA).  Work:
+ * 2 * 8 * iters * blocks * threads * active_lanes / 32 flop (FMA = 2); the
+ * caller times the launch on `stream`.  out: device scratch of
+ * blocks * threads doubles, caller-owned (written, meaningless).  Invalid
+ * sizes: LQT_EINVAL before any launch. */
+lqt_status lqt_probe_fma_rate(int32_t precision, int32_t blocks, int32_t threads, int32_t iters,
+                              int32_t active_lanes, double *out, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *lqt_strerror(lqt_status s);

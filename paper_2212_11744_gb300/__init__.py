@@ -30,6 +30,7 @@ __all__ = [
     "lqt_trajectory_method2", "lqt_solve_method2", "lqt_build_elements_invariant", "lqt_solve_invariant",
     "lqt_get_status", "lqt_strerror", "lqt_last_launch_count", "LQTError", "library_path", "lqt_backward",
     "grid_struct", "lqt_grid_workspace_size", "lqt_grid_block", "lqt_grid_combine", "lqt_grid_values",
+    "lqt_probe_fma_rate",
 ]
 
 _COEFS = ("F", "L", "c", "H", "X", "U", "r")
@@ -373,6 +374,15 @@ def lqt_grid_values(g, Vblock: torch.Tensor, out: Optional[torch.Tensor] = None,
     ws = _grid_workspace(g, 1, ws, Vblock.device)
     _abi.check(_abi.lib().lqt_grid_values(ct.byref(grid_struct(g)), Vblock.data_ptr(), out.data_ptr(),
                                           ws.data_ptr(), ws.numel(), _stream_handle(stream)), "lqt_grid_values")
+    return out
+
+
+def lqt_probe_fma_rate(precision: int, blocks: int, threads: int, iters: int, active_lanes: int = 32,
+                       out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Launches the FMA-pipe probe (timing is the caller's); returns its scratch."""
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda") if out is None else out
+    _abi.check(_abi.lib().lqt_probe_fma_rate(precision, blocks, threads, iters, active_lanes, out.data_ptr(),
+                                             _stream_handle(stream)), "lqt_probe_fma_rate")
     return out
 
 

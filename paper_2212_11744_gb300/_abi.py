@@ -26,6 +26,7 @@ EXPORTED = (
     "lqt_batch_boundaries", "lqt_batch_plan", "lqt_solve_batched", "lqt_solve_mixed", "lqt_densify",
     "lqt_build_elements_forward", "lqt_trajectory_method2", "lqt_solve_method2", "lqt_build_elements_invariant",
     "lqt_solve_invariant", "lqt_grid_workspace_size", "lqt_grid_block", "lqt_grid_combine", "lqt_grid_values",
+    "lqt_probe_fma_rate",
 )
 
 _dp = ct.POINTER(ct.c_double)
@@ -126,6 +127,8 @@ def lib():
     L.lqt_grid_block.argtypes = [GP, v, v, ct.c_size_t, v]
     L.lqt_grid_combine.argtypes = [GP, v, v, v, v]
     L.lqt_grid_values.argtypes = [GP, v, v, v, ct.c_size_t, v]
+    L.lqt_probe_fma_rate.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, v, v]
+    L.lqt_probe_fma_rate.restype = ct.c_int
     L.lqt_last_launch_count.argtypes = []
     L.lqt_last_launch_count.restype = ct.c_int32
     for f in ("lqt_build_elements", "lqt_scan_value", "lqt_scan_trajectory", "lqt_solve", "lqt_solve_sequential",

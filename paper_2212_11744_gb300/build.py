@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "liblqt_gb300.so"
-SOURCES = ["lqt_api.cu", "lqt_build.cu", "lqt_scan.cu", "lqt_seq.cu", "lqt_static.cu", "lqt_adjoint.cu", "lqt_team.cu", "lqt_batched.cu", "lqt_dense.cu", "lqt_forward.cu", "lqt_invariant.cu", "lqt_invariant_batch.cu", "lqt_grid.cu"]
+SOURCES = ["lqt_api.cu", "lqt_build.cu", "lqt_scan.cu", "lqt_seq.cu", "lqt_static.cu", "lqt_adjoint.cu", "lqt_team.cu", "lqt_batched.cu", "lqt_dense.cu", "lqt_forward.cu", "lqt_invariant.cu", "lqt_invariant_batch.cu", "lqt_grid.cu", "lqt_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

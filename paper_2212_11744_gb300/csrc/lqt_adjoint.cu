@@ -100,17 +100,26 @@ __device__ __forceinline__ void symm(int n, double* a) {
       a[j * n + i] = s;
     }
 }
-// Solve W X = R (W n x n, R n x q, both overwritten) with partial pivoting.
-__device__ void solve_rt(int n, int q, double* W, double* R) {
+// Solve W X = R (W n x n, n <= 16, R n x q, both overwritten) with partial
+// pivoting; a pivot no larger than 2^-40 of its row's original scale sets the
+// SINGULAR status bit (pivot_too_small).  The row scale is max_j |W_ij|, and
+// at least 1 when unit_part (W = I + P: cancellation between I and P counts).
+__device__ void solve_rt(int n, int q, double* W, double* R, bool unit_part) {
+  unsigned long long rk[16];
+  for (int i = 0; i < n; ++i) {
+    rk[i] = unit_part ? mag_key(1.0) : 0ull;
+    for (int j = 0; j < n; ++j) rk[i] = umax64(rk[i], mag_key(W[i * n + j]));
+  }
   for (int k = 0; k < n; ++k) {
     int piv = k;
     double best = fabs(W[k * n + k]);
     for (int i = k + 1; i < n; ++i)
       if (fabs(W[i * n + k]) > best) { best = fabs(W[i * n + k]); piv = i; }
-    if (best == 0.0) flag(kStatusSingular);
+    if (pivot_too_small(best, rk[piv])) flag(kStatusSingular);
     if (piv != k) {
       for (int j = 0; j < n; ++j) { const double s = W[k * n + j]; W[k * n + j] = W[piv * n + j]; W[piv * n + j] = s; }
       for (int j = 0; j < q; ++j) { const double s = R[k * q + j]; R[k * q + j] = R[piv * q + j]; R[piv * q + j] = s; }
+      const unsigned long long t = rk[k]; rk[k] = rk[piv]; rk[piv] = t;
     }
     const double inv = 1.0 / W[k * n + k];
     for (int i = k + 1; i < n; ++i) {
@@ -225,13 +234,13 @@ __global__ void map_adjoint_kernel(MapAdjArgs a) {
       for (int c = 0; c < n; ++c) Wt[i * n + c] = W[c * n + i];
     double Wc[AN * AN];
     for (int i = 0; i < nn; ++i) Wc[i] = W[i];
-    solve_rt(n, q, Wc, Z);  // Z = [Psi | alpha]
+    solve_rt(n, q, Wc, Z, true);  // Z = [Psi | alpha]
     // Zbar = [xbar_k x_j^T | xbar_k]; Rbar = W^-T Zbar
     for (int i = 0; i < n; ++i) {
       for (int c = 0; c < n; ++c) Rb[i * q + c] = xbk[i] * xj[c];
       Rb[i * q + n] = xbk[i];
     }
-    solve_rt(n, q, Wt, Rb);
+    solve_rt(n, q, Wt, Rb, true);
     // Wbar = -Rbar Z^T  (n x n)
     double Wb[AN * AN];
     for (int i = 0; i < n; ++i)
@@ -874,7 +883,7 @@ __global__ void b_to_lu_kernel(int n, int m, int64_t cnt, const double* __restri
   for (int i = 0; i < m * m; ++i) W[i] = Us[i];
   for (int i = 0; i < m; ++i)
     for (int c = 0; c < n; ++c) R[i * n + c] = Ls[c * m + i];
-  solve_rt(m, n, W, R);  // R = U^-1 L^T  (m x n)
+  solve_rt(m, n, W, R, false);  // R = U^-1 L^T  (m x n)
   // Lbar = (Bbar + Bbar^T) G, G = R^T (n x m)
   for (int i = 0; i < n; ++i)
     for (int c = 0; c < m; ++c) {

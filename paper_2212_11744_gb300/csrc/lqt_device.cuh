@@ -262,12 +262,42 @@ __device__ __forceinline__ void store_val(double* __restrict__ p, const Val<N>& 
 // LU with partial pivoting, applied to an augmented right-hand side block
 // ---------------------------------------------------------------------------
 
+// Magnitude key of a double: its bit pattern without the sign.  For finite
+// values (and +inf) comparing keys as unsigned integers orders them like |x|,
+// on the integer pipes (FP64 compares share the slow FP64 pipe).
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+// Relative pivot tolerance 2^-40 (about 9.1e-13): a pivot this small next to
+// its row's original scale means a condition number beyond ~1e12, where an
+// FP64 solve no longer carries the digits a 1e-9 result needs.  Applied to the
+// key: subtracting 40 from the exponent field multiplies a normal double by
+// 2^-40 (row scales below 2^-982 get the threshold 0).
+constexpr unsigned long long kPivotTolExpShift = 40ull << 52;
+__device__ __forceinline__ bool pivot_too_small(double piv, unsigned long long row_key) {
+  const unsigned long long thr = row_key > kPivotTolExpShift ? row_key - kPivotTolExpShift : 0ull;
+  return mag_key(piv) <= thr;
+}
+
 // Solves W X = R in place (W: N x N, R: N x Q, both row-major in registers).
 // Row exchanges are done with predicated selects so every register index stays
-// a compile-time constant.  A zero pivot sets the SINGULAR status bit and the
-// solution is then meaningless (but finite work).
+// a compile-time constant.  W = I + P (P = C J or C S in every use): a pivot no
+// larger than 2^-40 times its row's original scale, max(1, max_j |W_ij|) (the
+// identity's 1 included, so that cancellation between I and P counts), sets
+// the SINGULAR status bit: the system is then singular to working precision
+// and the solution meaningless (but finite work).
 template <int N, int Q>
 __device__ __forceinline__ void lu_solve(double (&W)[N * N], double (&R)[N * Q]) {
+  unsigned long long rk[N];  // original row scales, as magnitude keys
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    rk[i] = mag_key(1.0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) rk[i] = umax64(rk[i], mag_key(W[i * N + j]));
+  }
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     // bring the largest |W[i][k]|, i >= k, to row k
@@ -286,9 +316,12 @@ __device__ __forceinline__ void lu_solve(double (&W)[N * N], double (&R)[N * Q])
         R[k * Q + j] = sw ? c : a;
         R[i * Q + j] = sw ? a : c;
       }
+      const unsigned long long a = rk[k], c = rk[i];
+      rk[k] = sw ? c : a;
+      rk[i] = sw ? a : c;
     }
     const double piv = W[k * N + k];
-    if (piv == 0.0) flag(kStatusSingular);
+    if (pivot_too_small(piv, rk[k])) flag(kStatusSingular);
     const double inv = 1.0 / piv;
 #pragma unroll
     for (int i = k + 1; i < N; ++i) {

@@ -252,7 +252,7 @@ template <int N, typename GT = double>
 __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce_team_kernel(TeamScanArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
   constexpr int SD = reduce_slot_doubles<N>();
-  __shared__ double fs[TEAM];
+  __shared__ double fs[2 * TEAM];
   __shared__ int is[TEAM];
   __shared__ double zero;
   const int lane = threadIdx.x;
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
   constexpr int SD = down_slot_doubles<N>();
   constexpr int VS = team::val_doubles<N>();
   constexpr int PM = N * N + N;
-  __shared__ double fs[TEAM];
+  __shared__ double fs[2 * TEAM];
   __shared__ int is[TEAM];
   __shared__ double zero;
   const int lane = threadIdx.x;
@@ -678,7 +678,7 @@ constexpr int prefix_slot_doubles() { return Rec<N>::SIZE + team::combine_scratc
 template <int N>
 __global__ void __launch_bounds__(TeamCfg<N>::TEAM) prefix_down_team_kernel(TeamPrefixArgs a) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
-  __shared__ double fs[TEAM];
+  __shared__ double fs[2 * TEAM];
   __shared__ int is[TEAM];
   const int lane = threadIdx.x;
   double* base = slot_base<N>(nullptr, prefix_slot_doubles<N>());

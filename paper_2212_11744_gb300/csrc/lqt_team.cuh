@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lqt_device.cuh"
 #include "lqt_internal.h"
 
 namespace lqt {
@@ -247,45 +248,72 @@ __device__ __forceinline__ void copy_rec(int lane, Rec<N> dst, Rec<N> src) {
 
 // ---------------------------------------------------------------------------
 // LU with partial pivoting on W (N x N), applied to R (N x Q); both in the
-// caller's buffers.  piv_scratch: 2 * TEAM doubles + TEAM ints of scratch.
+// caller's buffers.  Scratch: fscratch 2 * TEAM doubles, iscratch TEAM ints.
+// The pivot search compares magnitude keys (mag_key) on the integer pipes.
+// W = I + P in every use (P = C J or C S): a pivot no larger than 2^-40 times
+// its row's original scale max(1, max_j |W_ij|) sets the SINGULAR status bit
+// (pivot_too_small).
 // ---------------------------------------------------------------------------
 
 template <int N, int TEAM, int Q>
 __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* iscratch) {
+  static_assert(N <= TEAM, "one row scale per thread");
+  // original row scales: in a register of lane i (a warp), or in shared
+  // scratch (a larger team)
+  unsigned long long* rks = reinterpret_cast<unsigned long long*>(fscratch + TEAM);
+  unsigned long long rk = mag_key(1.0);
+  if (lane < N)
+    for (int j = 0; j < N; ++j) rk = umax64(rk, mag_key(W[lane * N + j]));
+  if constexpr (TEAM > 32) {
+    if (lane < N) rks[lane] = rk;
+    __syncthreads();
+  }
   for (int k = 0; k < N; ++k) {
     // arg max |W[i][k]|, i >= k (lowest index on ties)
-    double best = -1.0;
-    int bi = k;
+    unsigned long long best = 0;
+    int bi = N;
     for (int i = k + lane; i < N; i += TEAM) {
-      const double a = fabs(W[i * N + k]);
-      if (a > best) { best = a; bi = i; }
+      const unsigned long long a = mag_key(W[i * N + k]);
+      if (bi == N || a > best) { best = a; bi = i; }
     }
     if constexpr (TEAM <= 32) {
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        if (oi < N && (bi == N || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
       }
+      // exchange the row scales of rows k and bi with the rows
+      const unsigned long long rk_k = __shfl_sync(0xffffffffu, rk, k);
+      const unsigned long long rk_b = __shfl_sync(0xffffffffu, rk, bi);
+      if (lane == k) rk = rk_b;
+      else if (lane == bi) rk = rk_k;
+      if (lane == 0 && pivot_too_small(__longlong_as_double((long long)best), rk_b)) flag(kStatusSingular);
     } else {
-      fscratch[lane] = best;
+      unsigned long long* kb = reinterpret_cast<unsigned long long*>(fscratch);
+      kb[lane] = best;
       iscratch[lane] = bi;
       __syncthreads();
       for (int w = TEAM / 2; w > 0; w >>= 1) {
         if (lane < w) {
-          const double ob = fscratch[lane + w];
+          const unsigned long long ob = kb[lane + w];
           const int oi = iscratch[lane + w];
-          if (ob > fscratch[lane] || (ob == fscratch[lane] && oi < iscratch[lane])) {
-            fscratch[lane] = ob;
+          if (oi < N && (iscratch[lane] == N || ob > kb[lane] || (ob == kb[lane] && oi < iscratch[lane]))) {
+            kb[lane] = ob;
             iscratch[lane] = oi;
           }
         }
         __syncthreads();
       }
       bi = iscratch[0];
-      best = fscratch[0];
+      best = kb[0];
       __syncthreads();
+      if (lane == 0) {
+        const unsigned long long rk_b = rks[bi];
+        if (pivot_too_small(__longlong_as_double((long long)best), rk_b)) flag(kStatusSingular);
+        rks[bi] = rks[k];
+        rks[k] = rk_b;
+      }
     }
-    if (best == 0.0 && lane == 0) flag(kStatusSingular);
     if (bi != k) {
       for (int j = lane; j < N + Q; j += TEAM) {
         double* a = j < N ? &W[k * N + j] : &R[k * Q + (j - N)];

@@ -138,3 +138,27 @@ def test_grid_validation_on_host(lib):
         setattr(b, field, bad)
         assert L.lqt_grid_workspace_size(ct.byref(b), 0) == 0, field
         assert L.lqt_grid_block(ct.byref(b), d, d, 1 << 30, None) == _abi.LQT_EINVAL, field
+
+
+def test_noalloc_limits_match_the_header(lib):
+    """The largest T that lqt_scan_value_noalloc admits per state dimension,
+    as stated in include/lqt.h: the sizing function fits the static scratch
+    at that T and not at T + 1."""
+    import paper_2212_11744_gb300 as m
+    from paper_2212_11744_gb300 import _abi
+    src = open(os.path.join(ROOT, "include", "lqt.h")).read()
+    block = src[src.index("Allocation-free value scan"):src.index("lqt_scan_value_noalloc(const")]
+    block = re.sub(r"\s*\n\s*\*\s*", " ", block)
+    stated = {int(a): int(b.replace(" ", "")) for a, b in re.findall(r"n = (\d+): (\d[\d ]*\d|\d);", block)}
+    assert stated == {1: 7454719, 2: 2795391, 3: 44607, 4: 26877, 8: 7429, 16: 1951}, stated
+    assert "n = 64: none" in block
+    lim = _abi.LQT_STATIC_SCRATCH_BYTES
+    dims = {1: 1, 2: 1, 3: 2, 4: 2, 8: 4, 16: 8}
+    for n, Tmax in stated.items():
+        hp = m.HostProblem(W.general_time_varying(n, dims[n], n, T=4, K=1, seed=1), pinned=False)
+        hp.struct.T = Tmax
+        assert 0 < m.lqt_workspace_size(hp, m.LQT_WS_VALUE) <= lim, n
+        hp.struct.T = Tmax + 1
+        assert m.lqt_workspace_size(hp, m.LQT_WS_VALUE) > lim, n
+    hp = m.HostProblem(W.large_state_n64(T=1), pinned=False)
+    assert m.lqt_workspace_size(hp, m.LQT_WS_VALUE) > lim

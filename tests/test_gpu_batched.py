@@ -1,20 +1,14 @@
-"""Batched solves against the oracle, problem by problem."""
+"""Batched solves against the oracle, problem by problem.  Error measure as in
+test_gpu_parity.py (per boundary, relative, floored at 1e-8 of the largest)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads as W
+from tests.test_gpu_parity import TOL, relerr as rel
 
 pytestmark = pytest.mark.gpu
-
-TOL = 1e-9
-
-
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-12))
 
 
 def members(n, Ts, first_seed):

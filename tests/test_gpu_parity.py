@@ -1,9 +1,11 @@
 """GPU path (through the C ABI) against the oracle, element by element.
 
-Tolerance: relative 1e-9 per output tensor, measured as
-max |gpu - oracle| / max(max |oracle|, floor), the floor (1e-8 of the
-tensor's scale, at least 1e-12) keeping outputs that are identically ~0 from
-dividing by rounding noise.  Both sides use the same discretisation (K RK4
+Tolerance: relative 1e-9 per output tensor, measured boundary by boundary:
+max_i |gpu_i - oracle_i|_F / max(|oracle_i|_F, 1e-8 max_j |oracle_j|_F), with
+i the leading (boundary, sub-step or element) index, so a boundary whose S or
+v is small next to the largest one is held to the same relative bound; the
+floor keeps boundaries where an output is identically ~0 (v with a zero
+reference) from dividing by rounding noise.  Both sides use the same discretisation (K RK4
 steps of the element ODEs per sub-interval and the combination rule), so only
 rounding order differs: the GPU's chunked tree and factor form B = Lt Lt^T
 against the oracle's sequential fold and explicit B.
@@ -26,11 +28,28 @@ def lqt():
 
 
 def relerr(a, b):
+    """Per-boundary relative error: axis 0 indexes boundaries (each entry of a
+    1-D array is one boundary); each boundary's difference in the Frobenius
+    norm over its own entries, divided by that boundary's reference norm,
+    floored at 1e-8 of the largest reference norm (and at 1e-300)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    scale = np.abs(b).max() if b.size else 0.0
-    den = max(scale, 1e-12)
-    return float(np.abs(a - b).max() / den) if b.size else 0.0
+    assert a.shape == b.shape, (a.shape, b.shape)
+    if b.size == 0:
+        return 0.0
+    a = a.reshape(b.shape[0], -1) if b.ndim else a.reshape(1, 1)
+    b = b.reshape(b.shape[0], -1) if b.ndim else b.reshape(1, 1)
+    d = np.linalg.norm(a - b, axis=1)
+    r = np.linalg.norm(b, axis=1)
+    den = np.maximum(r, max(1e-8 * r.max(), 1e-300))
+    return float((d / den).max())
+
+
+def relerr_one(a, b):
+    """Relative error of one boundary's tensor in the Frobenius norm."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def to_np(t):
@@ -271,7 +290,7 @@ def test_large_state_full_size_local_checks():
     S, v, z, x, u = (to_np(out[k]) for k in ("S", "v", "zeta", "x", "u"))
     n, T = p.n, p.T
     term = oracle.build_elements(p, T, T + 1)
-    assert relerr(S[T], term["J"][0]) <= TOL and relerr(v[T], term["eta"][0]) <= TOL
+    assert relerr_one(S[T], term["J"][0]) <= TOL and relerr_one(v[T], term["eta"][0]) <= TOL
     L = p.L.values[0]
     U = p.U.values[0]
     for k in (0, 1, 4097, 31_000, T // 2 + 3, T - 2, T - 1):
@@ -279,12 +298,12 @@ def test_large_state_full_size_local_checks():
         val = {"A": np.zeros((n, n)), "b": np.zeros(n), "C": np.zeros((n, n)), "eta": v[k + 1], "J": S[k + 1],
                "zeta": z[k + 1]}
         c = oracle.combine(n, e, val)
-        assert relerr(S[k], c["J"]) <= TOL, k
-        assert relerr(v[k], c["eta"]) <= TOL, k
+        assert relerr_one(S[k], c["J"]) <= TOL, k
+        assert relerr_one(v[k], c["eta"]) <= TOL, k
         assert abs(z[k] - float(c["zeta"])) <= TOL * max(1.0, abs(float(c["zeta"]))), k
         xn = np.linalg.solve(np.eye(n) + e["C"] @ S[k + 1], e["A"] @ x[k] + e["b"] + e["C"] @ v[k + 1])
-        assert relerr(x[k + 1], xn) <= TOL, k
-        assert relerr(u[k], np.linalg.solve(U, L.T @ (v[k] - S[k] @ x[k]))) <= TOL, k
+        assert relerr_one(x[k + 1], xn) <= TOL, k
+        assert relerr_one(u[k], np.linalg.solve(U, L.T @ (v[k] - S[k] @ x[k]))) <= TOL, k
 
 
 @pytest.mark.slow
