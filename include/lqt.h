@@ -271,8 +271,10 @@ lqt_status lqt_densify(const lqt_problem *p, const double *S, const double *v, c
  * sampling mode of F, L, X, U, r (one gradient per sample); gXf [n][n],
  * grf [n]; gx0 [n].
  * The elements and the optimal-state maps are recomputed from the problem and
- * S, v; the RK4 stages of every sub-interval are recomputed from its start
- * (checkpointing per sub-interval).  Steps: state adjoint (a reverse linear
+ * S, v; the RK4 stage inputs that the discrete adjoint needs are recomputed
+ * in segments of 2280 sub-intervals just before that segment's reverse sweep,
+ * each from its sub-interval's fixed initial condition (A = I, the rest 0), so
+ * the workspace holds one segment's stage inputs, not T's.  Steps: state adjoint (a reverse linear
  * recurrence run as a forward affine scan), map adjoint, value adjoint (a
  * forward congruence scan Sigma_{k+1} = P_k Sigma_k P_k^T + D_{k+1} with the
  * homogeneous optimal-state maps P_k), element adjoint from the saddle point of

@@ -497,7 +497,8 @@ struct RK4AdjArgs {
   const double* r;      // may be null
   int32_t r_mode;
   const double* ebar;   // [T+1][fe]
-  double* ys;           // scratch [T][K][4][fe]: the stage inputs of every RK4 step
+  int64_t j0;           // this launch covers sub-intervals j0 .. j0 + T - 1 (T counts the segment)
+  double* ys;           // scratch [T][K][4][fe]: the segment's RK4 stage inputs, recomputed for it
   // per-sub-interval partials
   double *pF, *pB, *pX;  // [T][n^2]
   double* pr;            // [T][2K+1][n] (per stage sample) or null
@@ -714,7 +715,8 @@ __global__ void __launch_bounds__(32, 15) rk4_adjoint_warp_kernel(RK4AdjArgs a) 
   tmp.v2 = tmp.v1 + AN;
   double* qb = tmp.v2 + AN;          // [(2K+1) n]
   double* rhob = qb + (2 * 8 + 1) * AN;  // [2K+1]
-  for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
+  for (int64_t jj = blockIdx.x; jj < a.T; jj += gridDim.x) {
+    const int64_t j = a.j0 + jj;
     const double h = (a.t[j + 1] - a.t[j]) / K;
     const double* F = a.cf.F.ptr + sample_index(a.cf.F.mode, j, 0, K) * nn;
     const double* Lt = a.cf.Lt.ptr + sample_index(a.cf.Lt.mode, j, 0, K) * n * M;
@@ -731,9 +733,9 @@ __global__ void __launch_bounds__(32, 15) rk4_adjoint_warp_kernel(RK4AdjArgs a) 
     for (int e = lane; e < (2 * K + 1) * n; e += 32) qb[e] = 0.0;
     for (int e = lane; e <= 2 * K; e += 32) rhob[e] = 0.0;
     warp::sync();
-    // the four stage inputs of every RK4 step, written by this backward pass's
-    // element build (build_stages_kernel)
-    const double* ysj = a.ys + j * (int64_t)K * 4 * fs;
+    // the four stage inputs of every RK4 step, recomputed for this segment
+    // (build_stages_kernel) from the sub-interval's fixed initial condition
+    const double* ysj = a.ys + jj * (int64_t)K * 4 * fs;
     // adjoint
     const double* eb = a.ebar + j * fs;
     for (int e = lane; e < fs; e += 32) yb[e] = eb[e];
@@ -957,6 +959,14 @@ struct BackwardPlan {
       end;
 };
 
+// The RK4 adjoint runs over segments of sub-intervals, one full wave of its
+// kernel (152 SMs x 15 warps) each: the stage inputs it differentiates are
+// recomputed per segment from every sub-interval's fixed initial condition
+// (A = I, the rest 0; Theorem Backward_HJB_LQT's boundary, eq. abcej_boundary),
+// so their storage is one segment's, not T's.
+constexpr int64_t kAdjSegment = 152 * 15;
+static int64_t adjoint_segment(int64_t T) { return T < kAdjSegment ? T : kAdjSegment; }
+
 static BackwardPlan backward_plan(const lqt_problem& p, const Layout& L, size_t elem_bytes) {
   BackwardPlan b{};
   const size_t n = p.n, T = p.T, T1 = T + 1, K = p.K, m = p.m, fs = 3 * n * n + 2 * n + 1, m2 = (n + 1) * (n + 1);
@@ -978,7 +988,7 @@ static BackwardPlan backward_plan(const lqt_problem& p, const Layout& L, size_t 
     off = al(off + c);
   }
   b.ebar = off; off = al(off + T1 * fs * 8);
-  b.ys = off; off = al(off + T * K * 4 * fs * 8);
+  b.ys = off; off = al(off + (size_t)adjoint_segment(p.T) * K * 4 * fs * 8);
   b.pF = off; off = al(off + T * n * n * 8);
   b.pB = off; off = al(off + T * n * n * 8);
   b.pX = off; off = al(off + T * n * n * 8);
@@ -1009,8 +1019,9 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   cudaError_t e = launch_prepare_coefs(p, L, ws + b.coef, cf, st);
   if (e != cudaSuccess) return e;
   ElemPtrs el = carve_elements_at(p, ws + b.elems);
-  // the elements, and the RK4 stage inputs for the discrete adjoint (step 5)
-  e = launch_build_with_stages(p, L, cf, el, (double*)(ws + b.ys), st);
+  // the elements (the RK4 stage inputs for step 5 are recomputed there, segment
+  // by segment)
+  e = launch_build(p, L, cf, el, st);
   if (e != cudaSuccess) return e;
   double* maps = (double*)(ws + b.maps);
   e = launch_maps_from_values(p, el, S, v, maps, st);
@@ -1056,11 +1067,20 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   {
     const size_t smem = rk4w_smem_doubles() * sizeof(double);
     cudaFuncSetAttribute(rk4_adjoint_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // 14 KB of shared memory per warp (+1 KB reserved per CTA): 15 warps per SM
-    const int64_t grid = T < 152 * 15 ? T : 152 * 15;
-    rk4_adjoint_warp_kernel<<<(unsigned)grid, 32, smem, st>>>(ra);
+    // 14 KB of shared memory per warp (+1 KB reserved per CTA): 15 warps per
+    // SM, one segment per wave
+    const int64_t seg = adjoint_segment(T);
+    for (int64_t j0 = 0; j0 < T; j0 += seg) {
+      const int64_t cnt = T - j0 < seg ? T - j0 : seg;
+      e = launch_build_stages_range(p, L, cf, j0, cnt, ra.ys, st);
+      if (e != cudaSuccess) return e;
+      ra.j0 = j0;
+      ra.T = cnt;
+      rk4_adjoint_warp_kernel<<<(unsigned)cnt, 32, smem, st>>>(ra);
+      count_launch();
+    }
+    ra.T = T;
   }
-  count_launch();
   // 6. reductions
   auto reduce = [&](const double* part, int64_t rows, int size, int32_t mode, double* out) {
     if (!out) return;

@@ -112,7 +112,11 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
   const size_t T1 = (size_t)p->T + 1;
   switch (which) {
     case LQT_WS_BUILD: return L.coef_bytes + team_build_scratch_bytes(p->n);
-    case LQT_WS_VALUE: return scan_workspace_bytes(p->n, p->T, false);
+    case LQT_WS_VALUE: {
+      // a scan that fits one chunk needs no scratch; 0 is reserved for "invalid"
+      const size_t b = scan_workspace_bytes(p->n, p->T, false);
+      return b ? b : 256;
+    }
     case LQT_WS_TRAJ: return L.coef_bytes + scan_workspace_bytes(p->n, p->T, true);
     case LQT_WS_SOLVE:
       return L.coef_bytes + element_bytes(*p) + align_up(T1 * 8) + team_build_scratch_bytes(p->n) +
@@ -609,6 +613,7 @@ lqt_status lqt_get_status(void* stream, int32_t timeout_ms) {
   if (word & kStatusNonFinite) return LQT_ENONFINITE;
   if (word & kStatusSingular) return LQT_ESINGULAR;
   if (word & kStatusNonUniform) return LQT_EINVAL;
+  if (word & kStatusTimeout) return LQT_ETIMEOUT;
   return LQT_OK;
 }
 

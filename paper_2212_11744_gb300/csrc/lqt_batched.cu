@@ -7,8 +7,13 @@
 // A = b = C = 0 (Sec. IV-D, eq. LQT_final_initialisation): combining it with
 // whatever lies to its right gives its own J and eta exactly, so S and v never
 // leak across problems.  Only the state-free term zeta does leak, additively
-// (the combination adds zeta_1 + zeta_2 when z0 = 0), and is corrected after
-// the scan by subtracting the next problem's first zeta.  For the states, the
+// (the combination adds zeta_1 + zeta_2 when z0 = 0): the scan's running zeta
+// at a boundary of problem b carries the zeta of every later problem, and
+// removing that sum by a subtraction would leave its rounding (~1e-12 of a
+// batch's total) in values that are small near a problem's end.  So the
+// level-0 down-sweep of a batch writes each boundary's own share of zeta
+// (zeta_k - zeta_{k+1}, as the combination forms it, without a subtraction)
+// and a segmented suffix sum per problem adds them up.  For the states, the
 // map at each problem's last boundary is replaced by x -> x0 of the next
 // problem before the affine scan.  The controls and per-problem costs are
 // evaluated last, with each problem's own U^-1 L^T.
@@ -23,17 +28,65 @@ namespace lqt {
 
 static size_t bal(size_t x) { return (x + 255) & ~(size_t)255; }
 
-__global__ void zeta_first_kernel(BatchDev bd, const double* zeta, double* zfirst) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= bd.B) return;
-  zfirst[b] = zeta[bd.off[b]];
+// zeta_k = sum over j >= k of problem b of the shares left in zeta by the
+// level-0 down-sweep: one warp per problem, 32 boundaries at a time from the
+// problem's end (lane l holds boundary hi - l), a warp prefix sum over the
+// lanes plus the carry from the boundaries after them.
+__global__ void zeta_suffix_kernel(BatchDev bd, double* zeta) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= bd.B) return;  // uniform over the warp
+  const int64_t first = bd.off[w], last = bd.off[w + 1] - 1;
+  double carry = 0.0;
+  for (int64_t hi = last; hi >= first; hi -= 32) {
+    const int64_t k = hi - lane;
+    double x = (k >= first) ? zeta[k] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    x += carry;
+    if (k >= first) zeta[k] = x;
+    carry = __shfl_sync(0xffffffffu, x, 31);
+  }
 }
 
-__global__ void zeta_fix_kernel(BatchDev bd, double* zeta, const double* zfirst) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= bd.total) return;
+// The same with one warp per boundary (8 <= n <= 32): lane i < n forms row i of
+// e = v - S x (consecutive lanes read consecutive entries of S's rows as the
+// loop runs over the columns), then lane q < m forms u_q from e by shuffles;
+// one thread per boundary would read S_g with a 2 KB stride between lanes.
+__global__ void controls_cost_warp_kernel(BatchDev bd, const double* S, const double* v, const double* zeta,
+                                          const double* x, double* u, double* cost) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= bd.total) return;  // uniform over the warp
+  const int n = bd.n, m = bd.m;
   const int32_t b = batch_find(bd.off, bd.B, g);
-  if (b + 1 < bd.B) zeta[g] -= zfirst[b + 1];
+  const BatchProb& P = bd.probs[b];
+  const double* Sg = S + g * n * n;
+  const double* vg = v + g * n;
+  const double* xg = x + g * n;
+  double sx = 0.0;
+  if (lane < n)
+    for (int l = 0; l < n; ++l) sx = fma(Sg[lane * n + l], xg[l], sx);
+  const double xi = lane < n ? xg[lane] : 0.0;
+  const double vi = lane < n ? vg[lane] : 0.0;
+  const double e = vi - sx;
+  if (u) {
+    const double* Ku = P.cf.Ku;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double ei = __shfl_sync(0xffffffffu, e, i);
+      if (lane < m) s = fma(Ku[lane * n + i], ei, s);
+    }
+    if (lane < m) u[g * m + lane] = s;
+  }
+  if (cost && g == P.off) {
+    double c = lane < n ? xi * fma(0.5, sx, -vi) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cost[b] = zeta[g] + c;
+  }
 }
 
 // u_g = U_b^-1 L_b^T (v_g - S_g x_g); cost_b at the first boundary of b.
@@ -74,7 +127,7 @@ __global__ void controls_cost_kernel(BatchDev bd, const double* S, const double*
 struct BatchLayout {
   int32_t B, n, m, K, M;
   int64_t total, total_qr;
-  size_t off_probs, off_off, off_offqr, off_Lt, off_Ku, off_qr, off_el, off_team, off_zf, off_inv, off_scan, bytes;
+  size_t off_probs, off_off, off_offqr, off_Lt, off_Ku, off_qr, off_el, off_team, off_inv, off_scan, bytes;
 };
 
 static int32_t batch_factor_width(int n, int m) {
@@ -123,7 +176,6 @@ static lqt_status batch_validate(const lqt_batch* bt, BatchLayout& L) {
   const size_t T1 = (size_t)total;
   off = bal(off + bal(T1 * n * n * 8) * 3 + bal(T1 * n * 8) * 2 + bal(T1 * 8));
   L.off_team = off; off = bal(off + team_build_scratch_bytes(n));
-  L.off_zf = off; off = bal(off + (size_t)L.B * 8);
   // per-problem tables of the time-invariant build (when it supports n)
   L.off_inv = off;
   if (invariant_supported(n, L.M)) off = bal(off + (size_t)L.B * invariant_table_bytes(n, L.M, L.K));
@@ -259,11 +311,12 @@ lqt_status lqt_solve_batched(const lqt_batch* bt, const lqt_tuning* tune, double
     e = concat_scan(L.n, L.total - 1, el, S, v, zeta, bt->x0[0], x, patch, w + L.off_scan, st);
   set_scan_chunk(0);
   if (e != cudaSuccess) return LQT_ECUDA;
-  double* zf = (double*)(w + L.off_zf);
-  zeta_first_kernel<<<(unsigned)((L.B + 127) / 128), 128, 0, st>>>(bd, zeta, zf);
-  zeta_fix_kernel<<<(unsigned)((L.total + 127) / 128), 128, 0, st>>>(bd, zeta, zf);
-  controls_cost_kernel<<<(unsigned)((L.total + 127) / 128), 128, 0, st>>>(bd, S, v, zeta, x, u, cost);
-  count_launch(3);
+  zeta_suffix_kernel<<<(unsigned)((L.B + 3) / 4), 128, 0, st>>>(bd, zeta);
+  if (L.n >= 8 && L.n <= 32)
+    controls_cost_warp_kernel<<<(unsigned)((L.total + 3) / 4), 128, 0, st>>>(bd, S, v, zeta, x, u, cost);
+  else
+    controls_cost_kernel<<<(unsigned)((L.total + 127) / 128), 128, 0, st>>>(bd, S, v, zeta, x, u, cost);
+  count_launch(2);
   return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
 }
 

@@ -563,16 +563,18 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
   store_public<N>(a.out, j, y);
 }
 
-// The same, also writing every RK4 stage input of sub-interval j to
-// stages + j K 4 (3N^2 + 2N + 1) (full layout, step i = K-1 .. 0 at slot i).
+// The same for sub-intervals j0 .. j0 + T - 1 (a.T counts the range), writing
+// every RK4 stage input of sub-interval j0 + i to stages + i K 4 (3N^2 + 2N + 1)
+// (full layout, step i = K-1 .. 0 at slot i); the element itself is stored
+// only when a.out.A is not null.
 template <int N, int M>
-__global__ void __launch_bounds__(128) build_stages_kernel(BuildArgs a, double* stages) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.T) return;
+__global__ void __launch_bounds__(128) build_stages_kernel(BuildArgs a, int64_t j0, double* stages) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.T) return;
   constexpr int FS = 3 * N * N + 2 * N + 1;
   Elem<N> y;
-  build_one<N, M, true>(a.cf, a.t, j, a.K, y, stages + j * (int64_t)a.K * 4 * FS);
-  store_public<N>(a.out, j, y);
+  build_one<N, M, true>(a.cf, a.t, j0 + i, a.K, y, stages + i * (int64_t)a.K * 4 * FS);
+  if (a.out.A) store_public<N>(a.out, j0 + i, y);
 }
 
 // Terminal element a_T: A = b = C = 0, J = Hf^T Xf Hf, eta = Hf^T Xf rf,
@@ -778,45 +780,44 @@ cudaError_t batch_build(const BatchDev& bd, const ElemPtrs& el, char* team_scrat
 }
 
 template <int N, int M>
-static void launch_build_nm(const BuildArgs& a, cudaStream_t st, double* stages) {
+static void launch_build_nm(const BuildArgs& a, cudaStream_t st, double* stages, int64_t j0) {
   const int threads = 128;
   const int64_t blocks = (a.T + threads - 1) / threads;
   if (stages)
-    build_stages_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a, stages);
+    build_stages_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a, j0, stages);
   else
     build_kernel<N, M><<<(unsigned)blocks, threads, 0, st>>>(a);
   count_launch();
 }
 
 template <int N>
-static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st, double* stages = nullptr) {
+static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st, double* stages = nullptr,
+                                  int64_t j0 = 0) {
   switch (M) {
-    case 1: launch_build_nm<N, 1>(a, st, stages); break;
-    case 2: if constexpr (N >= 2) { launch_build_nm<N, 2>(a, st, stages); break; } else return cudaErrorInvalidValue;
-    case 4: if constexpr (N >= 3) { launch_build_nm<N, 4>(a, st, stages); break; } else return cudaErrorInvalidValue;
-    case 8: if constexpr (N >= 8) { launch_build_nm<N, 8>(a, st, stages); break; } else return cudaErrorInvalidValue;
+    case 1: launch_build_nm<N, 1>(a, st, stages, j0); break;
+    case 2: if constexpr (N >= 2) { launch_build_nm<N, 2>(a, st, stages, j0); break; } else return cudaErrorInvalidValue;
+    case 4: if constexpr (N >= 3) { launch_build_nm<N, 4>(a, st, stages, j0); break; } else return cudaErrorInvalidValue;
+    case 8: if constexpr (N >= 8) { launch_build_nm<N, 8>(a, st, stages, j0); break; } else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   return cudaSuccess;
 }
 
-// Elements 0..T (terminal included) of p, n <= 8, with every RK4 stage input
-// of sub-interval j at stages + j K 4 (3n^2 + 2n + 1) (full layout).
-cudaError_t launch_build_with_stages(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
-                                     double* stages, cudaStream_t st) {
-  BuildArgs a;
-  a.T = p.T; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
-  cudaError_t e;
+// The RK4 stage inputs of sub-intervals j0 .. j0 + cnt - 1 of p (n <= 8), the
+// stages of sub-interval j0 + i at stages + i K 4 (3n^2 + 2n + 1) (full
+// layout); the elements themselves are not stored.
+cudaError_t launch_build_stages_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, int64_t j0,
+                                      int64_t cnt, double* stages, cudaStream_t st) {
+  BuildArgs a{};
+  a.T = cnt; a.K = p.K; a.t = p.t; a.cf = cf;
   switch (p.n) {
-    case 1: e = launch_build_n<1>(a, lay.M, st, stages); break;
-    case 2: e = launch_build_n<2>(a, lay.M, st, stages); break;
-    case 3: e = launch_build_n<3>(a, lay.M, st, stages); break;
-    case 4: e = launch_build_n<4>(a, lay.M, st, stages); break;
-    case 8: e = launch_build_n<8>(a, lay.M, st, stages); break;
+    case 1: return launch_build_n<1>(a, lay.M, st, stages, j0);
+    case 2: return launch_build_n<2>(a, lay.M, st, stages, j0);
+    case 3: return launch_build_n<3>(a, lay.M, st, stages, j0);
+    case 4: return launch_build_n<4>(a, lay.M, st, stages, j0);
+    case 8: return launch_build_n<8>(a, lay.M, st, stages, j0);
     default: return cudaErrorInvalidValue;
   }
-  if (e != cudaSuccess) return e;
-  return launch_terminal_element(p, out, st);
 }
 
 // Elements 0..T-1 of p alone (no terminal element), n <= 8.

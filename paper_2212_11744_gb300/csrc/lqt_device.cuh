@@ -515,7 +515,7 @@ __device__ __forceinline__ void combine(const Elem<N>& e1, const Elem<N>& e2, El
 //          z0 = alpha, l0 = S2 z0 - v2
 template <int N, typename G = double>
 __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V, Val<N>& out, double (&Psi)[N * N],
-                                              double (&alpha)[N]) {
+                                              double (&alpha)[N], double* zeta_inc = nullptr) {
   constexpr int Q = N + 1;
   double W[N * N];
   double R[N * Q];
@@ -545,7 +545,9 @@ __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V,
     alpha[i] = R[i * Q + N];
   }
   G Sz[N], l0[N];
-  G zeta = gf<G>(e.zeta) + gf<G>(V.zeta);
+  // the element's own share of zeta (its zeta and the saddle-point terms);
+  // the carry's zeta is added to it in FP64
+  G zeta = gf<G>(e.zeta);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     G s = 0;
@@ -598,7 +600,8 @@ __device__ __forceinline__ void combine_value(const Elem<N>& e, const Val<N>& V,
       for (int l = 0; l < N; ++l) s = fma(gf<G>(Psi[l * N + i]), T1[l * N + j], s);
       out.S[sidx<N>(i, j)] = (double)s;
     }
-  out.zeta = (double)zeta;
+  out.zeta = (double)zeta + V.zeta;
+  if (zeta_inc) *zeta_inc = (double)zeta;
 }
 
 // ---------------------------------------------------------------------------

@@ -14,6 +14,7 @@ namespace lqt {
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusSingular = 2u;
 constexpr unsigned kStatusNonUniform = 4u;  // a time-invariant build met sub-intervals of different lengths
+constexpr unsigned kStatusTimeout = 8u;     // a kernel's bounded wait (a TMA copy) gave up
 
 extern __device__ unsigned g_status_word;
 
@@ -100,8 +101,8 @@ cudaError_t launch_prepare_into(const lqt_problem& p, const Layout& lay, double*
 Coefs coefs_view(const lqt_problem& p, const Layout& lay, double* Lt, double* Q, double* qr, double* Ku);
 cudaError_t launch_build_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                                cudaStream_t st);
-cudaError_t launch_build_with_stages(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
-                                     double* stages, cudaStream_t st);
+cudaError_t launch_build_stages_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, int64_t j0,
+                                      int64_t cnt, double* stages, cudaStream_t st);
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                          cudaStream_t s, double* team_scratch = nullptr);
 // n = 16, 64 (team kernels, lqt_team.cu)

@@ -95,6 +95,10 @@ struct DownOut {
   double* maps;       // [T][N*N + N]
   double* composite;  // [chunks-1][N*N + N]
   int64_t T;
+  // batches: zeta[k] receives the element's own share of zeta (zeta_k minus
+  // zeta_{k+1}, formed without that subtraction); a segmented suffix sum per
+  // problem then gives zeta without the later problems' zeta leaking in
+  int zeta_inc;
 };
 
 template <int N>
@@ -141,8 +145,10 @@ __global__ void __launch_bounds__(128) down_values_kernel(Src src, int64_t cnt, 
   double Psi[N * N], alpha[N];
   for (int64_t k = last; k >= first; --k) {
     src.load(k, e);
-    combine_value<N, GT>(e, carry, nv, Psi, alpha);
+    double zinc;
+    combine_value<N, GT>(e, carry, nv, Psi, alpha, &zinc);
     store_val_public<N>(o, k, nv);
+    if (o.zeta_inc && o.zeta) o.zeta[k] = zinc;
     if (o.maps != nullptr && k < o.T) {
       double* mp = o.maps + k * PM;
 #pragma unroll
@@ -688,7 +694,7 @@ static cudaError_t concat_n(int64_t Tcat, const ElemPtrs& el, double* S, double*
   const ScanPlan pl = make_plan<N>(Tcat, true);
   double* maps0 = (double*)(ws + pl.off_maps);
   DownOut o{};
-  o.S = S; o.v = v; o.zeta = zeta; o.T = Tcat; o.maps = maps0; o.composite = nullptr;
+  o.S = S; o.v = v; o.zeta = zeta; o.T = Tcat; o.maps = maps0; o.composite = nullptr; o.zeta_inc = 1;
   value_scan<N>(pl, el, o, ws, st);
   launch_boundary_patch(N, maps0, patch, st);
   if (pl.tlev > 0) {

@@ -9,6 +9,7 @@
 #include "lqt_device.cuh"
 #include "lqt_internal.h"
 #include "lqt_team.cuh"
+#include "lqt_warp16.cuh"
 
 namespace lqt {
 
@@ -240,6 +241,7 @@ struct TeamScanArgs {
   double *maps, *comp;   // level-0 maps [T][N^2+N] and chunk composites
   int64_t T;
   double* gscratch;
+  int zeta_inc;          // level 0 of a batch: zeta[k] receives the element's own share (see DownOut)
 };
 
 template <int N>
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
   __shared__ double fs[2 * TEAM];
   __shared__ int is[TEAM];
   __shared__ double zero;
+  __shared__ double zinc;
   const int lane = threadIdx.x;
   if (lane == 0) zero = 0.0;
   double* base = slot_base<N>(a.gscratch, SD);
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
       }
     team::sync<TEAM>();
     for (int64_t k = last; k >= first; --k) {
-      team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is);
+      team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is, &zinc);
       if (Level0) {
         bool ok = true;
         for (int e = lane; e < VS; e += TEAM) {
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
           ok = ok && isfinite(x);
           if (e < N * N) a.S[k * N * N + e] = x;
           else if (e < N * N + N) a.v[k * N + e - N * N] = x;
-          else if (a.zeta) a.zeta[k] = x;
+          else if (a.zeta) a.zeta[k] = a.zeta_inc ? zinc : x;
         }
         if (!ok) flag(kStatusNonFinite);
         if (a.maps != nullptr && k < a.T) {
@@ -340,6 +343,120 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
     if (Level0 && a.comp != nullptr && last + 1 <= a.T)
       for (int e = lane; e < PM; e += TEAM) a.comp[g * PM + e] = e < N * N ? P[e] : pv[e - N * N];
     team::sync<TEAM>();
+  }
+}
+
+// n = 16: one warp per combination with the register Gauss-Jordan solve and
+// TMA-staged element operands (lqt_warp16.cuh).  Same levels, groups and
+// records as the kernels above.
+constexpr int kW16ReduceSmem = 2 * w16::kRecPad + w16::kScratch;
+constexpr int kW16DownSmem = 2 * 276 + w16::kRecPad + w16::kVScratch + 256 + 16 + 256 + 16 + 16 * w16::kWld;
+
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+template <typename GT>
+__global__ void __launch_bounds__(32, 10) reduce_w16_kernel(TeamScanArgs a, int bulk) {
+  extern __shared__ __align__(16) double w16_smem[];
+  __shared__ unsigned long long bar;
+  __shared__ double zero;
+  const int lane = threadIdx.x;
+  double* bufA = w16_smem;
+  double* bufB = bufA + w16::kRecPad;
+  double* scr = bufB + w16::kRecPad;
+  if (lane == 0) {
+    zero = 0.0;
+    w16::mbar_init(&bar, 1);
+  }
+  __syncwarp();
+  unsigned phase = 0;
+  const w16::ElemSrc src{a.el, a.src, bulk != 0};
+  const int64_t groups = tdiv(a.cnt, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.cnt ? first + a.G : a.cnt) - 1;
+    double* acc = bufA;
+    double* nxt = bufB;
+    w16::stage(lane, src, last, acc, &bar, phase, &zero);
+    for (int64_t k = last - 1; k >= first; --k) {
+      w16::stage(lane, src, k, nxt, &bar, phase, &zero);
+      w16::combine<GT>(lane, nxt, acc, scr);
+      double* t = acc;
+      acc = nxt;
+      nxt = t;
+    }
+    double* out = a.agg + g * w16::kRec;
+    for (int e = lane; e < w16::kRec; e += 32) out[e] = acc[e];
+    __syncwarp();
+  }
+}
+
+template <bool Level0, typename GT>
+__global__ void __launch_bounds__(32, 10) down_w16_kernel(TeamScanArgs a, int bulk) {
+  extern __shared__ __align__(16) double w16_smem[];
+  __shared__ unsigned long long bar;
+  __shared__ double zero;
+  __shared__ double zinc;
+  constexpr int VS = w16::kVal;
+  const int lane = threadIdx.x;
+  double* c0 = w16_smem;
+  double* c1 = c0 + 276;
+  double* E = c1 + 276;
+  double* scr = E + w16::kRecPad;
+  double* Psi = scr + w16::kVScratch;
+  double* alpha = Psi + 256;
+  double* P = alpha + 16;
+  double* pv = P + 256;
+  double* Tm = pv + 16;
+  if (lane == 0) {
+    zero = 0.0;
+    w16::mbar_init(&bar, 1);
+  }
+  __syncwarp();
+  unsigned phase = 0;
+  const w16::ElemSrc src{a.el, a.src, bulk != 0};
+  const int64_t groups = tdiv(a.cnt, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.cnt ? first + a.G : a.cnt) - 1;
+    double* carry = c0;
+    double* nv = c1;
+    for (int e = lane; e < VS; e += 32)
+      carry[e] = (a.above != nullptr && g + 1 < a.cnt_above) ? a.above[(g + 1) * VS + e] : 0.0;
+    if (Level0) {
+      for (int e = lane; e < 256; e += 32) P[e] = ((e >> 4) == (e & 15)) ? 1.0 : 0.0;
+      if (lane < 16) pv[lane] = 0.0;
+    }
+    __syncwarp();
+    for (int64_t k = last; k >= first; --k) {
+      w16::stage(lane, src, k, E, &bar, phase, &zero);
+      w16::combine_value<GT>(lane, E, carry, nv, Psi, alpha, scr, &zinc);
+      if (Level0) {
+        bool ok = true;
+        for (int e = lane; e < VS; e += 32) {
+          const double x = nv[e];
+          ok = ok && finite_bits(x);
+          if (e < 256) a.S[k * 256 + e] = x;
+          else if (e < 272) a.v[k * 16 + e - 256] = x;
+          else if (a.zeta) a.zeta[k] = a.zeta_inc ? zinc : x;
+        }
+        if (!ok) flag(kStatusNonFinite);
+        if (a.maps != nullptr && k < a.T) {
+          for (int e = lane; e < 272; e += 32) a.maps[k * 272 + e] = e < 256 ? Psi[e] : alpha[e - 256];
+          w16::compose_right(lane, P, pv, Psi, alpha, Tm);
+        }
+      } else {
+        for (int e = lane; e < VS; e += 32) a.vals[k * VS + e] = nv[e];
+      }
+      __syncwarp();
+      double* t = carry;
+      carry = nv;
+      nv = t;
+    }
+    if (Level0 && a.comp != nullptr && last + 1 <= a.T)
+      for (int e = lane; e < 272; e += 32) a.comp[g * 272 + e] = e < 256 ? P[e] : pv[e - 256];
+    __syncwarp();
   }
 }
 
@@ -553,6 +670,37 @@ static void team_launch(Kern k, int64_t work, size_t smem_doubles, const Args& a
   count_launch();
 }
 
+// Elements of the public layout can be staged by TMA when every array is
+// 16-byte aligned.
+static int bulk_ok(const ElemPtrs& el) {
+  const uintptr_t m = (uintptr_t)el.A | (uintptr_t)el.b | (uintptr_t)el.C | (uintptr_t)el.eta | (uintptr_t)el.J;
+  return (m & 15) == 0 ? 1 : 0;
+}
+
+template <int N, typename GT>
+static void launch_reduce(const TeamScanArgs& a, int64_t groups, cudaStream_t st) {
+  if constexpr (N == 16) {
+    reduce_w16_kernel<GT><<<(unsigned)(groups < TeamCfg<16>::SCAN_SLOTS ? (groups > 0 ? groups : 1)
+                                                                         : TeamCfg<16>::SCAN_SLOTS),
+                            32, kW16ReduceSmem * sizeof(double), st>>>(a, a.src == nullptr ? bulk_ok(a.el) : 0);
+    count_launch();
+  } else {
+    team_launch<N>(reduce_team_kernel<N, GT>, groups, reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+  }
+}
+
+template <int N, bool Level0, typename GT>
+static void launch_down(const TeamScanArgs& a, int64_t groups, cudaStream_t st) {
+  if constexpr (N == 16) {
+    down_w16_kernel<Level0, GT><<<(unsigned)(groups < TeamCfg<16>::SCAN_SLOTS ? (groups > 0 ? groups : 1)
+                                                                              : TeamCfg<16>::SCAN_SLOTS),
+                                  32, kW16DownSmem * sizeof(double), st>>>(a, a.src == nullptr ? bulk_ok(a.el) : 0);
+    count_launch();
+  } else {
+    team_launch<N>(down_team_kernel<N, Level0, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+  }
+}
+
 template <int N, int M>
 static cudaError_t team_build_nm(const lqt_problem& p, const Coefs& cf, const ElemPtrs& out, double* gscratch,
                                  cudaStream_t st) {
@@ -576,7 +724,7 @@ static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemP
       TeamScanArgs a{};
       a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
       a.agg = (double*)(ws + pl.off_agg[l]); a.T = p.T; a.gscratch = gs;
-      team_launch<N>(reduce_team_kernel<N, GT>, pl.cnt[l], reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+      launch_reduce<N, GT>(a, pl.cnt[l], st);
       c = pl.cnt[l];
       G = 2;
     }
@@ -595,10 +743,10 @@ static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemP
         a.S = S; a.v = v; a.zeta = zeta;
         a.maps = do_traj ? maps0 : nullptr;
         a.comp = do_traj ? comp1 : nullptr;
-        team_launch<N>(down_team_kernel<N, true, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+        launch_down<N, true, GT>(a, groups, st);
       } else {
         a.vals = (double*)(ws + pl.off_val[l - 1]);
-        team_launch<N>(down_team_kernel<N, false, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+        launch_down<N, false, GT>(a, groups, st);
       }
     }
   } else if (do_traj) {
@@ -830,7 +978,7 @@ static cudaError_t team_concat(int64_t Tcat, const ElemPtrs& el, double* S, doub
     TeamScanArgs a{};
     a.el = el; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
     a.agg = (double*)(ws + pl.off_agg[l]); a.T = Tcat; a.gscratch = gs;
-    team_launch<N>(reduce_team_kernel<N>, pl.cnt[l], reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+    launch_reduce<N, double>(a, pl.cnt[l], st);
     c = pl.cnt[l];
     G = 2;
   }
@@ -846,11 +994,11 @@ static cudaError_t team_concat(int64_t Tcat, const ElemPtrs& el, double* S, doub
     a.gscratch = gs;
     const int64_t groups = tdiv(a.cnt, a.G);
     if (l == 0) {
-      a.S = S; a.v = v; a.zeta = zeta; a.maps = maps0; a.comp = nullptr;
-      team_launch<N>(down_team_kernel<N, true>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+      a.S = S; a.v = v; a.zeta = zeta; a.maps = maps0; a.comp = nullptr; a.zeta_inc = 1;
+      launch_down<N, true, double>(a, groups, st);
     } else {
       a.vals = (double*)(ws + pl.off_val[l - 1]);
-      team_launch<N>(down_team_kernel<N, false>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
+      launch_down<N, false, double>(a, groups, st);
     }
   }
   launch_boundary_patch(N, maps0, patch, st);

@@ -513,7 +513,7 @@ __host__ __device__ constexpr int val_doubles() {
 
 template <int N, int TEAM, typename G = double>
 __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, double* Psi, double* alpha,
-                              double* scr, double* fs, int* is) {
+                              double* scr, double* fs, int* is, double* zeta_inc = nullptr) {
   constexpr int Q = N + 1;
   const double* S2 = V;
   const double* v2 = V + N * N;
@@ -577,7 +577,11 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
       zt = fma(alpha[i], fma(0.5, Sz[i], -v2[i]), zt);
     }
     const double z = team_sum<TEAM>(lane, zt, fs);
-    if (lane == 0) out[N * N + N] = *e.zeta() + zeta2 + z;
+    if (lane == 0) {
+      const double inc = *e.zeta() + z;  // the element's own share; the carry's zeta added after
+      out[N * N + N] = inc + zeta2;
+      if (zeta_inc) *zeta_inc = inc;
+    }
   }
   sync<TEAM>();
   for (int t = lane; t < N * N; t += TEAM) {

@@ -117,3 +117,33 @@ def test_full_batch_sampled_problems_against_oracle():
             got = bt.problem_slice(out, i)
             for k in ("S", "v", "zeta", "x", "u"):
                 assert rel(got[k].cpu().numpy(), ref[k]) <= TOL, (n, idx[i], p.T, k)
+
+
+def test_n16_batch_of_40_sampled_against_oracle():
+    """The first 40 problems of state dimension 16 in the 4096-problem batch
+    (about 1.7e5 sub-intervals: enough chunks to fill every warp slot of the
+    warp-per-combination scan), solved as one batch; the shortest and the
+    longest problem checked against the oracle."""
+    from paper_2212_11744_gb300.batch import Batch
+    probs = []
+    b = 0
+    while len(probs) < 40:
+        p = W.batched_member(b)
+        if p.n == 16:
+            probs.append(p)
+        b += 1
+    bt = Batch(probs)
+    out = bt.solve()
+    torch.cuda.synchronize()
+    assert lqt_status() == 0
+    Ts = [p.T for p in probs]
+    for i in {int(np.argmin(Ts)), int(np.argmax(Ts))}:
+        ref = oracle.solve(probs[i])
+        got = bt.problem_slice(out, i)
+        for k in ("S", "v", "zeta", "x", "u"):
+            assert rel(got[k].cpu().numpy(), ref[k]) <= TOL, (i, probs[i].T, k)
+
+
+def lqt_status():
+    import paper_2212_11744_gb300 as lqt
+    return lqt.lqt_get_status()

@@ -111,3 +111,20 @@ def test_mixed_large_state_full_size_against_oracle():
         assert rel(v[k], c["eta"]) <= 1e-4, k
         assert abs(z[k] - float(c["zeta"])) <= 1e-4 * abs(float(c["zeta"])), k
         assert rel(got["u"][k], np.linalg.solve(U, L.T @ (v[k] - S[k] @ got["x"][k]))) <= 1e-4, k
+
+
+def test_mixed_n64_T4096_against_fp64_path():
+    """The n = 64 workload at T = 4096 (every CTA slot of the CTA-per-element
+    scan busy): the FP32-product path against the FP64 path (itself checked
+    against the oracle at T = 64, 129 and at sampled boundaries of T = 2^16)
+    within the 1e-4 target; the mixed solve runs first."""
+    import paper_2212_11744_gb300 as lqt
+    p = W.large_state_n64(T=4096)
+    dp = lqt.DeviceProblem(p)
+    mixed = lqt.lqt_solve_mixed(dp)
+    torch.cuda.synchronize()
+    full = lqt.lqt_solve(dp)
+    torch.cuda.synchronize()
+    assert lqt.lqt_get_status() == 0
+    errs = {k: rel(mixed[k].cpu().numpy(), full[k].cpu().numpy()) for k in ("S", "v", "zeta", "x", "u")}
+    assert max(errs.values()) <= 1e-4, errs
