@@ -167,9 +167,12 @@ lqt_status lqt_solve(const lqt_problem *p, const double *x0, double *S, double *
  * the element build (RK4 of the conditional HJB ODEs) and the LU solves of
  * I + C J inside every combination stay FP64, while the matrix products of the
  * combinations in both scans (forming I + C J, and every product after the
- * solve) run in FP32 with FP32 accumulation.  Results are FP64 arrays; their
- * error against the FP64 path is a property of the problem (reported by the
- * benchmark and tested against a 1e-4 relative target). */
+ * solve) run in FP32 with FP32 accumulation: on the CUDA cores for n <= 16,
+ * and for n = 64 on the tensor core (tcgen05.mma kind::tf32 with each FP32
+ * operand split into three TF32 pieces, so that the products keep FP32
+ * accuracy).  Results are FP64 arrays; their error against the FP64 path is a
+ * property of the problem (reported by the benchmark and tested against a
+ * 1e-4 relative target). */
 lqt_status lqt_solve_mixed(const lqt_problem *p, const double *x0, double *S, double *v, double *zeta, double *x,
                            double *u, double *cost, void *ws, size_t ws_bytes, void *stream);
 

@@ -228,6 +228,10 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::BUILD_MIN)
 // stage (b): reduce / down-sweep of the value scan
 // ---------------------------------------------------------------------------
 
+// The FP32 products of the n = 64 combinations run on the tensor core.
+template <int N, typename GT>
+constexpr bool kTensorProducts = (N == 64 && std::is_same<GT, float>::value);
+
 struct TeamScanArgs {
   ElemPtrs el;           // level-0 elements (public layout)
   const double* src;     // packed elements of the level (levels >= 1), or null at level 0
@@ -263,6 +267,15 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
   double* bufA = base;
   double* bufB = bufA + Rec<N>::SIZE;
   double* scr = bufB + Rec<N>::SIZE;
+  tc::Ctx* tcx = nullptr;
+  tc::Ctx tc_ctx;
+  if constexpr (kTensorProducts<N, GT>) {
+    extern __shared__ __align__(16) unsigned char tc_smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ unsigned long long tc_bar;
+    tc::init(tc_ctx, &tmem_slot, &tc_bar, tc_smem);
+    tcx = &tc_ctx;
+  }
   team::sync<TEAM>();
   const int64_t groups = tdiv(a.cnt, a.G);
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -271,13 +284,14 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
     Rec<N> acc = Rec<N>::packed(bufA), nxt = Rec<N>::packed(bufB);
     team::copy_rec<N, TEAM>(lane, acc, level_elem<N>(a, last, &zero));
     for (int64_t k = last - 1; k >= first; --k) {
-      team::combine<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is);
+      team::combine<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is, tcx);
       const Rec<N> t = acc;
       acc = nxt;
       nxt = t;
     }
     team::copy_rec<N, TEAM>(lane, Rec<N>::packed(a.agg + g * Rec<N>::SIZE), acc);
   }
+  if constexpr (kTensorProducts<N, GT>) tc::release(tc_ctx);
 }
 
 template <int N, bool Level0, typename GT = double>
@@ -301,6 +315,15 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
   double* P = alpha + N;
   double* pv = P + N * N;
   double* Tm = pv + N;
+  tc::Ctx* tcx = nullptr;
+  tc::Ctx tc_ctx;
+  if constexpr (kTensorProducts<N, GT>) {
+    extern __shared__ __align__(16) unsigned char tc_smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ unsigned long long tc_bar;
+    tc::init(tc_ctx, &tmem_slot, &tc_bar, tc_smem);
+    tcx = &tc_ctx;
+  }
   team::sync<TEAM>();
   const int64_t groups = tdiv(a.cnt, a.G);
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -317,7 +340,8 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
       }
     team::sync<TEAM>();
     for (int64_t k = last; k >= first; --k) {
-      team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is, &zinc);
+      team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is, &zinc,
+                                       tcx);
       if (Level0) {
         bool ok = true;
         for (int e = lane; e < VS; e += TEAM) {
@@ -344,6 +368,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
       for (int e = lane; e < PM; e += TEAM) a.comp[g * PM + e] = e < N * N ? P[e] : pv[e - N * N];
     team::sync<TEAM>();
   }
+  if constexpr (kTensorProducts<N, GT>) tc::release(tc_ctx);
 }
 
 // n = 16: one warp per combination with the register Gauss-Jordan solve and
@@ -684,6 +709,10 @@ static void launch_reduce(const TeamScanArgs& a, int64_t groups, cudaStream_t st
                                                                          : TeamCfg<16>::SCAN_SLOTS),
                             32, kW16ReduceSmem * sizeof(double), st>>>(a, a.src == nullptr ? bulk_ok(a.el) : 0);
     count_launch();
+  } else if constexpr (kTensorProducts<N, GT>) {
+    cudaFuncSetAttribute(reduce_team_kernel<N, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes);
+    reduce_team_kernel<N, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, tc::kSmemBytes, st>>>(a);
+    count_launch();
   } else {
     team_launch<N>(reduce_team_kernel<N, GT>, groups, reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
   }
@@ -695,6 +724,12 @@ static void launch_down(const TeamScanArgs& a, int64_t groups, cudaStream_t st) 
     down_w16_kernel<Level0, GT><<<(unsigned)(groups < TeamCfg<16>::SCAN_SLOTS ? (groups > 0 ? groups : 1)
                                                                               : TeamCfg<16>::SCAN_SLOTS),
                                   32, kW16DownSmem * sizeof(double), st>>>(a, a.src == nullptr ? bulk_ok(a.el) : 0);
+    count_launch();
+  } else if constexpr (kTensorProducts<N, GT>) {
+    cudaFuncSetAttribute(down_team_kernel<N, Level0, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc::kSmemBytes);
+    down_team_kernel<N, Level0, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, tc::kSmemBytes,
+                                      st>>>(a);
     count_launch();
   } else {
     team_launch<N>(down_team_kernel<N, Level0, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);

@@ -14,8 +14,11 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lqt_device.cuh"
 #include "lqt_internal.h"
+#include "lqt_tc64.cuh"
 
 namespace lqt {
 namespace team {
@@ -99,6 +102,20 @@ __device__ __forceinline__ void gemm(int lane, FA a, FB b, FO out) {
 #pragma unroll
       for (int c = 0; c < CB; ++c) out(i0 + r, j0 + c, acc[r][c]);
   }
+}
+
+// A product of the combination rule in the type G: on the tensor core
+// (lqt_tc64.cuh) for the FP32 products of n = 64 when the kernel set up a
+// tensor-core context, else the team product above.
+template <int N, int TEAM, typename G, class FA, class FB, class FO>
+__device__ __forceinline__ void pgemm(int lane, tc::Ctx* tcx, FA a, FB b, FO out) {
+  if constexpr (N == 64 && TEAM == tc::kTeam && std::is_same<G, float>::value) {
+    if (tcx) {
+      tc::gemm64(*tcx, a, b, out);
+      return;
+    }
+  }
+  gemm<N, N, N, TEAM, G>(lane, a, b, out);
 }
 
 // An element as six field pointers (full n x n matrices), so that a record can
@@ -248,7 +265,8 @@ __device__ __forceinline__ void copy_rec(int lane, Rec<N> dst, Rec<N> src) {
 
 // ---------------------------------------------------------------------------
 // LU with partial pivoting on W (N x N), applied to R (N x Q); both in the
-// caller's buffers.  Scratch: fscratch 2 * TEAM doubles, iscratch TEAM ints.
+// caller's buffers.  Scratch: fscratch 2 * TEAM doubles (a CTA keeps its row
+// scales at TEAM.., its pivot reciprocals at TEAM + 64..), iscratch TEAM ints.
 // The pivot search compares magnitude keys (mag_key) on the integer pipes.
 // W = I + P in every use (P = C J or C S): a pivot no larger than 2^-40 times
 // its row's original scale max(1, max_j |W_ij|) sets the SINGULAR status bit
@@ -272,11 +290,11 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
     // arg max |W[i][k]|, i >= k (lowest index on ties)
     unsigned long long best = 0;
     int bi = N;
-    for (int i = k + lane; i < N; i += TEAM) {
-      const unsigned long long a = mag_key(W[i * N + k]);
-      if (bi == N || a > best) { best = a; bi = i; }
-    }
     if constexpr (TEAM <= 32) {
+      for (int i = k + lane; i < N; i += TEAM) {
+        const unsigned long long a = mag_key(W[i * N + k]);
+        if (bi == N || a > best) { best = a; bi = i; }
+      }
       for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -289,30 +307,34 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
       else if (lane == bi) rk = rk_k;
       if (lane == 0 && pivot_too_small(__longlong_as_double((long long)best), rk_b)) flag(kStatusSingular);
     } else {
+      // the first warp searches the (at most 64) candidate rows with shuffles
+      // and publishes the pivot row: one barrier per step
+      static_assert(N <= 64, "two candidate rows per lane of the first warp");
       unsigned long long* kb = reinterpret_cast<unsigned long long*>(fscratch);
-      kb[lane] = best;
-      iscratch[lane] = bi;
-      __syncthreads();
-      for (int w = TEAM / 2; w > 0; w >>= 1) {
-        if (lane < w) {
-          const unsigned long long ob = kb[lane + w];
-          const int oi = iscratch[lane + w];
-          if (oi < N && (iscratch[lane] == N || ob > kb[lane] || (ob == kb[lane] && oi < iscratch[lane]))) {
-            kb[lane] = ob;
-            iscratch[lane] = oi;
-          }
+      if (lane < 32) {
+        unsigned long long wb = 0;
+        int wi = N;
+        for (int i = k + lane; i < N; i += 32) {
+          const unsigned long long a = mag_key(W[i * N + k]);
+          if (wi == N || a > wb) { wb = a; wi = i; }
         }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long ob = __shfl_xor_sync(0xffffffffu, wb, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+          if (oi < N && (wi == N || ob > wb || (ob == wb && oi < wi))) { wb = ob; wi = oi; }
+        }
+        if (lane == 0) {
+          kb[0] = wb;
+          iscratch[0] = wi;
+          const unsigned long long rk_b = rks[wi];
+          if (pivot_too_small(__longlong_as_double((long long)wb), rk_b)) flag(kStatusSingular);
+          rks[wi] = rks[k];
+          rks[k] = rk_b;
+        }
       }
+      __syncthreads();
       bi = iscratch[0];
       best = kb[0];
-      __syncthreads();
-      if (lane == 0) {
-        const unsigned long long rk_b = rks[bi];
-        if (pivot_too_small(__longlong_as_double((long long)best), rk_b)) flag(kStatusSingular);
-        rks[bi] = rks[k];
-        rks[k] = rk_b;
-      }
     }
     if (bi != k) {
       for (int j = lane; j < N + Q; j += TEAM) {
@@ -325,11 +347,32 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
     }
     sync<TEAM>();
     const double inv = 1.0 / W[k * N + k];
+    const int wc = N - k - 1, cols = wc + Q;
+    if constexpr (TEAM > 32) {
+      // a CTA: warp w updates rows k+1+w, k+1+w+8, ..., forming each row's
+      // multiplier itself (one instruction per row), the lanes over the
+      // row's columns; 1/pivot kept for the back substitution
+      if (lane == 0) fscratch[TEAM + 64 + k] = inv;
+      const int warp = lane >> 5, wl = lane & 31;
+      for (int i = k + 1 + warp; i < N; i += TEAM / 32) {
+        const double f = W[i * N + k] * inv;
+        for (int c = wl; c < cols; c += 32) {
+          if (c < wc) {
+            const int j = k + 1 + c;
+            W[i * N + j] = fma(-f, W[k * N + j], W[i * N + j]);
+          } else {
+            const int j = c - wc;
+            R[i * Q + j] = fma(-f, R[k * Q + j], R[i * Q + j]);
+          }
+        }
+      }
+      sync<TEAM>();
+      continue;
+    }
     // multipliers into column k (below the diagonal)
     for (int i = k + 1 + lane; i < N; i += TEAM) W[i * N + k] *= inv;
     sync<TEAM>();
     // rank-1 update of the trailing rows
-    const int wc = N - k - 1, cols = wc + Q;
     if constexpr (TEAM <= 32) {
       // a warp: one row at a time, the lanes over its columns (no division by
       // the step-dependent row length in the warp's instruction stream)
@@ -363,7 +406,9 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
   }
   // back substitution, one pivot row at a time
   for (int k = N - 1; k >= 0; --k) {
-    const double inv = 1.0 / W[k * N + k];
+    double inv;
+    if constexpr (TEAM > 32) inv = fscratch[TEAM + 64 + k];
+    else inv = 1.0 / W[k * N + k];
     for (int j = lane; j < Q; j += TEAM) R[k * Q + j] *= inv;
     sync<TEAM>();
     for (int e = lane; e < k * Q; e += TEAM) {
@@ -409,7 +454,8 @@ __host__ __device__ constexpr int combine_scratch_doubles() {
 // products are register-blocked team products (gemm above); the symmetric
 // results J, C are formed in full and stored as (X + X^T)/2.
 template <int N, int TEAM, typename G = double>
-__device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr, double* fs, int* is) {
+__device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr, double* fs, int* is,
+                        tc::Ctx* tcx = nullptr) {
   constexpr int Q = 2 * N + 1;
   double* W = scr;
   double* R = W + N * N;
@@ -423,7 +469,7 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
   const double* A2 = e2.A();
   const double* J2 = e2.J();
   // W = I + C1 J2 ; R = [A1 | C1 | b1 + C1 eta2]
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return C1[i * N + l]; }, [&](int l, int j) { return J2[l * N + j]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return C1[i * N + l]; }, [&](int l, int j) { return J2[l * N + j]; },
                          [&](int i, int j, G v) { W[i * N + j] = (double)v + (i == j ? 1.0 : 0.0); });
   for (int e = lane; e < 2 * N * N; e += TEAM) {
     const int i = e / (2 * N), j = e % (2 * N);
@@ -449,7 +495,7 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
     for (int l = 0; l < N; ++l) w = fma((G)(-J2[e * N + l]), (G)(e1.b()[l]), w);
     wv[e] = w;
   }
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return J2[i * N + l]; }, [&](int l, int j) { return A1[l * N + j]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return J2[i * N + l]; }, [&](int l, int j) { return A1[l * N + j]; },
                          [&](int i, int j, G v) { T1[i * N + j] = v; });
   sync<TEAM>();
   // eta = K1^T w + eta1 ; b = A2 z0 + b2 ; W <- K1^T T1 ; A = A2 K1 ; zeta
@@ -461,10 +507,10 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
     for (int l = 0; l < N; ++l) sb = fma((G)(A2[t * N + l]), (G)(z0[l]), sb);
     out.b()[t] = sb;
   }
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return R[l * Q + i]; }, [&](int l, int j) { return T1[l * N + j]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return R[l * Q + i]; }, [&](int l, int j) { return T1[l * N + j]; },
                          [&](int i, int j, G v) { W[i * N + j] = v; });
   double* oA = out.A();
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return A2[i * N + l]; }, [&](int l, int j) { return R[l * Q + j]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return A2[i * N + l]; }, [&](int l, int j) { return R[l * Q + j]; },
                          [&](int i, int j, G v) { oA[i * N + j] = v; });
   {
     double zt = 0.0;
@@ -484,11 +530,11 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
     const int i = e / N, j = e % N;
     oJ[e] = e1.J()[e] + 0.5 * (W[i * N + j] + W[j * N + i]);
   }
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return A2[i * N + l]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return A2[i * N + l]; },
                          [&](int l, int j) { return R[l * Q + N + j]; }, [&](int i, int j, G v) { T1[i * N + j] = v; });
   sync<TEAM>();
   // C = C2 + sym(T1 A2^T)
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return T1[i * N + l]; }, [&](int l, int j) { return A2[j * N + l]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return T1[i * N + l]; }, [&](int l, int j) { return A2[j * N + l]; },
                          [&](int i, int j, G v) { W[i * N + j] = v; });
   sync<TEAM>();
   double* oC = out.C();
@@ -513,7 +559,8 @@ __host__ __device__ constexpr int val_doubles() {
 
 template <int N, int TEAM, typename G = double>
 __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, double* Psi, double* alpha,
-                              double* scr, double* fs, int* is, double* zeta_inc = nullptr) {
+                              double* scr, double* fs, int* is, double* zeta_inc = nullptr,
+                              tc::Ctx* tcx = nullptr) {
   constexpr int Q = N + 1;
   const double* S2 = V;
   const double* v2 = V + N * N;
@@ -555,7 +602,7 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
     for (int l = 0; l < N; ++l) w = fma((G)(-S2[t * N + l]), (G)(e.b()[l]), w);
     wv[t] = w;
   }
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return S2[i * N + l]; }, [&](int l, int j) { return A[l * N + j]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return S2[i * N + l]; }, [&](int l, int j) { return A[l * N + j]; },
                          [&](int i, int j, G v) { T1[i * N + j] = v; });
   sync<TEAM>();
   double* So = out;
@@ -566,7 +613,7 @@ __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, 
     vo[t] = s;
   }
   // W <- Psi^T T1 ; S = J + sym(W)
-  gemm<N, N, N, TEAM, G>(lane, [&](int i, int l) { return Psi[l * N + i]; },
+  pgemm<N, TEAM, G>(lane, tcx, [&](int i, int l) { return Psi[l * N + i]; },
                          [&](int l, int j) { return T1[l * N + j]; }, [&](int i, int j, G v) { W[i * N + j] = v; });
   {
     double zt = 0.0;
