@@ -467,6 +467,13 @@ def _relmax(a, b):
     return float((a - b).abs().max() / b.abs().max().clamp_min(1e-12))
 
 
+def tune_candidates(n: int):
+    """First-level chunk lengths the batch autotuner tries for state dimension
+    n (0 = the library's own choice): all of them where a solve of the class
+    takes well under a second, three where it takes seconds (n = 16)."""
+    return (0, 2, 4, 8, 16, 32) if n <= 8 else (0, 8, 32)
+
+
 def measure_rows(T_headline, pk=None):
     """Batched (4096 problems), mixed precision (point mass at T = 2^20 and the
     n = 64 workload), adjoint (n = 8, T = 2^14), the short double-integrator
@@ -493,7 +500,7 @@ def measure_rows(T_headline, pk=None):
         for p in probs:
             byn.setdefault(p.n, []).append(p)
         bts = {n: Batch(v) for n, v in sorted(byn.items())}
-        chunks = {n: bt.autotune(candidates=(0, 8, 32), reps=1) for n, bt in bts.items()}
+        chunks = {n: bt.autotune(candidates=tune_candidates(n), reps=3 if n <= 8 else 2) for n, bt in bts.items()}
         outs = {n: bt.new_outputs() for n, bt in bts.items()}
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
@@ -524,7 +531,9 @@ def measure_rows(T_headline, pk=None):
                 "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "sub_intervals": total,
                 "per_n_ms": per, "per_n_count": {str(n): bt.B for n, bt in bts.items()},
                 "per_n_sub_intervals": {str(n): v for n, v in subs_n.items()},
-                "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": st, "roofline": rl,
+                "tuned_chunk": {str(n): c for n, c in chunks.items()},
+                "tuning_ms": {str(n): {str(c): t for c, t in bt.tuned_timings().items()} for n, bt in bts.items()},
+                "status": st, "roofline": rl,
                 "cpu_baseline": cpu_baseline_batch(probs)}
 
     def mixed():
@@ -677,7 +686,7 @@ def measure_rows(T_headline, pk=None):
         bts = {n: Batch(v) for n, v in sorted(byn.items())}
         for bt in bts.values():
             bt.set_invariant_build(True)
-        chunks = {n: bt.autotune(candidates=(0, 8, 32), reps=1) for n, bt in bts.items()}
+        chunks = {n: bt.autotune(candidates=tune_candidates(n), reps=3) for n, bt in bts.items()}
         outs = {n: bt.new_outputs() for n, bt in bts.items()}
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
@@ -704,8 +713,9 @@ def measure_rows(T_headline, pk=None):
                        for n in bts}
         res = {"workload": "the 4096-problem batch (as a4) with the time-invariant element build",
                "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "per_n_ms": per,
-               "tuned_chunk": {str(n): c for n, c in chunks.items()}, "status": lqt.lqt_get_status(),
-               "roofline": rl,
+               "tuned_chunk": {str(n): c for n, c in chunks.items()},
+               "tuning_ms": {str(n): {str(c): t for c, t in bt.tuned_timings().items()} for n, bt in bts.items()},
+               "status": lqt.lqt_get_status(), "roofline": rl,
                "cpu_baseline": "as a4 (the oracle's general element build is the reference of this build)"}
         del bts, outs, g
         p = W.large_state_n64(T=1 << 16)

@@ -275,9 +275,10 @@ lqt_status lqt_densify(const lqt_problem *p, const double *S, const double *v, c
  * grf [n]; gx0 [n].
  * The elements and the optimal-state maps are recomputed from the problem and
  * S, v; the RK4 stage inputs that the discrete adjoint needs are recomputed
- * in segments of 2280 sub-intervals just before that segment's reverse sweep,
+ * in segments of 2^15 sub-intervals just before that segment's reverse sweep,
  * each from its sub-interval's fixed initial condition (A = I, the rest 0), so
- * the workspace holds one segment's stage inputs, not T's.  Steps: state adjoint (a reverse linear
+ * the workspace holds at most one segment's stage inputs, not T's.  Steps:
+ * state adjoint (a reverse linear
  * recurrence run as a forward affine scan), map adjoint, value adjoint (a
  * forward congruence scan Sigma_{k+1} = P_k Sigma_k P_k^T + D_{k+1} with the
  * homogeneous optimal-state maps P_k), element adjoint from the saddle point of

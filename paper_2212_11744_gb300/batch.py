@@ -114,28 +114,37 @@ class Batch:
         return {k: (v[lo:hi] if k != "cost" else v[b]) for k, v in out.items()}
 
     def autotune(self, candidates=(0, 2, 4, 8, 16, 32), reps: int = 3) -> int:
-        """Times the batched solve for each first-level chunk length and keeps
-        the fastest (cached per state dimension, problem count and total
-        boundaries)."""
+        """Times the batched solve for each first-level chunk length (one
+        untimed run, then `reps` runs each timed with CUDA events, the median
+        kept) and keeps the fastest; cached per state dimension, problem
+        count, total boundaries and build flags.  The timing table is
+        `tuning_table()[key][1]`."""
         key = (self.n, self.B, self.total, self.flags)
         if key in _TUNED:
             self.chunk = _TUNED[key][0]
             return self.chunk
         out = self.new_outputs()
         timings = {}
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for c in candidates:
             self.solve(out, chunk=c)
-            e0.record()
+            runs = []
             for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
                 self.solve(out, chunk=c)
-            e1.record()
-            torch.cuda.synchronize()
-            timings[c] = e0.elapsed_time(e1) / reps
+                e1.record()
+                torch.cuda.synchronize()
+                runs.append(e0.elapsed_time(e1))
+            timings[c] = float(np.median(runs))
         best = min(timings, key=timings.get)
         _TUNED[key] = (best, timings)
         self.chunk = best
         return best
+
+    def tuned_timings(self) -> dict:
+        """The autotuner's median time (ms) per candidate chunk, if tuned."""
+        entry = _TUNED.get((self.n, self.B, self.total, self.flags))
+        return dict(entry[1]) if entry else {}
 
     @staticmethod
     def tuning_table():

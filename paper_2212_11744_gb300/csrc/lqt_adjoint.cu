@@ -959,12 +959,16 @@ struct BackwardPlan {
       end;
 };
 
-// The RK4 adjoint runs over segments of sub-intervals, one full wave of its
-// kernel (152 SMs x 15 warps) each: the stage inputs it differentiates are
-// recomputed per segment from every sub-interval's fixed initial condition
-// (A = I, the rest 0; Theorem Backward_HJB_LQT's boundary, eq. abcej_boundary),
-// so their storage is one segment's, not T's.
-constexpr int64_t kAdjSegment = 152 * 15;
+// The RK4 adjoint runs over segments of sub-intervals: the stage inputs it
+// differentiates are recomputed per segment from every sub-interval's fixed
+// initial condition (A = I, the rest 0; Theorem Backward_HJB_LQT's boundary,
+// eq. abcej_boundary), so their storage is one segment's, not T's.  A segment
+// of 2^15 sub-intervals keeps the stage-recording build (one thread per
+// sub-interval: 1024 warps) filling every sub-partition; a shorter one left
+// most of them idle (2280 sub-intervals per segment made the backward pass
+// 2.5x slower at T = 2^14).  Up to one segment, the stages come from the same
+// build as the elements.
+constexpr int64_t kAdjSegment = 1 << 15;
 static int64_t adjoint_segment(int64_t T) { return T < kAdjSegment ? T : kAdjSegment; }
 
 static BackwardPlan backward_plan(const lqt_problem& p, const Layout& L, size_t elem_bytes) {
@@ -1019,9 +1023,15 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
   cudaError_t e = launch_prepare_coefs(p, L, ws + b.coef, cf, st);
   if (e != cudaSuccess) return e;
   ElemPtrs el = carve_elements_at(p, ws + b.elems);
-  // the elements (the RK4 stage inputs for step 5 are recomputed there, segment
-  // by segment)
-  e = launch_build(p, L, cf, el, st);
+  // the elements; with T beyond one segment the RK4 stage inputs for step 5
+  // are recomputed there, segment by segment
+  const bool one_segment = T <= adjoint_segment(T) && T <= kAdjSegment;
+  if (one_segment) {
+    e = launch_build_stages_range(p, L, cf, 0, T, (double*)(ws + b.ys), st, el);
+    if (e == cudaSuccess) e = launch_terminal_element(p, el, st);
+  } else {
+    e = launch_build(p, L, cf, el, st);
+  }
   if (e != cudaSuccess) return e;
   double* maps = (double*)(ws + b.maps);
   e = launch_maps_from_values(p, el, S, v, maps, st);
@@ -1072,11 +1082,14 @@ cudaError_t run_backward(const lqt_problem& p, const Layout& L, size_t elem_byte
     const int64_t seg = adjoint_segment(T);
     for (int64_t j0 = 0; j0 < T; j0 += seg) {
       const int64_t cnt = T - j0 < seg ? T - j0 : seg;
-      e = launch_build_stages_range(p, L, cf, j0, cnt, ra.ys, st);
-      if (e != cudaSuccess) return e;
+      if (!one_segment) {
+        e = launch_build_stages_range(p, L, cf, j0, cnt, ra.ys, st, ElemPtrs{});
+        if (e != cudaSuccess) return e;
+      }
       ra.j0 = j0;
       ra.T = cnt;
-      rk4_adjoint_warp_kernel<<<(unsigned)cnt, 32, smem, st>>>(ra);
+      const int64_t grid = cnt < 152 * 15 ? cnt : 152 * 15;
+      rk4_adjoint_warp_kernel<<<(unsigned)grid, 32, smem, st>>>(ra);
       count_launch();
     }
     ra.T = T;

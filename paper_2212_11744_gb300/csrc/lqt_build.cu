@@ -805,11 +805,11 @@ static cudaError_t launch_build_n(const BuildArgs& a, int M, cudaStream_t st, do
 
 // The RK4 stage inputs of sub-intervals j0 .. j0 + cnt - 1 of p (n <= 8), the
 // stages of sub-interval j0 + i at stages + i K 4 (3n^2 + 2n + 1) (full
-// layout); the elements themselves are not stored.
+// layout); the elements themselves go to `out` when out.A is not null.
 cudaError_t launch_build_stages_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, int64_t j0,
-                                      int64_t cnt, double* stages, cudaStream_t st) {
+                                      int64_t cnt, double* stages, cudaStream_t st, const ElemPtrs& out) {
   BuildArgs a{};
-  a.T = cnt; a.K = p.K; a.t = p.t; a.cf = cf;
+  a.T = cnt; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
   switch (p.n) {
     case 1: return launch_build_n<1>(a, lay.M, st, stages, j0);
     case 2: return launch_build_n<2>(a, lay.M, st, stages, j0);

@@ -102,7 +102,8 @@ Coefs coefs_view(const lqt_problem& p, const Layout& lay, double* Lt, double* Q,
 cudaError_t launch_build_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                                cudaStream_t st);
 cudaError_t launch_build_stages_range(const lqt_problem& p, const Layout& lay, const Coefs& cf, int64_t j0,
-                                      int64_t cnt, double* stages, cudaStream_t st);
+                                      int64_t cnt, double* stages, cudaStream_t st, const ElemPtrs& out);
+cudaError_t launch_terminal_element(const lqt_problem& p, const ElemPtrs& out, cudaStream_t st);
 cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                          cudaStream_t s, double* team_scratch = nullptr);
 // n = 16, 64 (team kernels, lqt_team.cu)
@@ -163,7 +164,6 @@ bool invariant_supported(int n, int M);
 size_t invariant_table_bytes(int n, int M, int K);
 cudaError_t launch_build_invariant(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                                    double* table, cudaStream_t st);
-cudaError_t launch_terminal_element(const lqt_problem& p, const ElemPtrs& out, cudaStream_t st);
 
 bool densify_supported(const lqt_problem& p);
 cudaError_t launch_densify(const lqt_problem& p, const Layout& lay, const Coefs& cf, const double* S, const double* v,

@@ -162,3 +162,22 @@ def test_noalloc_limits_match_the_header(lib):
         assert m.lqt_workspace_size(hp, m.LQT_WS_VALUE) > lim, n
     hp = m.HostProblem(W.large_state_n64(T=1), pinned=False)
     assert m.lqt_workspace_size(hp, m.LQT_WS_VALUE) > lim
+
+
+def test_backward_workspace_holds_one_segment_of_stage_inputs(lib):
+    """Beyond one segment (2^15 sub-intervals) the backward workspace grows by
+    less per sub-interval than the 16 RK4 stage records of a sub-interval
+    (n = 8, K = 4: 16 x (3n^2 + 2n + 1) doubles): the stage inputs are
+    recomputed per segment, not stored for all T."""
+    import paper_2212_11744_gb300 as m
+    hp = m.HostProblem(W.differentiable_n8(T=64), pinned=False)
+    n, K = 8, 4
+
+    def ws(T):
+        hp.struct.T = T
+        return m.lqt_workspace_size(hp, m.LQT_WS_BACKWARD)
+
+    stage_record = 4 * K * (3 * n * n + 2 * n + 1) * 8
+    T1, T2 = 1 << 16, 1 << 20
+    assert ws(T2) > ws(T1) > 0
+    assert (ws(T2) - ws(T1)) / (T2 - T1) < 0.5 * stage_record
