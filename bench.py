@@ -667,12 +667,26 @@ def measure_rows(T_headline, pk=None):
         m2 = lqt.lqt_solve_method2(dp, ws=ws)
         m1 = lqt.lqt_solve(dp)
         ms = _events_ms(lambda: lqt.lqt_solve_method2(dp, out=m2, ws=ws), 3)
-        return {"workload": "point mass T=2^20, K=4: values by the suffix scan, states by Method 2 (forward-ODE "
-                            "elements, prefix scan)", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms,
-                "rel_diff_vs_method1": {k: _relmax(m2[k], m1[k]) for k in ("x", "u")},
-                "roofline": roofline("lqt_solve_method2 n=4", alg_method2(p.n, p.m, p.K),
-                                     "2 K (40 n^3 + 60 n^2) + 2 (22 n^3) + 3 n^3 + 2 m n", p.T, ms, pk),
-                "status": lqt.lqt_get_status(), "cpu_baseline": cpu_baseline_method2()}
+        formula = "2 K (40 n^3 + 60 n^2) + 2 (22 n^3) + 3 n^3 + 2 m n"
+        row = {"workload": "point mass T=2^20, K=4: values by the suffix scan, states by Method 2 (forward-ODE "
+                           "elements, prefix scan)", "value": p.T / (ms * 1e-3), "unit": UNIT, "ms": ms,
+               "rel_diff_vs_method1": {k: _relmax(m2[k], m1[k]) for k in ("x", "u")},
+               "roofline": roofline("lqt_solve_method2 n=4", alg_method2(p.n, p.m, p.K), formula, p.T, ms, pk),
+               "status": lqt.lqt_get_status(), "cpu_baseline": cpu_baseline_method2()}
+        del ws, m2, m1
+        # the team kernels: a warp per element and combination (n = 16), a
+        # 256-thread CTA (n = 64)
+        for name, q in (("n16_m8_K4_T65536", W.batched_member(7, T=1 << 16, n=16)),
+                        ("n64_m16_K2_T4096", W.large_state_n64(T=1 << 12))):
+            dq = lqt.DeviceProblem(q)
+            wq = torch.empty(lqt.lqt_workspace_size(dq, lqt.LQT_WS_SOLVE_METHOD2), dtype=torch.uint8, device="cuda")
+            oq = lqt.lqt_solve_method2(dq, ws=wq)
+            mq = _events_ms(lambda: lqt.lqt_solve_method2(dq, out=oq, ws=wq), 2)
+            row[name] = {"ms": mq, "value": q.T / (mq * 1e-3), "unit": UNIT, "status": lqt.lqt_get_status(),
+                         "roofline": roofline(f"lqt_solve_method2 n={q.n}", alg_method2(q.n, q.m, q.K), formula,
+                                              q.T, mq, pk)}
+            del wq, oq
+        return row
 
     def invariant():
         """The 4096-problem batch and the n = 64 problem with the time-invariant

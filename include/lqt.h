@@ -210,8 +210,10 @@ lqt_status lqt_solve_invariant(const lqt_problem *p, const double *x0, double *S
 
 /* Method 2 of the optimal-trajectory recovery (Sec. IV-E, eq.
  * Opt_trajectory_method2) with elements from the forward conditional HJB ODEs
- * (Sec. IV-C, Theorem Forward_HJB_LQT).  Supported: n <= 8 (otherwise
- * LQT_EUNSUPPORTED).  All three are asynchronous and allocation-free.
+ * (Sec. IV-C, Theorem Forward_HJB_LQT).  Supported: every n of lqt_solve
+ * (n <= 8 one thread per element; n = 16 one warp, n = 64 one 256-thread CTA
+ * per element and per combination).  All three are asynchronous and
+ * allocation-free.
  *
  * lqt_build_elements_forward: the T elements a_j = V(., t_j; ., t_{j+1}),
  * j = 0..T-1 (no terminal element), each by K classical RK4 steps of the

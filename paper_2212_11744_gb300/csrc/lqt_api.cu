@@ -124,7 +124,7 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
     case LQT_WS_SEQUENTIAL: return L.coef_bytes + align_up(sequential_workspace_bytes(p->n, p->T, p->K));
     case LQT_WS_BACKWARD: return backward_workspace_bytes(*p, L, element_bytes(*p)) + 4096;
     case LQT_WS_DENSIFY: return L.coef_bytes;
-    case LQT_WS_METHOD2: return p->n > 8 ? 0 : L.coef_bytes + prefix_workspace_bytes(p->n, p->T);
+    case LQT_WS_METHOD2: return L.coef_bytes + prefix_workspace_bytes(p->n, p->T);
     case LQT_WS_INVARIANT:
       return invariant_supported(p->n, L.M) ? L.coef_bytes + align_up(invariant_table_bytes(p->n, L.M, p->K)) : 0;
     case LQT_WS_SOLVE_INVARIANT:
@@ -133,9 +133,8 @@ size_t lqt_workspace_size(const lqt_problem* p, int32_t which) {
                        scan_workspace_bytes(p->n, p->T, true) + align_up(invariant_table_bytes(p->n, L.M, p->K))
                  : 0;
     case LQT_WS_SOLVE_METHOD2:
-      return p->n > 8 ? 0
-                      : L.coef_bytes + 2 * element_bytes(*p) + align_up(T1 * 8) +
-                            scan_workspace_bytes(p->n, p->T, false) + prefix_workspace_bytes(p->n, p->T);
+      return L.coef_bytes + 2 * element_bytes(*p) + align_up(T1 * 8) + team_build_scratch_bytes(p->n) +
+             scan_workspace_bytes(p->n, p->T, false) + prefix_workspace_bytes(p->n, p->T);
     default: return 0;
   }
 }
@@ -293,15 +292,14 @@ lqt_status lqt_build_elements_forward(const lqt_problem* p, const lqt_elements* 
   t_launches = 0;
   lqt_status s = validate(p);
   if (s != LQT_OK) return s;
-  if (p->n > 8) return LQT_EUNSUPPORTED;
   if (!out || !out->A || !out->b || !out->C || !out->eta || !out->J) return LQT_EINVAL;
   const Layout L = make_layout(*p);
-  if (!ws || ws_bytes < L.coef_bytes) return LQT_EWORKSPACE;
+  if (!ws || ws_bytes < lqt_workspace_size(p, LQT_WS_BUILD)) return LQT_EWORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   Coefs cf;
   if (launch_prepare_coefs(*p, L, (char*)ws, cf, st) != cudaSuccess) return LQT_ECUDA;
   ElemPtrs el{out->A, out->b, out->C, out->eta, out->J, out->zeta};
-  return from_cuda(launch_build_forward(*p, L, cf, el, st));
+  return from_cuda(launch_build_forward(*p, L, cf, el, st, (double*)((char*)ws + L.coef_bytes)));
 }
 
 lqt_status lqt_trajectory_method2(const lqt_problem* p, const lqt_elements* fwd, const double* S, const double* v,
@@ -309,7 +307,6 @@ lqt_status lqt_trajectory_method2(const lqt_problem* p, const lqt_elements* fwd,
   t_launches = 0;
   lqt_status s = validate(p);
   if (s != LQT_OK) return s;
-  if (p->n > 8) return LQT_EUNSUPPORTED;
   if (!fwd || !fwd->A || !fwd->b || !fwd->C || !fwd->eta || !fwd->J || !S || !v || !x0 || !x) return LQT_EINVAL;
   const size_t need = lqt_workspace_size(p, LQT_WS_METHOD2);
   if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
@@ -326,7 +323,6 @@ lqt_status lqt_solve_method2(const lqt_problem* p, const double* x0, double* S, 
   t_launches = 0;
   lqt_status s = validate(p);
   if (s != LQT_OK) return s;
-  if (p->n > 8) return LQT_EUNSUPPORTED;
   if (!x0 || !S || !v || !x) return LQT_EINVAL;
   const size_t need = lqt_workspace_size(p, LQT_WS_SOLVE_METHOD2);
   if (!ws || ws_bytes < need) return LQT_EWORKSPACE;
@@ -343,15 +339,17 @@ lqt_status lqt_solve_method2(const lqt_problem* p, const double* x0, double* S, 
   double* zbuf = (double*)cur;
   cur += align_up(((size_t)p->T + 1) * 8);
   double* zout = zeta ? zeta : zbuf;
+  double* team_scr = (double*)cur;  // both element builds (n = 64), one after the other
+  cur += team_build_scratch_bytes(p->n);
   // values: backward-ODE elements and the suffix scan (Sec. IV-B, IV-D, IV-A)
-  if (launch_build(*p, L, cf, bwd, st, nullptr) != cudaSuccess) return LQT_ECUDA;
+  if (launch_build(*p, L, cf, bwd, st, team_scr) != cudaSuccess) return LQT_ECUDA;
   const size_t scan_bytes = scan_workspace_bytes(p->n, p->T, false);
   if (run_value_and_traj(*p, L, cf, bwd, S, v, zout, nullptr, nullptr, nullptr, nullptr, true, false, nullptr,
                          nullptr, cur, scan_bytes, st) != cudaSuccess)
     return LQT_ECUDA;
   cur += scan_bytes;
   // states: forward-ODE elements, prefix scan, Method 2 (Sec. IV-C, IV-E)
-  if (launch_build_forward(*p, L, cf, fwd, st) != cudaSuccess) return LQT_ECUDA;
+  if (launch_build_forward(*p, L, cf, fwd, st, team_scr) != cudaSuccess) return LQT_ECUDA;
   return from_cuda(run_method2(*p, cf, fwd, S, v, zout, x0, x, u, cost, cur, st));
 }
 

@@ -1,8 +1,9 @@
 // Elements from the forward conditional HJB ODEs (Sec. IV-C, Theorem
 // Forward_HJB_LQT), for Method 2 of the optimal-trajectory recovery (Sec. IV-E).
-// One thread per sub-interval j: K classical RK4 steps in tau from the
-// boundary A = I, b = C = eta = J = 0, zeta = 0 at tau = t_j (eq.
-// abcej_boundary) up to tau = t_{j+1}.  With Q = H^T X H, q = H^T X r,
+// One thread per sub-interval j (n <= 8; n = 16 and 64 run one team per
+// element, build_forward_team_kernel in lqt_team.cu): K classical RK4 steps
+// in tau from the boundary A = I, b = C = eta = J = 0, zeta = 0 at tau = t_j
+// (eq. abcej_boundary) up to tau = t_{j+1}.  With Q = H^T X H, q = H^T X r,
 // rho = r^T X r and B = L U^-1 L^T = Lt Lt^T:
 //   dA/dtau    = F A - C Q A
 //   db/dtau    = c + F b + C (q - Q b)
@@ -208,7 +209,7 @@ static cudaError_t launch_fwd_n(const ForwardArgs& a, int M, cudaStream_t st) {
 }
 
 cudaError_t launch_build_forward(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, double* team_scratch) {
   ForwardArgs a{p.T, p.K, p.t, cf, out};
   switch (p.n) {
     case 1: return launch_fwd_n<1>(a, lay.M, st);
@@ -216,6 +217,8 @@ cudaError_t launch_build_forward(const lqt_problem& p, const Layout& lay, const 
     case 3: return launch_fwd_n<3>(a, lay.M, st);
     case 4: return launch_fwd_n<4>(a, lay.M, st);
     case 8: return launch_fwd_n<8>(a, lay.M, st);
+    case 16:
+    case 64: return team_launch_build_forward(p, lay, cf, out, team_scratch, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -148,13 +148,22 @@ void team_maps_down(const double* maps, int64_t cnt, int G, const double* above,
                     cudaStream_t st);
 
 template <int N>
-void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, double* pre, cudaStream_t st);
+void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, double* pre, cudaStream_t st,
+                      double* gscratch = nullptr);
 
 // Method 2 (lqt_forward.cu, lqt_scan.cu): forward-ODE elements, prefix scan
 // and the optimal states from the prefixes and the values.
 cudaError_t launch_build_forward(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
-                                 cudaStream_t st);
+                                 cudaStream_t st, double* team_scratch = nullptr);
 size_t prefix_workspace_bytes(int n, int64_t T);
+// n = 16, 64 (team kernels, lqt_team.cu); the forward build's scratch is
+// team_build_scratch_bytes(n)
+cudaError_t team_launch_build_forward(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                                      double* gscratch, cudaStream_t st);
+size_t team_prefix_workspace_bytes(int n, int64_t T);
+cudaError_t team_run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
+                             const double* v, const double* zeta, const double* x0, double* x, double* u,
+                             double* cost, char* ws, cudaStream_t st);
 cudaError_t run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
                         const double* v, const double* zeta, const double* x0, double* x, double* u, double* cost,
                         char* ws, cudaStream_t st);

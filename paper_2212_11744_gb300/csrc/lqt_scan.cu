@@ -999,6 +999,8 @@ size_t prefix_workspace_bytes(int n, int64_t T) {
     case 3: return make_prefix_plan<3>(T).bytes;
     case 4: return make_prefix_plan<4>(T).bytes;
     case 8: return make_prefix_plan<8>(T).bytes;
+    case 16:
+    case 64: return team_prefix_workspace_bytes(n, T);
     default: return 0;
   }
 }
@@ -1012,6 +1014,8 @@ cudaError_t run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& f
     case 3: return method2_n<3>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
     case 4: return method2_n<4>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
     case 8: return method2_n<8>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    case 16:
+    case 64: return team_run_method2(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -224,6 +224,57 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::BUILD_MIN)
   }
 }
 
+// Elements of the forward conditional ODEs (Sec. IV-C, Theorem
+// Forward_HJB_LQT) for Method 2: element j by K classical RK4 steps in tau
+// from A = I, b = C = eta = J = 0, zeta = 0 at tau = t_j (eq.
+// abcej_boundary) to t_{j+1}, stage samples at half-steps 2i, 2i+1, 2i+2 of
+// step i.  One team per element; records y (state), yn (the four-stage sum),
+// yt (stage input), k (rate), all packed.
+template <int N>
+constexpr int forward_slot_doubles() { return 4 * Rec<N>::SIZE + 2 * N * N + N + 8; }
+
+template <int N, int M>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_forward_team_kernel(TeamBuildArgs a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int RS = Rec<N>::SIZE;
+  const int lane = threadIdx.x;
+  double* y = slot_base<N>(a.gscratch, forward_slot_doubles<N>());
+  double* yn = y + RS;
+  double* yt = yn + RS;
+  double* k = yt + RS;
+  double* QA = k + RS;
+  double* CQ = QA + N * N;
+  double* w = CQ + N * N;
+  const Coefs& cf = a.cf;
+  for (int64_t j = blockIdx.x; j < a.T; j += gridDim.x) {
+    const double h = (a.t[j + 1] - a.t[j]) / a.K;
+    for (int e = lane; e < RS; e += TEAM) y[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
+    team::sync<TEAM>();
+    for (int32_t i = 0; i < a.K; ++i) {
+      const int32_t ps[3] = {2 * i, 2 * i + 1, 2 * i + 2};
+      const double *F[3], *c[3], *Lt[3], *Q[3], *qr[3];
+      for (int q = 0; q < 3; ++q) {
+        F[q] = cf.F.ptr + sample_index(cf.F.mode, j, ps[q], a.K) * N * N;
+        c[q] = cf.c.ptr ? cf.c.ptr + sample_index(cf.c.mode, j, ps[q], a.K) * N : nullptr;
+        Lt[q] = cf.Lt.ptr + sample_index(cf.Lt.mode, j, ps[q], a.K) * N * M;
+        Q[q] = cf.Q.ptr + sample_index(cf.Q.mode, j, ps[q], a.K) * N * N;
+        qr[q] = cf.qr.ptr + sample_index(cf.qr.mode, j, ps[q], a.K) * (N + 1);
+      }
+      const Rec<N> Ry = Rec<N>::packed(y), Rt = Rec<N>::packed(yt), Rk = Rec<N>::packed(k);
+      team::forward_rhs<N, M, TEAM>(lane, Ry, Rk, F[0], c[0], Lt[0], Q[0], qr[0], QA, CQ, w);
+      team::axpy2_rec<N, TEAM>(lane, yn, y, h / 6.0, yt, y, 0.5 * h, k);
+      team::forward_rhs<N, M, TEAM>(lane, Rt, Rk, F[1], c[1], Lt[1], Q[1], qr[1], QA, CQ, w);
+      team::axpy2_rec<N, TEAM>(lane, yn, yn, h / 3.0, yt, y, 0.5 * h, k);
+      team::forward_rhs<N, M, TEAM>(lane, Rt, Rk, F[1], c[1], Lt[1], Q[1], qr[1], QA, CQ, w);
+      team::axpy2_rec<N, TEAM>(lane, yn, yn, h / 3.0, yt, y, h, k);
+      team::forward_rhs<N, M, TEAM>(lane, Rt, Rk, F[2], c[2], Lt[2], Q[2], qr[2], QA, CQ, w);
+      team::axpy2_rec<N, TEAM>(lane, y, yn, h / 6.0, nullptr, nullptr, 0.0, k);
+    }
+    double zz = 0.0;
+    team::copy_rec<N, TEAM>(lane, Rec<N>::pub(a.out, j, &zz), Rec<N>::packed(y));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // stage (b): reduce / down-sweep of the value scan
 // ---------------------------------------------------------------------------
@@ -853,6 +904,7 @@ struct TeamPrefixArgs {
   int64_t cnt;           // entries at level l
   const double* pre_up;  // prefixes of level l+1 (full records), or null at the top
   double* pre;           // out: prefixes of level l
+  double* gscratch;      // per-CTA slots (teams whose buffers live in global memory)
 };
 
 template <int N>
@@ -864,7 +916,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) prefix_down_team_kernel(Team
   __shared__ double fs[2 * TEAM];
   __shared__ int is[TEAM];
   const int lane = threadIdx.x;
-  double* base = slot_base<N>(nullptr, prefix_slot_doubles<N>());
+  double* base = slot_base<N>(a.gscratch, prefix_slot_doubles<N>());
   double* ident = base;
   double* scr = ident + Rec<N>::SIZE;
   for (int e = lane; e < Rec<N>::SIZE; e += TEAM) ident[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
@@ -882,9 +934,266 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) prefix_down_team_kernel(Team
 }
 
 template <int N>
-void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, double* pre, cudaStream_t st) {
-  TeamPrefixArgs a{agg, cnt, pre_up, pre};
+void team_prefix_down(const double* agg, int64_t cnt, const double* pre_up, double* pre, cudaStream_t st,
+                      double* gscratch) {
+  TeamPrefixArgs a{agg, cnt, pre_up, pre, gscratch};
   team_launch<N>(prefix_down_team_kernel<N>, tdiv(cnt, 2), prefix_slot_doubles<N>(), a, st);
+}
+
+// ---------------------------------------------------------------------------
+// Method 2 of the trajectory recovery (Sec. IV-E, eq.
+// Opt_trajectory_method2), n = 16 and 64
+// ---------------------------------------------------------------------------
+
+// The forward elements' prefixes V(., t_0; ., t_k) = a_0 (x) ... (x) a_{k-1}:
+// chunk aggregates by the value scan's reduce kernels (the same combination,
+// Sec. IV-A eq. lqt_comb), their exclusive prefixes by prefix_down_team_kernel,
+// and in each level-0 chunk a team folds the chunk's elements onto the chunk's
+// prefix left to right, emitting at every boundary k
+//   x_k = (I + C_k S_k)^-1 (A_k x0 + b_k + C_k v_k),  u_k = Ku (v_k - S_k x_k).
+struct TeamM2Args {
+  ElemPtrs el;         // forward-ODE elements, T of them
+  int64_t T;
+  int G;               // level-0 chunk length
+  const double* pre0;  // exclusive prefixes of the level-0 chunks (packed), or null (one chunk)
+  const double *S, *v, *zeta, *x0, *Ku;
+  int32_t Ku_per_boundary, m;
+  double *x, *u, *cost;
+  double* gscratch;
+  int bulk;            // n = 16: stage the elements by TMA
+};
+
+// Per-team buffers: the prefix P and (n = 16) the staged element or (n = 64)
+// the prefix's successor, the combination's scratch, then W (N x N), r, e (N).
+template <int N>
+constexpr int m2_rec_doubles() { return N == 16 ? w16::kRecPad : Rec<N>::SIZE; }
+template <int N>
+constexpr int m2_scratch_doubles() { return N == 16 ? w16::kScratch : team::combine_scratch_doubles<N>(); }
+template <int N>
+constexpr int m2_slot_doubles() { return 2 * m2_rec_doubles<N>() + m2_scratch_doubles<N>() + N * N + 2 * N + 8; }
+
+// State and control at boundary k from the prefix P (packed record).
+template <int N, int TEAM>
+__device__ void m2_state(int lane, const TeamM2Args& a, int64_t k, const double* P, double* W, double* r,
+                         double* ev, double* fs, int* is) {
+  const double* PA = P;
+  const double* Pb = P + N * N;
+  const double* PC = P + N * N + N;
+  const double* Sk = a.S + k * N * N;
+  const double* vk = a.v + k * N;
+  team::gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return PC[i * N + l]; }, [&](int l, int j) { return Sk[l * N + j]; },
+      [&](int i, int j, double s) { W[i * N + j] = s + (i == j ? 1.0 : 0.0); });
+  for (int i = lane; i < N; i += TEAM) {
+    double s = Pb[i];
+    for (int l = 0; l < N; ++l) {
+      s = fma(PA[i * N + l], a.x0[l], s);
+      s = fma(PC[i * N + l], vk[l], s);
+    }
+    r[i] = s;
+  }
+  team::sync<TEAM>();
+  team::lu_solve<N, TEAM, 1>(lane, W, r, fs, is);
+  for (int i = lane; i < N; i += TEAM) {
+    a.x[k * N + i] = r[i];
+    if (!isfinite(r[i])) flag(kStatusNonFinite);
+  }
+  if (a.u) {
+    for (int i = lane; i < N; i += TEAM) {
+      double s = vk[i];
+      for (int l = 0; l < N; ++l) s = fma(-Sk[i * N + l], r[l], s);
+      ev[i] = s;
+    }
+    team::sync<TEAM>();
+    const double* Kk = a.Ku + (a.Ku_per_boundary ? k * a.m * N : 0);
+    for (int q = lane; q < a.m; q += TEAM) {
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(Kk[q * N + l], ev[l], s);
+      a.u[k * a.m + q] = s;
+    }
+  }
+  team::sync<TEAM>();
+}
+
+template <int N>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) method2_team_kernel(TeamM2Args a) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int RS = Rec<N>::SIZE;
+  __shared__ double fs[2 * TEAM];
+  __shared__ int is[TEAM];
+  __shared__ unsigned long long bar;
+  __shared__ double zero;
+  const int lane = threadIdx.x;
+  double* base;
+  if constexpr (N == 16) {
+    extern __shared__ __align__(16) double m2_smem[];
+    base = m2_smem;
+  } else {
+    base = slot_base<N>(a.gscratch, m2_slot_doubles<N>());
+  }
+  double* P = base;
+  double* Pn = P + m2_rec_doubles<N>();
+  double* scr = Pn + m2_rec_doubles<N>();
+  double* W = scr + m2_scratch_doubles<N>();
+  double* r = W + N * N;
+  double* ev = r + N;
+  if (lane == 0) {
+    zero = 0.0;
+    if constexpr (N == 16) w16::mbar_init(&bar, 1);
+  }
+  team::sync<TEAM>();
+  unsigned phase = 0;
+  const int64_t groups = tdiv(a.T, a.G);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = g * a.G;
+    const int64_t last = (first + a.G < a.T ? first + a.G : a.T) - 1;
+    for (int e = lane; e < RS; e += TEAM)
+      P[e] = a.pre0 ? a.pre0[g * RS + e] : ((e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0);
+    team::sync<TEAM>();
+    for (int64_t k = first; k <= last; ++k) {
+      m2_state<N, TEAM>(lane, a, k, P, W, r, ev, fs, is);
+      if constexpr (N == 16) {
+        w16::stage(lane, w16::ElemSrc{a.el, nullptr, a.bulk != 0}, k, Pn, &bar, phase, &zero);
+        w16::combine<double>(lane, P, Pn, scr);
+      } else {
+        team::combine<N, TEAM>(lane, Rec<N>::packed(P), Rec<N>::pub(a.el, k, &zero), Rec<N>::packed(Pn), scr, fs,
+                               is);
+        double* t = P;
+        P = Pn;
+        Pn = t;
+      }
+    }
+    if (last == a.T - 1) m2_state<N, TEAM>(lane, a, a.T, P, W, r, ev, fs, is);
+    if (g == 0 && a.cost != nullptr && lane == 0) {
+      double c = a.zeta ? a.zeta[0] : 0.0;
+      for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int l = 0; l < N; ++l) s = fma(a.S[i * N + l], a.x0[l], s);
+        c = fma(a.x0[i], fma(0.5, s, -a.v[i]), c);
+      }
+      *a.cost = c;
+    }
+    team::sync<TEAM>();
+  }
+}
+
+template <int N>
+struct TeamPrefixPlan {
+  int G0;
+  int nlev;
+  int64_t cnt[64];
+  size_t off_agg[64], off_pre[64];
+  size_t off_scratch;
+  size_t bytes;
+};
+
+template <int N>
+static TeamPrefixPlan<N> team_prefix_plan(int64_t T) {
+  TeamPrefixPlan<N> pl{};
+  pl.G0 = team_group0<N>(T - 1);
+  const size_t PE = sizeof(double) * Rec<N>::SIZE;
+  size_t off = 0;
+  int64_t c = T;
+  int G = pl.G0;
+  while (c > G) {
+    const int64_t nc = tdiv(c, G);
+    pl.cnt[pl.nlev] = nc;
+    pl.off_agg[pl.nlev] = off;
+    off = tal(off + nc * PE);
+    pl.off_pre[pl.nlev] = off;
+    off = tal(off + nc * PE);
+    ++pl.nlev;
+    c = nc;
+    G = 2;
+  }
+  pl.off_scratch = off;
+  if (!TeamCfg<N>::SMEM) {
+    size_t sd = m2_slot_doubles<N>();
+    if ((size_t)reduce_slot_doubles<N>() > sd) sd = reduce_slot_doubles<N>();
+    if ((size_t)prefix_slot_doubles<N>() > sd) sd = prefix_slot_doubles<N>();
+    off = tal(off + (size_t)TeamCfg<N>::SLOTS * sd * sizeof(double));
+  }
+  pl.bytes = tal(off);
+  return pl;
+}
+
+template <int N>
+static cudaError_t team_method2_n(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
+                                 const double* v, const double* zeta, const double* x0, double* x, double* u,
+                                 double* cost, char* ws, cudaStream_t st) {
+  const TeamPrefixPlan<N> pl = team_prefix_plan<N>(p.T);
+  double* gs = TeamCfg<N>::SMEM ? nullptr : (double*)(ws + pl.off_scratch);
+  int64_t c = p.T;
+  int G = pl.G0;
+  for (int l = 0; l < pl.nlev; ++l) {
+    TeamScanArgs a{};
+    a.el = fwd; a.src = l ? (const double*)(ws + pl.off_agg[l - 1]) : nullptr; a.cnt = c; a.G = G;
+    a.agg = (double*)(ws + pl.off_agg[l]); a.T = p.T; a.gscratch = gs;
+    launch_reduce<N, double>(a, pl.cnt[l], st);
+    c = pl.cnt[l];
+    G = 2;
+  }
+  for (int l = pl.nlev - 1; l >= 0; --l) {
+    const double* up = l + 1 < pl.nlev ? (const double*)(ws + pl.off_pre[l + 1]) : nullptr;
+    team_prefix_down<N>((const double*)(ws + pl.off_agg[l]), pl.cnt[l], up, (double*)(ws + pl.off_pre[l]), st, gs);
+  }
+  TeamM2Args a{};
+  a.el = fwd; a.T = p.T; a.G = pl.G0;
+  a.pre0 = pl.nlev > 0 ? (const double*)(ws + pl.off_pre[0]) : nullptr;
+  a.S = S; a.v = v; a.zeta = zeta; a.x0 = x0;
+  a.Ku = cf.Ku; a.Ku_per_boundary = cf.Ku_per_boundary; a.m = p.m;
+  a.x = x; a.u = u; a.cost = cost; a.gscratch = gs; a.bulk = bulk_ok(fwd);
+  team_launch<N>(method2_team_kernel<N>, tdiv(p.T, pl.G0), m2_slot_doubles<N>(), a, st);
+  return cudaGetLastError();
+}
+
+size_t team_prefix_workspace_bytes(int n, int64_t T) {
+  switch (n) {
+    case 16: return team_prefix_plan<16>(T).bytes;
+    case 64: return team_prefix_plan<64>(T).bytes;
+    default: return 0;
+  }
+}
+
+cudaError_t team_run_method2(const lqt_problem& p, const Coefs& cf, const ElemPtrs& fwd, const double* S,
+                             const double* v, const double* zeta, const double* x0, double* x, double* u,
+                             double* cost, char* ws, cudaStream_t st) {
+  switch (p.n) {
+    case 16: return team_method2_n<16>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    case 64: return team_method2_n<64>(p, cf, fwd, S, v, zeta, x0, x, u, cost, ws, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, int M>
+static cudaError_t team_fwd_nm(const lqt_problem& p, const Coefs& cf, const ElemPtrs& out, double* gscratch,
+                               cudaStream_t st) {
+  TeamBuildArgs a{p.T, p.K, p.t, cf, out, gscratch};
+  // n = 16: 29.9 KB of shared memory per warp, 7 warps per SM
+  team_launch<N>(build_forward_team_kernel<N, M>, p.T, forward_slot_doubles<N>(), a, st,
+                 N == 16 ? 152 * 7 : TeamCfg<N>::SLOTS);
+  return cudaGetLastError();
+}
+
+cudaError_t team_launch_build_forward(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
+                                      double* gscratch, cudaStream_t st) {
+  switch (p.n) {
+    case 16:
+      switch (lay.M) {
+        case 1: return team_fwd_nm<16, 1>(p, cf, out, gscratch, st);
+        case 2: return team_fwd_nm<16, 2>(p, cf, out, gscratch, st);
+        case 4: return team_fwd_nm<16, 4>(p, cf, out, gscratch, st);
+        case 8: return team_fwd_nm<16, 8>(p, cf, out, gscratch, st);
+        case 16: return team_fwd_nm<16, 16>(p, cf, out, gscratch, st);
+        default: return cudaErrorInvalidValue;
+      }
+    case 64:
+      switch (lay.M) {
+        case 16: return team_fwd_nm<64, 16>(p, cf, out, gscratch, st);
+        default: return cudaErrorInvalidValue;
+      }
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Time-invariant element build (lqt_invariant.cu), n = 16 and 64: the shared
@@ -991,7 +1300,7 @@ template void launch_inv_master_team<64, 16>(int32_t, int32_t, const BatchProb*,
   template void team_maps_reduce<N>(const double*, int64_t, int, double*, cudaStream_t);                 \
   template void team_maps_down<N>(const double*, int64_t, int, const double*, const double*, double*,    \
                                   cudaStream_t);                                                         \
-  template void team_prefix_down<N>(const double*, int64_t, const double*, double*, cudaStream_t);
+  template void team_prefix_down<N>(const double*, int64_t, const double*, double*, cudaStream_t, double*);
 LQT_TEAM_UPPER(1)
 LQT_TEAM_UPPER(2)
 LQT_TEAM_UPPER(3)
@@ -1117,9 +1426,14 @@ static cudaError_t team_run(const lqt_problem& p, const Coefs& cf, const ElemPtr
   return team_run_g<N, double>(p, cf, el, S, v, zeta, x0, x, u, cost, do_value, do_traj, ws, st);
 }
 
-// Build scratch for n = 64 (per-slot element buffers).
+// Build scratch for n = 64: per-slot element buffers of the backward-ODE build
+// and of the forward-ODE build of Method 2.
 size_t team_build_scratch_bytes(int n) {
-  if (n == 64) return tal((size_t)TeamCfg<64>::SLOTS * build_slot_doubles<64, 16>() * sizeof(double));
+  if (n == 64) {
+    const size_t sd = build_slot_doubles<64, 16>() > forward_slot_doubles<64>() ? build_slot_doubles<64, 16>()
+                                                                                : forward_slot_doubles<64>();
+    return tal((size_t)TeamCfg<64>::SLOTS * sd * sizeof(double));
+  }
   return 0;
 }
 

@@ -249,6 +249,98 @@ __device__ __forceinline__ void axpy_flow(int lane, Rec<N> out, Rec<N> base, dou
 }
 
 
+// ---------------------------------------------------------------------------
+// forward conditional ODEs (Sec. IV-C, Theorem Forward_HJB_LQT), full records
+// ---------------------------------------------------------------------------
+
+// k = f(y) for the forward element flow in tau, with B = Lt Lt^T,
+// Q = H^T X H, q = H^T X r, rho = r^T X r (qr = [q | rho]):
+//   dA = F A - C Q A             db = c + F b + C w      (w = q - Q b)
+//   dC = B + F C + (F C)^T - C Q C
+//   deta = A^T w                 dJ = A^T Q A
+//   dzeta = rho/2 - b^T (w + q)/2
+// y, k: packed records (k must not alias y).  Scratch QA, CQ (N x N), w (N).
+// Products that share a shape give every thread the same outputs (gemm), so
+// the terms of dA and dC are accumulated without barriers between them.
+template <int N, int M, int TEAM>
+__device__ void forward_rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
+                            const double* __restrict__ Lt, const double* __restrict__ Q,
+                            const double* __restrict__ qr, double* QA, double* CQ, double* w) {
+  const double* A = y.A();
+  const double* C = y.C();
+  const double* b = y.b();
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return Q[i * N + l]; }, [&](int l, int j) { return A[l * N + j]; },
+      [&](int i, int j, double s) { QA[i * N + j] = s; });
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return C[i * N + l]; }, [&](int l, int j) { return Q[l * N + j]; },
+      [&](int i, int j, double s) { CQ[i * N + j] = s; });
+  for (int i = lane; i < N; i += TEAM) {
+    double s = qr[i];
+    for (int l = 0; l < N; ++l) s = fma(-Q[i * N + l], b[l], s);
+    w[i] = s;
+  }
+  sync<TEAM>();
+  double* kA = k.A();
+  double* kC = k.C();
+  double* kJ = k.J();
+  // dA = F A - C (Q A)
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return F[i * N + l]; }, [&](int l, int j) { return A[l * N + j]; },
+      [&](int i, int j, double s) { kA[i * N + j] = s; });
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return C[i * N + l]; }, [&](int l, int j) { return QA[l * N + j]; },
+      [&](int i, int j, double s) { kA[i * N + j] -= s; });
+  // dC = F C + C F^T - (C Q) C + Lt Lt^T  (C F^T = (F C)^T, C symmetric)
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return F[i * N + l]; }, [&](int l, int j) { return C[l * N + j]; },
+      [&](int i, int j, double s) { kC[i * N + j] = s; });
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return C[i * N + l]; }, [&](int l, int j) { return F[j * N + l]; },
+      [&](int i, int j, double s) { kC[i * N + j] += s; });
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return CQ[i * N + l]; }, [&](int l, int j) { return C[l * N + j]; },
+      [&](int i, int j, double s) {
+        double bij = kC[i * N + j] - s;
+        for (int a = 0; a < M; ++a) bij = fma(Lt[i * M + a], Lt[j * M + a], bij);
+        kC[i * N + j] = bij;
+      });
+  // dJ = A^T (Q A)
+  gemm<N, N, N, TEAM, double>(
+      lane, [&](int i, int l) { return A[l * N + i]; }, [&](int l, int j) { return QA[l * N + j]; },
+      [&](int i, int j, double s) { kJ[i * N + j] = s; });
+  // db = c + F b + C w ; deta = A^T w
+  for (int i = lane; i < N; i += TEAM) {
+    double s = c ? c[i] : 0.0, se = 0.0;
+    for (int l = 0; l < N; ++l) {
+      s = fma(F[i * N + l], b[l], s);
+      s = fma(C[i * N + l], w[l], s);
+      se = fma(A[l * N + i], w[l], se);
+    }
+    k.b()[i] = s;
+    k.eta()[i] = se;
+  }
+  if (lane == 0) {
+    double z = 0.5 * qr[N];
+    for (int i = 0; i < N; ++i) z = fma(-0.5 * b[i], w[i] + qr[i], z);
+    *k.zeta() = z;
+  }
+  sync<TEAM>();
+}
+
+// out1 = base1 + s1 k and out2 = base2 + s2 k over whole packed records (out1
+// may alias base1; out2 may not alias base1).
+template <int N, int TEAM>
+__device__ __forceinline__ void axpy2_rec(int lane, double* out1, const double* base1, double s1, double* out2,
+                                         const double* base2, double s2, const double* k) {
+  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) {
+    const double ke = k[e];
+    out1[e] = fma(s1, ke, base1[e]);
+    if (out2) out2[e] = fma(s2, ke, base2[e]);
+  }
+  sync<TEAM>();
+}
+
 // copy a record (any layout) to another
 template <int N, int TEAM>
 __device__ __forceinline__ void copy_rec(int lane, Rec<N> dst, Rec<N> src) {

@@ -24,6 +24,12 @@ CASES = [
     ("T1", lambda: W.general_time_varying(3, 1, 3, T=1, K=4, seed=26, tf=0.5)),
     ("T2", lambda: W.general_time_varying(2, 2, 2, T=2, K=1, seed=27)),
     ("T3", lambda: W.general_time_varying(4, 2, 4, T=3, K=2, seed=28)),
+    # n = 16 (one warp per element and per combination) and n = 64 (one CTA)
+    ("n16_m8_T40_general", lambda: W.general_time_varying(16, 8, 16, T=40, K=2, seed=81, tf=1.0)),
+    ("n16_batched_member_T300", lambda: W.batched_member(7, T=300, n=16)),
+    ("n16_m1_T3", lambda: W.general_time_varying(16, 1, 16, T=3, K=2, seed=82, tf=0.5)),
+    ("n64_m16_T64", lambda: W.large_state_n64(T=64)),
+    ("n64_m16_T129_ragged", lambda: W.large_state_n64(T=129)),
 ]
 IDS = [c[0] for c in CASES]
 
@@ -89,3 +95,20 @@ def test_method2_agrees_with_method1_at_full_size():
     assert lqt.lqt_get_status() == 0
     for k in ("S", "v", "zeta", "x", "u"):
         assert relerr(to_np(m2[k]), to_np(m1[k])) <= TOL, k
+
+
+def test_method2_n16_level0_chunks_of_four():
+    """n = 16 at T = 5000: the level-0 chunks hold 4 forward elements (the
+    fold inside a chunk runs 4 combinations), 1250 chunks with a ragged
+    prefix tree above them."""
+    import paper_2212_11744_gb300 as lqt
+    p = W.batched_member(7, T=5000, n=16)
+    sol = oracle.solve(p)
+    ref = oracle.trajectory_method2(p, sol["S"], sol["v"])
+    got = lqt.lqt_solve_method2(lqt.DeviceProblem(p))
+    torch.cuda.synchronize()
+    assert lqt.lqt_get_status() == 0
+    for k in ("S", "v", "zeta"):
+        assert relerr(to_np(got[k]), sol[k]) <= TOL, k
+    for k in ("x", "u"):
+        assert relerr(to_np(got[k]), ref[k]) <= TOL, k
