@@ -17,9 +17,11 @@
 //  * every thread converts its share of A and B (from FP64 storage) once and
 //    writes the three pieces into shared memory in the tensor core's K-major,
 //    unswizzled layout: 8-row x 16-byte core matrices, 128 contiguous bytes
-//    each; core matrices 2048 B apart along K and 128 B apart along M (A,
-//    padded to 128 rows whose last 64 stay zero) and 1024 B / 128 B for B
-//    (stored transposed, N x K);
+//    each, 1024 B apart along K and 128 B apart along M (A) or N (B, stored
+//    transposed, N x K).  The MMA's M is 128: rows 64..127 of A are read
+//    from the next 1024 bytes (the next K chunk, or for the last chunk of
+//    the last A piece the first B piece) and only produce rows 64..127 of D,
+//    which nothing reads, so A needs no zero padding;
 //  * one thread issues 8 x 6 MMAs of M = 128, N = 64, K = 8, K step s into its
 //    own 64 TMEM columns (all 512 of the SM's: one CTA per SM), and commits
 //    them to an mbarrier; every thread waits on it with an iteration limit (on
@@ -41,11 +43,13 @@ namespace tc {
 constexpr int kTeam = 256;
 constexpr int kSteps = 8;             // K = 64 in MMAs of K = 8
 constexpr int kCols = 64 * kSteps;    // TMEM columns: one 64-column accumulator per K step
-// shared memory: A's three pieces (128 x 64 floats each), B's (64 x 64 each),
-// from a 1024-byte boundary (the MMA composes a core matrix's row addresses
-// into the low address bits, so the operands must start 128-byte aligned; the
-// dynamic region itself is only guaranteed 16-byte alignment)
-constexpr int kAFloats = 128 * 64, kBFloats = 64 * 64;
+// shared memory: A's three pieces, then B's (64 x 64 floats each), from a
+// 1024-byte boundary (the MMA composes a core matrix's row addresses into the
+// low address bits, so the operands must start 128-byte aligned; the dynamic
+// region itself is only guaranteed 16-byte alignment).  B follows A, so the
+// unused rows 64..127 of the last A piece's last K chunk stay inside the
+// region.
+constexpr int kAFloats = 64 * 64, kBFloats = 64 * 64;
 constexpr size_t kSmemBytes = (3 * kAFloats + 3 * kBFloats) * sizeof(float) + 1024;
 constexpr unsigned kWaitLimit = 1u << 24;
 
@@ -73,9 +77,8 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Allocates the accumulator (warp 0), sets up the barrier and zeroes the
-// padding rows 64..127 of A; every thread of the CTA calls it once, before
-// any product.  `tmem_slot`, `bar`: this CTA's shared words; `smem`: kSmemBytes
+// Allocates the accumulator (warp 0) and sets up the barrier; every thread of
+// the CTA calls it once, before any product.  `tmem_slot`, `bar`: this CTA's shared words; `smem`: kSmemBytes
 // of dynamic shared memory, declared with no more than 16-byte alignment (with
 // relocatable device code the dynamic region starts wherever the static
 // variables end; a larger declared alignment would let the compiler fold the
@@ -88,13 +91,6 @@ __device__ __forceinline__ void init(Ctx& c, uint32_t* tmem_slot, unsigned long 
   c.b[0] = c.a[2] + kAFloats;
   c.b[1] = c.b[0] + kBFloats;
   c.b[2] = c.b[1] + kBFloats;
-  // rows 64..127 are the core matrices with M-group index 8..15 of every K chunk
-  for (int e = tid; e < kAFloats; e += kTeam)
-    if (((e >> 5) & 15) >= 8) {
-      c.a[0][e] = 0.0f;
-      c.a[1][e] = 0.0f;
-      c.a[2][e] = 0.0f;
-    }
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(tmem_slot)),
                  "n"(kCols)
@@ -152,17 +148,15 @@ __device__ __forceinline__ void gemm64(Ctx& c, FA a, FB b, FO out) {
   const int tid = threadIdx.x;
   // stage: consecutive threads fill consecutive floats of the core matrices
   for (int e = tid; e < 64 * 64; e += kTeam) {
-    // A, rows 0..63: e = ((kc * 8 + mg) * 8 + r) * 4 + kk within the first
-    // eight M groups of each K chunk; stored at ((kc * 16 + mg) * 8 + r) * 4 + kk
+    // e = ((kc * 8 + g) * 8 + r) * 4 + kk: K chunk kc (4 floats), row group g,
+    // row r within it; A row m = 8 g + r, and B^T (N x K) the same with n = m
     const int kk = e & 3, r = (e >> 2) & 7, mg = (e >> 5) & 7, kc = e >> 8;
     const int m = mg * 8 + r, k = kc * 4 + kk;
     float p0, p1, p2;
     split3(a(m, k), p0, p1, p2);
-    const int off = ((kc * 16 + mg) * 8 + r) * 4 + kk;
-    c.a[0][off] = p0;
-    c.a[1][off] = p1;
-    c.a[2][off] = p2;
-    // B^T (N x K): n = mg * 8 + r, the same index pattern with 8 N groups
+    c.a[0][e] = p0;
+    c.a[1][e] = p1;
+    c.a[2][e] = p2;
     split3(b(k, m), p0, p1, p2);
     c.b[0][e] = p0;
     c.b[1][e] = p1;
@@ -187,7 +181,7 @@ __device__ __forceinline__ void gemm64(Ctx& c, FA a, FB b, FO out) {
 #pragma unroll
       for (int pass = 0; pass < 6; ++pass) {
         const unsigned a0 = s32(c.a[pa[pass]]), b0 = s32(c.b[pb[pass]]);
-        mma(c.tmem + (uint32_t)(64 * s), smem_desc(a0 + s * 4096, 2048, 128), smem_desc(b0 + s * 2048, 1024, 128),
+        mma(c.tmem + (uint32_t)(64 * s), smem_desc(a0 + s * 2048, 1024, 128), smem_desc(b0 + s * 2048, 1024, 128),
             id, pass > 0 ? 1u : 0u);
       }
     }

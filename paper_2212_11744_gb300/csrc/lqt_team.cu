@@ -282,6 +282,25 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_forward_team_kernel(Te
 // The FP32 products of the n = 64 combinations run on the tensor core.
 template <int N, typename GT>
 constexpr bool kTensorProducts = (N == 64 && std::is_same<GT, float>::value);
+// The FP64 n = 64 combinations keep their scratch (W, R = [K1 | MC1 | z0],
+// T1, vectors; 131 KB) in dynamic shared memory: the 64 dependent pivot steps
+// of the LU then wait on shared memory instead of L2.
+template <int N, typename GT>
+constexpr bool kSharedScratch = (N == 64 && !kTensorProducts<N, GT>);
+template <int N>
+constexpr size_t kReduceSmemBytes = sizeof(double) * team::combine_scratch_doubles<N>();
+template <int N>
+constexpr size_t kDownSmemBytes = sizeof(double) * (team::value_scratch_doubles<N>() + N * N + N);
+// The tensor-core instances: the operand tiles, then W, R and the vectors
+// (and the map Psi, alpha in the down-sweep); T1 stays in the slot.
+template <int N>
+constexpr int kTcReduceScr = N * N + N * (2 * N + 1) + 4 * N;
+template <int N>
+constexpr int kTcDownScr = N * N + N * (N + 1) + 3 * N + N * N + N;
+template <int N>
+constexpr size_t kTcReduceSmemBytes = tc::kSmemBytes + sizeof(double) * kTcReduceScr<N>;
+template <int N>
+constexpr size_t kTcDownSmemBytes = tc::kSmemBytes + sizeof(double) * kTcDownScr<N>;
 
 struct TeamScanArgs {
   ElemPtrs el;           // level-0 elements (public layout)
@@ -318,6 +337,11 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
   double* bufA = base;
   double* bufB = bufA + Rec<N>::SIZE;
   double* scr = bufB + Rec<N>::SIZE;
+  double* t1 = nullptr;
+  if constexpr (kSharedScratch<N, GT>) {
+    extern __shared__ __align__(16) double scr_smem[];
+    scr = scr_smem;
+  }
   tc::Ctx* tcx = nullptr;
   tc::Ctx tc_ctx;
   if constexpr (kTensorProducts<N, GT>) {
@@ -326,6 +350,8 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
     __shared__ unsigned long long tc_bar;
     tc::init(tc_ctx, &tmem_slot, &tc_bar, tc_smem);
     tcx = &tc_ctx;
+    t1 = scr + N * N + N * (2 * N + 1);
+    scr = reinterpret_cast<double*>(tc_smem + tc::kSmemBytes);
   }
   team::sync<TEAM>();
   const int64_t groups = tdiv(a.cnt, a.G);
@@ -335,7 +361,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
     Rec<N> acc = Rec<N>::packed(bufA), nxt = Rec<N>::packed(bufB);
     team::copy_rec<N, TEAM>(lane, acc, level_elem<N>(a, last, &zero));
     for (int64_t k = last - 1; k >= first; --k) {
-      team::combine<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is, tcx);
+      team::combine<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is, tcx, t1);
       const Rec<N> t = acc;
       acc = nxt;
       nxt = t;
@@ -366,6 +392,15 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
   double* P = alpha + N;
   double* pv = P + N * N;
   double* Tm = pv + N;
+  double* t1 = nullptr;
+  if constexpr (kSharedScratch<N, GT>) {
+    // the combination's scratch and its map (Psi, alpha) in shared memory;
+    // the chunk composite (P, pv, Tm) stays in the slot
+    extern __shared__ __align__(16) double scr_smem[];
+    scr = scr_smem;
+    Psi = scr + team::value_scratch_doubles<N>();
+    alpha = Psi + N * N;
+  }
   tc::Ctx* tcx = nullptr;
   tc::Ctx tc_ctx;
   if constexpr (kTensorProducts<N, GT>) {
@@ -374,6 +409,10 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
     __shared__ unsigned long long tc_bar;
     tc::init(tc_ctx, &tmem_slot, &tc_bar, tc_smem);
     tcx = &tc_ctx;
+    t1 = scr + N * N + N * (N + 1);
+    scr = reinterpret_cast<double*>(tc_smem + tc::kSmemBytes);
+    Psi = scr + N * N + N * (N + 1) + 3 * N;
+    alpha = Psi + N * N;
   }
   team::sync<TEAM>();
   const int64_t groups = tdiv(a.cnt, a.G);
@@ -392,7 +431,7 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
     team::sync<TEAM>();
     for (int64_t k = last; k >= first; --k) {
       team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is, &zinc,
-                                       tcx);
+                                       tcx, t1);
       if (Level0) {
         bool ok = true;
         for (int e = lane; e < VS; e += TEAM) {
@@ -760,9 +799,10 @@ static void launch_reduce(const TeamScanArgs& a, int64_t groups, cudaStream_t st
                                                                          : TeamCfg<16>::SCAN_SLOTS),
                             32, kW16ReduceSmem * sizeof(double), st>>>(a, a.src == nullptr ? bulk_ok(a.el) : 0);
     count_launch();
-  } else if constexpr (kTensorProducts<N, GT>) {
-    cudaFuncSetAttribute(reduce_team_kernel<N, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes);
-    reduce_team_kernel<N, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, tc::kSmemBytes, st>>>(a);
+  } else if constexpr (kTensorProducts<N, GT> || kSharedScratch<N, GT>) {
+    const size_t smem = kTensorProducts<N, GT> ? kTcReduceSmemBytes<N> : kReduceSmemBytes<N>;
+    cudaFuncSetAttribute(reduce_team_kernel<N, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    reduce_team_kernel<N, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(a);
     count_launch();
   } else {
     team_launch<N>(reduce_team_kernel<N, GT>, groups, reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
@@ -776,11 +816,10 @@ static void launch_down(const TeamScanArgs& a, int64_t groups, cudaStream_t st) 
                                                                               : TeamCfg<16>::SCAN_SLOTS),
                                   32, kW16DownSmem * sizeof(double), st>>>(a, a.src == nullptr ? bulk_ok(a.el) : 0);
     count_launch();
-  } else if constexpr (kTensorProducts<N, GT>) {
-    cudaFuncSetAttribute(down_team_kernel<N, Level0, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tc::kSmemBytes);
-    down_team_kernel<N, Level0, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, tc::kSmemBytes,
-                                      st>>>(a);
+  } else if constexpr (kTensorProducts<N, GT> || kSharedScratch<N, GT>) {
+    const size_t smem = kTensorProducts<N, GT> ? kTcDownSmemBytes<N> : kDownSmemBytes<N>;
+    cudaFuncSetAttribute(down_team_kernel<N, Level0, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    down_team_kernel<N, Level0, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(a);
     count_launch();
   } else {
     team_launch<N>(down_team_kernel<N, Level0, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
@@ -1024,16 +1063,18 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM) method2_team_kernel(TeamM2Ar
   __shared__ unsigned long long bar;
   __shared__ double zero;
   const int lane = threadIdx.x;
-  double* base;
+  extern __shared__ __align__(16) double m2_smem[];
+  double *P, *Pn, *scr;
   if constexpr (N == 16) {
-    extern __shared__ __align__(16) double m2_smem[];
-    base = m2_smem;
+    P = m2_smem;
+    Pn = P + m2_rec_doubles<N>();
+    scr = Pn + m2_rec_doubles<N>();
   } else {
-    base = slot_base<N>(a.gscratch, m2_slot_doubles<N>());
+    // the records in the slot, the scratch (W, r, e included) in shared memory
+    P = slot_base<N>(a.gscratch, m2_slot_doubles<N>());
+    Pn = P + m2_rec_doubles<N>();
+    scr = m2_smem;
   }
-  double* P = base;
-  double* Pn = P + m2_rec_doubles<N>();
-  double* scr = Pn + m2_rec_doubles<N>();
   double* W = scr + m2_scratch_doubles<N>();
   double* r = W + N * N;
   double* ev = r + N;
@@ -1143,7 +1184,14 @@ static cudaError_t team_method2_n(const lqt_problem& p, const Coefs& cf, const E
   a.S = S; a.v = v; a.zeta = zeta; a.x0 = x0;
   a.Ku = cf.Ku; a.Ku_per_boundary = cf.Ku_per_boundary; a.m = p.m;
   a.x = x; a.u = u; a.cost = cost; a.gscratch = gs; a.bulk = bulk_ok(fwd);
-  team_launch<N>(method2_team_kernel<N>, tdiv(p.T, pl.G0), m2_slot_doubles<N>(), a, st);
+  if constexpr (N == 64) {
+    const size_t smem = sizeof(double) * (m2_scratch_doubles<N>() + N * N + 2 * N);
+    cudaFuncSetAttribute(method2_team_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    method2_team_kernel<N><<<team_grid<N>(tdiv(p.T, pl.G0)), TeamCfg<N>::TEAM, smem, st>>>(a);
+    count_launch();
+  } else {
+    team_launch<N>(method2_team_kernel<N>, tdiv(p.T, pl.G0), m2_slot_doubles<N>(), a, st);
+  }
   return cudaGetLastError();
 }
 

@@ -422,6 +422,9 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
           if (pivot_too_small(__longlong_as_double((long long)wb), rk_b)) flag(kStatusSingular);
           rks[wi] = rks[k];
           rks[k] = rk_b;
+          // 1 / pivot, once for the team (the elimination and the back
+          // substitution read it)
+          fscratch[TEAM + 64 + k] = 1.0 / W[wi * N + k];
         }
       }
       __syncthreads();
@@ -438,13 +441,12 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
       }
     }
     sync<TEAM>();
-    const double inv = 1.0 / W[k * N + k];
     const int wc = N - k - 1, cols = wc + Q;
     if constexpr (TEAM > 32) {
       // a CTA: warp w updates rows k+1+w, k+1+w+8, ..., forming each row's
       // multiplier itself (one instruction per row), the lanes over the
-      // row's columns; 1/pivot kept for the back substitution
-      if (lane == 0) fscratch[TEAM + 64 + k] = inv;
+      // row's columns
+      const double inv = fscratch[TEAM + 64 + k];
       const int warp = lane >> 5, wl = lane & 31;
       for (int i = k + 1 + warp; i < N; i += TEAM / 32) {
         const double f = W[i * N + k] * inv;
@@ -462,6 +464,7 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
       continue;
     }
     // multipliers into column k (below the diagonal)
+    const double inv = 1.0 / W[k * N + k];
     for (int i = k + 1 + lane; i < N; i += TEAM) W[i * N + k] *= inv;
     sync<TEAM>();
     // rank-1 update of the trailing rows
@@ -544,15 +547,17 @@ __host__ __device__ constexpr int combine_scratch_doubles() {
 
 // out = e1 (x) e2 (full elements; out must not alias e1 or e2).  The O(N^3)
 // products are register-blocked team products (gemm above); the symmetric
-// results J, C are formed in full and stored as (X + X^T)/2.
+// results J, C are formed in full and stored as (X + X^T)/2.  Scratch: W, R,
+// T1, vectors back to back at scr, or T1 at t1 (when given) and the rest at
+// scr.
 template <int N, int TEAM, typename G = double>
 __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr, double* fs, int* is,
-                        tc::Ctx* tcx = nullptr) {
+                        tc::Ctx* tcx = nullptr, double* t1 = nullptr) {
   constexpr int Q = 2 * N + 1;
   double* W = scr;
   double* R = W + N * N;
-  double* T1 = R + N * Q;
-  double* z0 = T1 + N * N;
+  double* T1 = t1 ? t1 : R + N * Q;
+  double* z0 = t1 ? R + N * Q : T1 + N * N;
   double* l0 = z0 + N;
   double* J2z = l0 + N;
   double* wv = J2z + N;
@@ -639,7 +644,8 @@ __device__ void combine(int lane, Rec<N> e1, Rec<N> e2, Rec<N> out, double* scr,
 
 // Value form: out = e (x) V, V = (S2 full N^2, v2 N, zeta2); also Psi (N^2) and
 // alpha (N) of the one-sub-interval map.  Value record layout: S (N^2), v (N),
-// zeta.  Scratch: W (N^2), R (N (N+1)), T1 (N^2), 3 vectors.
+// zeta.  Scratch: W (N^2), R (N (N+1)), T1 (N^2), 3 vectors (T1 at t1 when
+// given, as in combine()).
 template <int N>
 __host__ __device__ constexpr int value_scratch_doubles() {
   return N * N + N * (N + 1) + N * N + 3 * N;
@@ -652,15 +658,15 @@ __host__ __device__ constexpr int val_doubles() {
 template <int N, int TEAM, typename G = double>
 __device__ void combine_value(int lane, Rec<N> e, const double* V, double* out, double* Psi, double* alpha,
                               double* scr, double* fs, int* is, double* zeta_inc = nullptr,
-                              tc::Ctx* tcx = nullptr) {
+                              tc::Ctx* tcx = nullptr, double* t1 = nullptr) {
   constexpr int Q = N + 1;
   const double* S2 = V;
   const double* v2 = V + N * N;
   const double zeta2 = V[N * N + N];
   double* W = scr;
   double* R = W + N * N;
-  double* T1 = R + N * Q;
-  double* Sz = T1 + N * N;
+  double* T1 = t1 ? t1 : R + N * Q;
+  double* Sz = t1 ? R + N * Q : T1 + N * N;
   double* l0 = Sz + N;
   double* wv = l0 + N;
   const double* A = e.A();
