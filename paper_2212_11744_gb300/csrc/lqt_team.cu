@@ -287,10 +287,12 @@ constexpr bool kTensorProducts = (N == 64 && std::is_same<GT, float>::value);
 // of the LU then wait on shared memory instead of L2.
 template <int N, typename GT>
 constexpr bool kSharedScratch = (N == 64 && !kTensorProducts<N, GT>);
+// After the scratch: the A and C blocks of the element being combined, staged
+// by the TMA unit at level 0 (stage_ac).
 template <int N>
-constexpr size_t kReduceSmemBytes = sizeof(double) * team::combine_scratch_doubles<N>();
+constexpr size_t kReduceSmemBytes = sizeof(double) * (team::combine_scratch_doubles<N>() + 2 * N * N);
 template <int N>
-constexpr size_t kDownSmemBytes = sizeof(double) * (team::value_scratch_doubles<N>() + N * N + N);
+constexpr size_t kDownSmemBytes = sizeof(double) * (team::value_scratch_doubles<N>() + N * N + N + 2 * N * N);
 // The tensor-core instances: the operand tiles, then W, R and the vectors
 // (and the map Psi, alpha in the down-sweep); T1 stays in the slot.
 template <int N>
@@ -316,12 +318,37 @@ struct TeamScanArgs {
   int64_t T;
   double* gscratch;
   int zeta_inc;          // level 0 of a batch: zeta[k] receives the element's own share (see DownOut)
+  int bulk;              // FP64 n = 64, level 0: stage A, C of each element by TMA
 };
 
 template <int N>
 __device__ __forceinline__ Rec<N> level_elem(const TeamScanArgs& a, int64_t k, double* zero) {
   if (a.src) return Rec<N>::packed(const_cast<double*>(a.src) + k * Rec<N>::SIZE);
   return Rec<N>::pub(a.el, k, zero);
+}
+
+// Element k of the public arrays with its A and C blocks (N x N each, 32 KB at
+// n = 64) copied into shared memory sA, sC by the TMA unit (cp.async.bulk,
+// completion on the mbarrier `bar` with a bounded wait); every thread of the
+// CTA calls it after its last read of sA, sC.  The arrays must be 16-byte
+// aligned (bulk_ok).
+template <int N>
+__device__ __forceinline__ Rec<N> stage_ac(const ElemPtrs& el, int64_t k, double* sA, double* sC,
+                                           unsigned long long* bar, unsigned& phase, double* zero) {
+  constexpr unsigned kBytes = N * N * sizeof(double);
+  w16::fence_proxy_async();  // this thread's reads of sA, sC before the copies' writes
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    w16::mbar_expect_tx(bar, 2 * kBytes);
+    w16::bulk_g2s(sA, el.A + k * N * N, kBytes, bar);
+    w16::bulk_g2s(sC, el.C + k * N * N, kBytes, bar);
+  }
+  w16::mbar_wait_bounded(bar, phase);
+  phase ^= 1u;
+  Rec<N> e = Rec<N>::pub(el, k, zero);
+  e.a_ = sA;
+  e.c_ = sC;
+  return e;
 }
 
 template <int N, typename GT = double>
@@ -338,9 +365,15 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
   double* bufB = bufA + Rec<N>::SIZE;
   double* scr = bufB + Rec<N>::SIZE;
   double* t1 = nullptr;
+  double *sA = nullptr, *sC = nullptr;
+  __shared__ unsigned long long st_bar;
+  unsigned st_phase = 0;
   if constexpr (kSharedScratch<N, GT>) {
     extern __shared__ __align__(16) double scr_smem[];
     scr = scr_smem;
+    sA = scr + team::combine_scratch_doubles<N>();
+    sC = sA + N * N;
+    if (lane == 0) w16::mbar_init(&st_bar, 1);
   }
   tc::Ctx* tcx = nullptr;
   tc::Ctx tc_ctx;
@@ -361,7 +394,10 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) reduce
     Rec<N> acc = Rec<N>::packed(bufA), nxt = Rec<N>::packed(bufB);
     team::copy_rec<N, TEAM>(lane, acc, level_elem<N>(a, last, &zero));
     for (int64_t k = last - 1; k >= first; --k) {
-      team::combine<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), acc, nxt, scr, fs, is, tcx, t1);
+      Rec<N> e1 = level_elem<N>(a, k, &zero);
+      if constexpr (kSharedScratch<N, GT>)
+        if (a.bulk) e1 = stage_ac<N>(a.el, k, sA, sC, &st_bar, st_phase, &zero);
+      team::combine<N, TEAM, GT>(lane, e1, acc, nxt, scr, fs, is, tcx, t1);
       const Rec<N> t = acc;
       acc = nxt;
       nxt = t;
@@ -393,13 +429,19 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
   double* pv = P + N * N;
   double* Tm = pv + N;
   double* t1 = nullptr;
+  double *sA = nullptr, *sC = nullptr;
+  __shared__ unsigned long long st_bar;
+  unsigned st_phase = 0;
   if constexpr (kSharedScratch<N, GT>) {
-    // the combination's scratch and its map (Psi, alpha) in shared memory;
-    // the chunk composite (P, pv, Tm) stays in the slot
+    // the combination's scratch, its map (Psi, alpha) and the staged A, C in
+    // shared memory; the chunk composite (P, pv, Tm) stays in the slot
     extern __shared__ __align__(16) double scr_smem[];
     scr = scr_smem;
     Psi = scr + team::value_scratch_doubles<N>();
     alpha = Psi + N * N;
+    sA = alpha + N;
+    sC = sA + N * N;
+    if (lane == 0) w16::mbar_init(&st_bar, 1);
   }
   tc::Ctx* tcx = nullptr;
   tc::Ctx tc_ctx;
@@ -430,8 +472,10 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::SCAN_MIN) down_t
       }
     team::sync<TEAM>();
     for (int64_t k = last; k >= first; --k) {
-      team::combine_value<N, TEAM, GT>(lane, level_elem<N>(a, k, &zero), carry, nv, Psi, alpha, scr, fs, is, &zinc,
-                                       tcx, t1);
+      Rec<N> e = level_elem<N>(a, k, &zero);
+      if constexpr (kSharedScratch<N, GT>)
+        if (a.bulk) e = stage_ac<N>(a.el, k, sA, sC, &st_bar, st_phase, &zero);
+      team::combine_value<N, TEAM, GT>(lane, e, carry, nv, Psi, alpha, scr, fs, is, &zinc, tcx, t1);
       if (Level0) {
         bool ok = true;
         for (int e = lane; e < VS; e += TEAM) {
@@ -801,8 +845,10 @@ static void launch_reduce(const TeamScanArgs& a, int64_t groups, cudaStream_t st
     count_launch();
   } else if constexpr (kTensorProducts<N, GT> || kSharedScratch<N, GT>) {
     const size_t smem = kTensorProducts<N, GT> ? kTcReduceSmemBytes<N> : kReduceSmemBytes<N>;
+    TeamScanArgs b = a;
+    b.bulk = (kSharedScratch<N, GT> && a.src == nullptr) ? bulk_ok(a.el) : 0;
     cudaFuncSetAttribute(reduce_team_kernel<N, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    reduce_team_kernel<N, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(a);
+    reduce_team_kernel<N, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(b);
     count_launch();
   } else {
     team_launch<N>(reduce_team_kernel<N, GT>, groups, reduce_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
@@ -818,8 +864,10 @@ static void launch_down(const TeamScanArgs& a, int64_t groups, cudaStream_t st) 
     count_launch();
   } else if constexpr (kTensorProducts<N, GT> || kSharedScratch<N, GT>) {
     const size_t smem = kTensorProducts<N, GT> ? kTcDownSmemBytes<N> : kDownSmemBytes<N>;
+    TeamScanArgs b = a;
+    b.bulk = (kSharedScratch<N, GT> && a.src == nullptr) ? bulk_ok(a.el) : 0;
     cudaFuncSetAttribute(down_team_kernel<N, Level0, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    down_team_kernel<N, Level0, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(a);
+    down_team_kernel<N, Level0, GT><<<team_grid<N>(groups, TeamCfg<N>::SCAN_SLOTS), TeamCfg<N>::TEAM, smem, st>>>(b);
     count_launch();
   } else {
     team_launch<N>(down_team_kernel<N, Level0, GT>, groups, down_slot_doubles<N>(), a, st, TeamCfg<N>::SCAN_SLOTS);
