@@ -494,24 +494,16 @@ def measure_rows(T_headline, pk=None):
             rows[name] = {"error": repr(exc)[:300]}
 
     def batched():
-        from paper_2212_11744_gb300.batch import Batch
+        from paper_2212_11744_gb300.batch import BatchSet
         probs = [W.batched_member(b) for b in range(4096)]
-        byn = {}
-        for p in probs:
-            byn.setdefault(p.n, []).append(p)
-        bts = {n: Batch(v) for n, v in sorted(byn.items())}
+        bset = BatchSet(probs)
+        bts = bset.batches
         chunks = {n: bt.autotune(candidates=tune_candidates(n), reps=3 if n <= 8 else 2) for n, bt in bts.items()}
-        outs = {n: bt.new_outputs() for n, bt in bts.items()}
+        outs = bset.new_outputs()
         s = torch.cuda.Stream()
-        with torch.cuda.stream(s):
-            for n, bt in bts.items():
-                bt.solve(out=outs[n], stream=s)
+        bset.solve(outs, stream=s)
         torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                for n, bt in bts.items():
-                    bt.solve(out=outs[n], stream=s)
+        g = bset.capture(outs, stream=s)
         g.replay()
         torch.cuda.synchronize()
         ms = _events_ms(g.replay, 2)
@@ -520,14 +512,14 @@ def measure_rows(T_headline, pk=None):
         subs_n = {n: int(bt.T.sum()) for n, bt in bts.items()}
         st = lqt.lqt_get_status()
         flop = sum(alg_solve(n, max(1, n // 2), 4) * subs_n[n] for n in bts)
-        rl = roofline("the four batched solves (one CUDA graph)", flop / total,
+        rl = roofline("the four batched solves (one CUDA graph, one stream per n)", flop / total,
                       "sum over n of K (40 n^3 + 60 n^2) + 22 n^3 + 9 n^3 + 2 m n per sub-interval, averaged",
                       total, ms, pk)
         rl["per_n"] = {str(n): roofline(f"lqt_solve_batched n={n}", alg_solve(n, max(1, n // 2), 4),
                                         "K (40 n^3 + 60 n^2) + 22 n^3 + 9 n^3 + 2 m n", subs_n[n], per[str(n)], pk)
                        for n in bts}
         return {"workload": "4096 LQT problems, n in {2,4,8,16} (m = n/2), T in [256, 8192], K = 4, one CUDA graph "
-                            "of four batched solves (one per n)",
+                            "of four batched solves (one per n, each on its own stream)",
                 "value": total / (ms * 1e-3), "unit": UNIT, "ms": ms, "sub_intervals": total,
                 "per_n_ms": per, "per_n_count": {str(n): bt.B for n, bt in bts.items()},
                 "per_n_sub_intervals": {str(n): v for n, v in subs_n.items()},
@@ -692,26 +684,17 @@ def measure_rows(T_headline, pk=None):
         """The 4096-problem batch and the n = 64 problem with the time-invariant
         element build (every problem there has constant F, L, U, X and a uniform
         grid)."""
-        from paper_2212_11744_gb300.batch import Batch
+        from paper_2212_11744_gb300.batch import BatchSet
         probs = [W.batched_member(b) for b in range(4096)]
-        byn = {}
-        for p in probs:
-            byn.setdefault(p.n, []).append(p)
-        bts = {n: Batch(v) for n, v in sorted(byn.items())}
-        for bt in bts.values():
-            bt.set_invariant_build(True)
+        bset = BatchSet(probs)
+        bts = bset.batches
+        bset.set_invariant_build(True)
         chunks = {n: bt.autotune(candidates=tune_candidates(n), reps=3) for n, bt in bts.items()}
-        outs = {n: bt.new_outputs() for n, bt in bts.items()}
+        outs = bset.new_outputs()
         s = torch.cuda.Stream()
-        with torch.cuda.stream(s):
-            for n, bt in bts.items():
-                bt.solve(out=outs[n], stream=s)
+        bset.solve(outs, stream=s)
         torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                for n, bt in bts.items():
-                    bt.solve(out=outs[n], stream=s)
+        g = bset.capture(outs, stream=s)
         g.replay()
         torch.cuda.synchronize()
         ms = _events_ms(g.replay, 2)
@@ -731,7 +714,7 @@ def measure_rows(T_headline, pk=None):
                "tuning_ms": {str(n): {str(c): t for c, t in bt.tuned_timings().items()} for n, bt in bts.items()},
                "status": lqt.lqt_get_status(), "roofline": rl,
                "cpu_baseline": "as a4 (the oracle's general element build is the reference of this build)"}
-        del bts, outs, g
+        del bts, bset, outs, g
         p = W.large_state_n64(T=1 << 16)
         dp = lqt.DeviceProblem(p)
         try:

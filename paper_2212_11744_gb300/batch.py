@@ -4,6 +4,11 @@
     out = b.solve()                # concatenated S, v, zeta, x, u and per-problem cost
     b.autotune()                   # picks the first-level chunk length by timing
 
+    s = BatchSet(problems)         # problems of several state dimensions
+    s.autotune()                   # each dimension's batch tuned on its own
+    g = s.capture(out)             # one CUDA graph: the dimensions' solves on
+    g.replay()                     # concurrent streams, forked and joined
+
 Marshalling only: the per-problem arrays of a batch are packed into a few
 device tensors and the C descriptors point into them.
 """
@@ -149,3 +154,66 @@ class Batch:
     @staticmethod
     def tuning_table():
         return dict(_TUNED)
+
+
+class BatchSet:
+    """Problems of several state dimensions: one Batch per dimension, solved on
+    one stream each (forked from and joined back into the caller's stream), so
+    that one dimension's short upper scan levels overlap the others' work;
+    capture() records the whole set as one CUDA graph."""
+
+    def __init__(self, problems, device: str = "cuda"):
+        if not problems:
+            raise ValueError("empty batch")
+        self.device = torch.device(device)
+        idx = {}
+        for i, p in enumerate(problems):
+            idx.setdefault(p.n, []).append(i)
+        self.index = {n: v for n, v in sorted(idx.items())}
+        self.batches = {n: Batch([problems[i] for i in v], device) for n, v in self.index.items()}
+        self.streams = {n: torch.cuda.Stream(self.device) for n in self.batches}
+
+    def set_invariant_build(self, on: bool = True):
+        for b in self.batches.values():
+            b.set_invariant_build(on)
+
+    def autotune(self, candidates=None, reps: int = 3) -> dict:
+        """Each dimension's first-level chunk (Batch.autotune); `candidates`
+        maps a dimension to its candidate list (None: Batch's default)."""
+        out = {}
+        for n, b in self.batches.items():
+            c = candidates(n) if callable(candidates) else candidates
+            out[n] = b.autotune(reps=reps) if c is None else b.autotune(candidates=c, reps=reps)
+        return out
+
+    def new_outputs(self) -> dict:
+        return {n: b.new_outputs() for n, b in self.batches.items()}
+
+    def solve(self, out=None, stream=None) -> dict:
+        out = self.new_outputs() if out is None else out
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
+        for n, b in self.batches.items():
+            s = self.streams[n]
+            s.wait_stream(main)
+            b.solve(out=out[n], stream=s)
+        for s in self.streams.values():
+            main.wait_stream(s)
+        return out
+
+    def capture(self, out=None, stream=None):
+        """Records solve() as one CUDA graph (run solve() once before, so that
+        nothing is first touched inside the capture); returns the graph."""
+        out = self.new_outputs() if out is None else out
+        main = torch.cuda.Stream(self.device) if stream is None else stream
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(main):
+            with torch.cuda.graph(g, stream=main):
+                self.solve(out, stream=main)
+        return g
+
+    def problem_slice(self, out, i):
+        """Problem i (position in the constructor's list) of the outputs."""
+        for n, v in self.index.items():
+            if i in v:
+                return self.batches[n].problem_slice(out[n], v.index(i))
+        raise IndexError(i)

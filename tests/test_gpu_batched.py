@@ -64,6 +64,40 @@ def test_batch_chunk_choices_agree_and_graph_replay():
             assert torch.equal(o[k], ref[k]), (bt.n, k)
 
 
+def test_batch_set_streams_and_graph_match_direct_solves():
+    """Problems of four state dimensions, interleaved, through BatchSet: one
+    batch per dimension on its own stream, forked from and joined back into
+    the caller's stream; the solution of every problem against the oracle,
+    and the set captured as one CUDA graph and replayed bit-identical."""
+    from paper_2212_11744_gb300.batch import BatchSet
+    probs = [W.batched_member(b, T=90 + 13 * b, n=(2, 4, 8, 16)[b % 4]) for b in range(8)]
+    bset = BatchSet(probs)
+    assert sorted(bset.batches) == [2, 4, 8, 16]
+    s = torch.cuda.Stream()
+    out = bset.solve(stream=s)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        ref = oracle.solve(p)
+        got = bset.problem_slice(out, i)
+        for k in ("S", "v", "zeta", "x", "u"):
+            assert rel(got[k].cpu().numpy(), ref[k]) <= TOL, (i, p.n, k)
+        assert abs(float(got["cost"]) - ref["cost"]) <= TOL * max(1.0, abs(ref["cost"])), i
+    replay = bset.new_outputs()
+    bset.solve(replay, stream=s)
+    torch.cuda.synchronize()
+    g = bset.capture(replay, stream=s)
+    for o in replay.values():
+        for v in o.values():
+            v.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    import paper_2212_11744_gb300 as lqt
+    assert lqt.lqt_get_status() == 0
+    for n in out:
+        for k in ("S", "v", "zeta", "x", "u", "cost"):
+            assert torch.equal(replay[n][k], out[n][k]), (n, k)
+
+
 def test_short_chunk_override_on_a_batch_whose_default_is_longer():
     """A batch large enough that the built-in first-level chunk is > 2, solved
     with every allowed chunk (the workspace must cover the shortest), checked
