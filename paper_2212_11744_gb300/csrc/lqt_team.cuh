@@ -151,14 +151,34 @@ struct Rec {
 // element build right-hand side (factor form, see build_kernel)
 // ---------------------------------------------------------------------------
 
+// Sum of x over the S consecutive lanes of an aligned group (S a power of two
+// <= 32); every lane of the warp calls it.
+template <int S>
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+  for (int o = S / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Lanes per output when `outputs` sums are spread over a team: the largest
+// power of two <= team / outputs, at most a warp.
+__host__ __device__ constexpr int split_lanes(int outputs, int team) {
+  int s = 1;
+  while (2 * s * outputs <= team && 2 * s <= 32) s *= 2;
+  return s;
+}
+
 // k = f(y) for the flow fields (A, eta, J); the quadrature fields' rates
 // (db, dC, dzeta: nothing reads b, C or zeta) are added, times the RK4 weight
 // sq, straight into qacc's b, C, zeta, in the order the four-stage sum takes
-// them.  y and k may be flow records.  Scratch: AL, P (N x M), w (M).  Plain
-// loops, one output per thread at a time, with the symmetric C, J formed on
-// their upper triangles: measured faster here than the register-blocked team
-// products (the products are thin, inner length M, and the triangles halve the
-// C and J work).
+// them.  y and k may be flow records.  Scratch: AL, P (N x M), w (M).
+// Outputs that fill the team (AL, P, dA and whole passes of the C, J upper
+// triangles) take one thread each; outputs fewer than the team (w, db, deta,
+// the last partial pass of C and J, dzeta) have each sum spread over a group
+// of lanes, strided terms, and the group's partial sums added by shuffles,
+// so that every lane issues FP64 work: on this GPU a warp's FP64 instruction
+// costs its sub-partition the same 64 cycles whatever the active lanes.  The
+// symmetric C, J are formed on their upper triangles.
 template <int N, int M, int TEAM>
 __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
                     const double* __restrict__ Lt, const double* __restrict__ Q, const double* __restrict__ qr,
@@ -166,7 +186,6 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
   const double* A = y.A();
   const double* J = y.J();
   const double* eta = y.eta();
-  // One loop per output kind (a warp's lanes then run the same code).
   for (int e = lane; e < N * M; e += TEAM) {
     const int i = e / M, a = e % M;
     double s1 = 0.0, s2 = 0.0;
@@ -177,10 +196,14 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
     AL[e] = s1;
     P[e] = s2;
   }
-  for (int a = lane; a < M; a += TEAM) {
+  {  // w = Lt^T eta
+    constexpr int S = split_lanes(M, TEAM);
+    const int o = lane / S, sub = lane % S;
     double s = 0.0;
-    for (int l = 0; l < N; ++l) s = fma(Lt[l * M + a], eta[l], s);
-    w[a] = s;
+    if (o < M)
+      for (int l = sub; l < N; l += S) s = fma(Lt[l * M + o], eta[l], s);
+    s = group_sum<S>(s);
+    if (sub == 0 && o < M) w[o] = s;
   }
   sync<TEAM>();
   constexpr int NS = N * (N + 1) / 2;
@@ -192,24 +215,34 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
     for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
     k.A()[t] = s;
   }
-  // db = -AL w - A c ; deta = -q - F^T eta + J c + P w
-  for (int t = lane; t < N; t += TEAM) {
-    double s = 0.0, se = -qr[t];
-    for (int a = 0; a < M; ++a) {
-      s = fma(-AL[t * M + a], w[a], s);
-      se = fma(P[t * M + a], w[a], se);
-    }
-    for (int l = 0; l < N; ++l) se = fma(-F[l * N + t], eta[l], se);
-    if (c)
-      for (int l = 0; l < N; ++l) {
-        s = fma(-A[t * N + l], c[l], s);
-        se = fma(J[t * N + l], c[l], se);
+  {  // db = -AL w - A c ; deta = -q - F^T eta + J c + P w
+    constexpr int S = split_lanes(N, TEAM);
+    const int o = lane / S, sub = lane % S;
+    double s = 0.0, se = 0.0;
+    if (o < N) {
+      if (sub == 0) se = -qr[o];
+      for (int a = sub; a < M; a += S) {
+        s = fma(-AL[o * M + a], w[a], s);
+        se = fma(P[o * M + a], w[a], se);
       }
-    qacc.b()[t] = fma(sq, s, qacc.b()[t]);
-    k.eta()[t] = se;
+      for (int l = sub; l < N; l += S) se = fma(-F[l * N + o], eta[l], se);
+      if (c)
+        for (int l = sub; l < N; l += S) {
+          s = fma(-A[o * N + l], c[l], s);
+          se = fma(J[o * N + l], c[l], se);
+        }
+    }
+    s = group_sum<S>(s);
+    se = group_sum<S>(se);
+    if (sub == 0 && o < N) {
+      qacc.b()[o] = fma(sq, s, qacc.b()[o]);
+      k.eta()[o] = se;
+    }
   }
-  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored)
-  for (int t = lane; t < NS; t += TEAM) {
+  // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored):
+  // whole passes one entry per thread, the remainder spread over lane groups
+  constexpr int NSF = NS - NS % TEAM;
+  for (int t = lane; t < NSF; t += TEAM) {
     int i, j;
     upper_ij(N, t, i, j);
     double sc = 0.0, sj = -Q[i * N + j];
@@ -227,12 +260,41 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
     k.J()[i * N + j] = sj;
     k.J()[j * N + i] = sj;
   }
-  if (lane == 0) {  // dzeta (O(M + N))
-    double z = -0.5 * qr[N];
-    for (int a = 0; a < M; ++a) z = fma(0.5 * w[a], w[a], z);
+  if constexpr (NS % TEAM != 0) {
+    constexpr int R = NS % TEAM;
+    constexpr int S = split_lanes(R, TEAM);
+    const int o = lane / S, sub = lane % S;
+    int i = 0, j = 0;
+    double sc = 0.0, sj = 0.0;
+    if (o < R) {
+      upper_ij(N, NSF + o, i, j);
+      if (sub == 0) sj = -Q[i * N + j];
+      for (int a = sub; a < M; a += S) {
+        sc = fma(-AL[i * M + a], AL[j * M + a], sc);
+        sj = fma(P[i * M + a], P[j * M + a], sj);
+      }
+      for (int l = sub; l < N; l += S) {
+        sj = fma(-J[i * N + l], F[l * N + j], sj);
+        sj = fma(-J[j * N + l], F[l * N + i], sj);
+      }
+    }
+    sc = group_sum<S>(sc);
+    sj = group_sum<S>(sj);
+    if (sub == 0 && o < R) {
+      const double cn = fma(sq, sc, qacc.C()[i * N + j]);
+      qacc.C()[i * N + j] = cn;
+      qacc.C()[j * N + i] = cn;
+      k.J()[i * N + j] = sj;
+      k.J()[j * N + i] = sj;
+    }
+  }
+  if (lane < 32) {  // dzeta = -rho/2 + |w|^2/2 + eta^T c, over the first warp
+    double z = 0.0;
+    for (int a = lane; a < M; a += 32) z = fma(0.5 * w[a], w[a], z);
     if (c)
-      for (int l = 0; l < N; ++l) z = fma(eta[l], c[l], z);
-    *qacc.zeta() = fma(sq, z, *qacc.zeta());
+      for (int l = lane; l < N; l += 32) z = fma(eta[l], c[l], z);
+    z = group_sum<32>(z);
+    if (lane == 0) *qacc.zeta() = fma(sq, z - 0.5 * qr[N], *qacc.zeta());
   }
   sync<TEAM>();
 }
