@@ -810,6 +810,7 @@ cudaError_t launch_build_stages_range(const lqt_problem& p, const Layout& lay, c
                                       int64_t cnt, double* stages, cudaStream_t st, const ElemPtrs& out) {
   BuildArgs a{};
   a.T = cnt; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
+  if (team_build_preferred(p.n, cnt)) return team_launch_build_small(p, lay, cf, j0, cnt, stages, out, st);
   switch (p.n) {
     case 1: return launch_build_n<1>(a, lay.M, st, stages, j0);
     case 2: return launch_build_n<2>(a, lay.M, st, stages, j0);
@@ -840,6 +841,11 @@ cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& c
   BuildArgs a;
   a.T = p.T; a.K = p.K; a.t = p.t; a.cf = cf; a.out = out;
   cudaError_t e;
+  if (team_build_preferred(p.n, p.T)) {
+    e = team_launch_build_small(p, lay, cf, 0, p.T, nullptr, out, st);
+    if (e != cudaSuccess) return e;
+    return launch_terminal_element(p, out, st);
+  }
   switch (p.n) {
     case 1: e = launch_build_n<1>(a, lay.M, st); break;
     case 2: e = launch_build_n<2>(a, lay.M, st); break;

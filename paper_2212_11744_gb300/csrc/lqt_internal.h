@@ -108,6 +108,11 @@ cudaError_t launch_build(const lqt_problem& p, const Layout& lay, const Coefs& c
                          cudaStream_t s, double* team_scratch = nullptr);
 // n = 16, 64 (team kernels, lqt_team.cu)
 size_t team_build_scratch_bytes(int n);
+// n = 4, 8 at short horizons: one warp per element (elements j0 .. j0 + cnt - 1,
+// optional RK4 stage inputs as launch_build_stages_range); where it pays
+bool team_build_preferred(int n, int64_t count);
+cudaError_t team_launch_build_small(const lqt_problem& p, const Layout& lay, const Coefs& cf, int64_t j0,
+                                    int64_t cnt, double* stages, const ElemPtrs& out, cudaStream_t st);
 size_t team_scan_workspace_bytes(int32_t n, int64_t T, bool with_traj);
 cudaError_t team_launch_build(const lqt_problem& p, const Layout& lay, const Coefs& cf, const ElemPtrs& out,
                               double* gscratch, cudaStream_t st);

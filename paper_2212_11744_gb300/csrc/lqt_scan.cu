@@ -507,11 +507,13 @@ static ScanPlan make_plan(int64_t T, bool with_traj) {
 // over its lanes, shortening the dependent FP64 chain); larger levels run one
 // thread per pair (throughput-bound: a thread-per-pair warp instruction
 // serves 32 combinations).  Both read and write the same full-matrix records.
+// A thread's chain grows as n^3 (~5 k FP64 instructions at n = 8, ~155 us at
+// 64 cycles each, against ~0.6 k at n = 4), so the crossing moves up with n.
 // For n <= 3 a thread's combination is already short, and the warp version
 // is not faster at any level size.
 template <int N>
 constexpr int64_t team_level_below() {
-  return N >= 4 ? 2048 : 0;
+  return N >= 8 ? 8192 : (N >= 4 ? 2048 : 0);
 }
 
 // Level 0 (chunks of G0 elements, one thread each, register-resident) and the

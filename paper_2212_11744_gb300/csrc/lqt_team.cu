@@ -113,17 +113,40 @@ struct TeamBuildArgs {
   double* gscratch;
 };
 
+// One RK4 stage input in the full layout (A, b, C, eta, J, zeta) at dst: a
+// packed record whole, a flow record's A, eta, J with b, C, zeta as zero (the
+// discrete adjoint reads only A, eta, J of a stage input).
+template <int N, int TEAM>
+__device__ void store_stage(int lane, double* dst, Rec<N> src, bool full) {
+  for (int e = lane; e < Rec<N>::SIZE; e += TEAM) {
+    double v;
+    if (e < N * N) v = src.A()[e];
+    else if (e < N * N + N) v = full ? src.b()[e - N * N] : 0.0;
+    else if (e < 2 * N * N + N) v = full ? src.C()[e - N * N - N] : 0.0;
+    else if (e < 2 * N * N + 2 * N) v = src.eta()[e - 2 * N * N - N];
+    else if (e < 3 * N * N + 2 * N) v = src.J()[e - 2 * N * N - 2 * N];
+    else v = full ? *src.zeta() : 0.0;
+    dst[e] = v;
+  }
+  team::sync<TEAM>();
+}
+
 // Element j of a problem (coefficients cf, grid t) into the packed record at
-// yb; the other buffers are scratch.
+// yb; the other buffers are scratch.  With `stages`, the four stage inputs of
+// RK4 step i go to stages + (i 4 + s) (3N^2 + 2N + 1), s = 0..3, in the full
+// layout.
 template <int N, int M>
 __device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64_t j, int32_t K, double* yb,
-                               double* ynb, double* ytb, double* kb, double* AL, double* P, double* w) {
+                               double* ynb, double* ytb, double* kb, double* AL, double* P, double* w,
+                               double* stages = nullptr) {
   constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int FS = Rec<N>::SIZE;
   const Rec<N> y = Rec<N>::packed(yb), yn = Rec<N>::flow(ynb), yt = Rec<N>::flow(ytb), k = Rec<N>::flow(kb);
   const double h = (t[j + 1] - t[j]) / K;
   for (int e = lane; e < Rec<N>::SIZE; e += TEAM) yb[e] = (e < N * N && e % (N + 1) == 0) ? 1.0 : 0.0;
   team::sync<TEAM>();
   for (int32_t i = K - 1; i >= 0; --i) {
+    double* st = stages ? stages + (int64_t)i * 4 * FS : nullptr;
     const int32_t ps[3] = {2 * i + 2, 2 * i + 1, 2 * i};
     const double *F[3], *c[3], *Lt[3], *Q[3], *qr[3];
     for (int q = 0; q < 3; ++q) {
@@ -135,15 +158,19 @@ __device__ void team_build_one(int lane, const Coefs& cf, const double* t, int64
     }
     // (A, eta, J) by classical RK4 through yn and yt; b, C, zeta accumulated
     // into y by the right-hand side
+    if (st) store_stage<N, TEAM>(lane, st, y, true);
     team::rhs<N, M, TEAM>(lane, y, k, F[0], c[0], Lt[0], Q[0], qr[0], AL, P, w, -h / 6.0, y);
     team::axpy_flow<N, TEAM>(lane, yn, y, -h / 6.0, k);
     team::axpy_flow<N, TEAM>(lane, yt, y, -0.5 * h, k);
+    if (st) store_stage<N, TEAM>(lane, st + FS, yt, false);
     team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w, -h / 3.0, y);
     team::axpy_flow<N, TEAM>(lane, yn, yn, -h / 3.0, k);
     team::axpy_flow<N, TEAM>(lane, yt, y, -0.5 * h, k);
+    if (st) store_stage<N, TEAM>(lane, st + 2 * FS, yt, false);
     team::rhs<N, M, TEAM>(lane, yt, k, F[1], c[1], Lt[1], Q[1], qr[1], AL, P, w, -h / 3.0, y);
     team::axpy_flow<N, TEAM>(lane, yn, yn, -h / 3.0, k);
     team::axpy_flow<N, TEAM>(lane, yt, y, -h, k);
+    if (st) store_stage<N, TEAM>(lane, st + 3 * FS, yt, false);
     team::rhs<N, M, TEAM>(lane, yt, k, F[2], c[2], Lt[2], Q[2], qr[2], AL, P, w, -h / 6.0, y);
     team::axpy_flow<N, TEAM>(lane, y, yn, -h / 6.0, k);
   }
@@ -167,6 +194,36 @@ __global__ void __launch_bounds__(TeamCfg<N>::TEAM, TeamCfg<N>::BUILD_MIN) build
     double zz = 0.0;
     Rec<N> dst = Rec<N>::pub(a.out, j, &zz);
     team::copy_rec<N, TEAM>(lane, dst, Rec<N>::packed(yb));
+  }
+}
+
+// Elements j0 .. j0 + a.T - 1 with one warp each, for n = 4 and 8 at short
+// horizons: one thread per element then leaves most sub-partitions without a
+// warp, and each warp's chain of FP64 instructions (64 cycles apiece) is a
+// whole element's; a warp per element spreads each right-hand side over its
+// lanes.  With `stages`, the stage inputs of element j0 + jj go to
+// stages + jj K 4 (3N^2 + 2N + 1); the element is stored when a.out.A is set.
+template <int N, int M>
+__global__ void __launch_bounds__(TeamCfg<N>::TEAM) build_team_range_kernel(TeamBuildArgs a, int64_t j0,
+                                                                            double* stages) {
+  constexpr int TEAM = TeamCfg<N>::TEAM;
+  constexpr int SD = build_slot_doubles<N, M>();
+  const int lane = threadIdx.x;
+  double* base = slot_base<N>(a.gscratch, SD);
+  double* yb = base;
+  double* ynb = yb + Rec<N>::SIZE;
+  double* ytb = ynb + Rec<N>::FLOW;
+  double* kb = ytb + Rec<N>::FLOW;
+  double* AL = kb + Rec<N>::FLOW;
+  double* P = AL + N * M;
+  double* w = P + N * M;
+  for (int64_t jj = blockIdx.x; jj < a.T; jj += gridDim.x) {
+    team_build_one<N, M>(lane, a.cf, a.t, j0 + jj, a.K, yb, ynb, ytb, kb, AL, P, w,
+                         stages ? stages + jj * (int64_t)a.K * 4 * Rec<N>::SIZE : nullptr);
+    if (a.out.A) {
+      double zz = 0.0;
+      team::copy_rec<N, TEAM>(lane, Rec<N>::pub(a.out, j0 + jj, &zz), Rec<N>::packed(yb));
+    }
   }
 }
 
@@ -820,12 +877,12 @@ static unsigned team_grid(int64_t work, int64_t s = TeamCfg<N>::SLOTS) {
   return (unsigned)(work < s ? (work > 0 ? work : 1) : s);
 }
 
-template <int N, class Kern, class Args>
+template <int N, class Kern, class Args, class... More>
 static void team_launch(Kern k, int64_t work, size_t smem_doubles, const Args& a, cudaStream_t st,
-                        int64_t slots = TeamCfg<N>::SLOTS) {
+                        int64_t slots = TeamCfg<N>::SLOTS, More... more) {
   const size_t smem = TeamCfg<N>::SMEM ? smem_doubles * sizeof(double) : 0;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<team_grid<N>(work, slots), TeamCfg<N>::TEAM, smem, st>>>(a);
+  k<<<team_grid<N>(work, slots), TeamCfg<N>::TEAM, smem, st>>>(a, more...);
   count_launch();
 }
 
@@ -1531,6 +1588,45 @@ size_t team_build_scratch_bytes(int n) {
     return tal((size_t)TeamCfg<64>::SLOTS * sd * sizeof(double));
   }
   return 0;
+}
+
+bool team_build_preferred(int n, int64_t count) {
+  // where one warp per element beats one thread (measured crossing points)
+  return (n == 4 && count < 4096) || (n == 8 && count < 24576);
+}
+
+template <int N, int M>
+static cudaError_t team_range_nm(const lqt_problem& p, const Coefs& cf, int64_t j0, int64_t cnt, double* stages,
+                                 const ElemPtrs& out, cudaStream_t st) {
+  TeamBuildArgs a{cnt, p.K, p.t, cf, out, nullptr};
+  // <= 120 registers and <= 6 KB of shared memory per warp: four warps per
+  // sub-partition
+  team_launch<N>(build_team_range_kernel<N, M>, cnt, build_slot_doubles<N, M>(), a, st, (int64_t)152 * 16, j0,
+                 stages);
+  return cudaGetLastError();
+}
+
+cudaError_t team_launch_build_small(const lqt_problem& p, const Layout& lay, const Coefs& cf, int64_t j0,
+                                    int64_t cnt, double* stages, const ElemPtrs& out, cudaStream_t st) {
+  if (cnt <= 0) return cudaSuccess;
+  switch (p.n) {
+    case 4:
+      switch (lay.M) {
+        case 1: return team_range_nm<4, 1>(p, cf, j0, cnt, stages, out, st);
+        case 2: return team_range_nm<4, 2>(p, cf, j0, cnt, stages, out, st);
+        case 4: return team_range_nm<4, 4>(p, cf, j0, cnt, stages, out, st);
+        default: return cudaErrorInvalidValue;
+      }
+    case 8:
+      switch (lay.M) {
+        case 1: return team_range_nm<8, 1>(p, cf, j0, cnt, stages, out, st);
+        case 2: return team_range_nm<8, 2>(p, cf, j0, cnt, stages, out, st);
+        case 4: return team_range_nm<8, 4>(p, cf, j0, cnt, stages, out, st);
+        case 8: return team_range_nm<8, 8>(p, cf, j0, cnt, stages, out, st);
+        default: return cudaErrorInvalidValue;
+      }
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 size_t team_scan_workspace_bytes(int32_t n, int64_t T, bool with_traj) {
