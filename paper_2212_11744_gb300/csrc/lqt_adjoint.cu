@@ -542,6 +542,23 @@ __device__ __forceinline__ void mmt(int lane, int n, const double* a, const doub
   }
   sync();
 }
+// c += a b or c -= a b, with a and / or b read transposed (TA, TB): the
+// product accumulated onto c's entries directly (no temporary, no separate
+// pass of adds).
+template <bool TA, bool TB, bool SUB>
+__device__ __forceinline__ void mm_acc(int lane, int n, const double* a, const double* b, double* c) {
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e % n;
+    double s = c[e];
+    for (int l = 0; l < n; ++l) {
+      const double av = TA ? a[l * n + i] : a[i * n + l];
+      const double bv = TB ? b[j * n + l] : b[l * n + j];
+      s = fma(SUB ? -av : av, bv, s);
+    }
+    c[e] = s;
+  }
+  sync();
+}
 // y = a x, y = a^T x (n <= 8): four lanes per output, each summing every
 // fourth column, then two butterfly steps, so that the warp's FP64
 // instructions run with all lanes rather than n of them.
@@ -606,19 +623,14 @@ __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const
   mm(lane, n, B, Y.J, t.t1);  // G = B J
   for (int e = lane; e < nn; e += 32) t.t2[e] = t.t1[e] - F[e];
   sync();
-  mmt(lane, n, Kb.A, t.t2, t.t3);
-  for (int e = lane; e < nn; e += 32) YB.A[e] += t.t3[e];
-  sync();
+  mm_acc<false, true, false>(lane, n, Kb.A, t.t2, YB.A);
   mtm(lane, n, Y.A, Kb.A, t.t3);  // Gbar
   for (int e = lane; e < nn; e += 32) Fb[e] -= t.t3[e];
   sync();
-  mmt(lane, n, t.t3, Y.J, t.t2);
-  for (int e = lane; e < nn; e += 32) Bb[e] += t.t2[e];
-  sync();
-  mtm(lane, n, B, t.t3, t.t2);
+  mm_acc<false, true, false>(lane, n, t.t3, Y.J, Bb);
+  mm_acc<true, false, false>(lane, n, B, t.t3, YB.J);
   for (int e = lane; e < nn; e += 32) {
     const int i = e / n, c = e % n;
-    YB.J[e] += t.t2[e];
     YB.A[e] -= Kb.b[i] * t.beta[c];
   }
   sync();
@@ -628,10 +640,9 @@ __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const
   mm(lane, n, t.t2, B, t.t3);
   for (int e = lane; e < nn; e += 32) YB.A[e] -= 2.0 * t.t3[e];
   sync();
-  mtm(lane, n, Y.A, t.t2, t.t3);
+  mm_acc<true, false, true>(lane, n, Y.A, t.t2, Bb);
   for (int e = lane; e < nn; e += 32) {
     const int i = e / n, c = e % n;
-    Bb[e] -= t.t3[e];
     Fb[e] -= Y.eta[i] * Kb.eta[c];
     YB.J[e] += Kb.eta[i] * t.beta[c];
   }
@@ -645,26 +656,15 @@ __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const
   }
   for (int e = lane; e < nn; e += 32) Qb[e] -= Kb.J[e];
   sync();
-  mmt(lane, n, Kb.J, F, t.t2);
-  for (int e = lane; e < nn; e += 32) YB.J[e] -= t.t2[e];
-  sync();
-  mm(lane, n, F, Kb.J, t.t2);
-  for (int e = lane; e < nn; e += 32) YB.J[e] -= t.t2[e];
-  sync();
-  mmt(lane, n, Kb.J, t.t1, t.t2);
-  for (int e = lane; e < nn; e += 32) YB.J[e] += t.t2[e];
-  sync();
+  mm_acc<false, true, true>(lane, n, Kb.J, F, YB.J);
+  mm_acc<false, false, true>(lane, n, F, Kb.J, YB.J);
+  mm_acc<false, true, false>(lane, n, Kb.J, t.t1, YB.J);
   mtm(lane, n, Y.J, Kb.J, t.t3);  // Gbar2
   for (int e = lane; e < nn; e += 32) Fb[e] -= t.t3[e];
   sync();
-  mmt(lane, n, Y.J, Kb.J, t.t2);
-  for (int e = lane; e < nn; e += 32) Fb[e] -= t.t2[e];
-  sync();
-  mmt(lane, n, t.t3, Y.J, t.t2);
-  for (int e = lane; e < nn; e += 32) Bb[e] += t.t2[e];
-  sync();
-  mtm(lane, n, B, t.t3, t.t2);
-  for (int e = lane; e < nn; e += 32) YB.J[e] += t.t2[e];
+  mm_acc<false, true, true>(lane, n, Y.J, Kb.J, Fb);
+  mm_acc<false, true, false>(lane, n, t.t3, Y.J, Bb);
+  mm_acc<true, false, false>(lane, n, B, t.t3, YB.J);
   const double zb = *Kb.z;
   if (lane == 0) *rhob -= 0.5 * zb;
   if (lane < n) {

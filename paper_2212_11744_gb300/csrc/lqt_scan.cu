@@ -645,8 +645,12 @@ static void affine_scan_n(const double* maps, int64_t cnt, const double* x_in, d
     const int64_t nc = ceil_div(mc, G);
     double* out = (double*)(ws + off);
     off = align_up(off + nc * PM * sizeof(double));
-    reduce_maps_kernel<N><<<blocks_for(nc), 128, 0, st>>>(prev, mc, G, out);
-    count_launch();
+    if (nc < team_level_below<N>()) {
+      team_maps_reduce<N>(prev, mc, G, out, st);
+    } else {
+      reduce_maps_kernel<N><<<blocks_for(nc), 128, 0, st>>>(prev, mc, G, out);
+      count_launch();
+    }
     c[nlev] = nc;
     lv[nlev] = out;
     sv[nlev] = (double*)(ws + off);
@@ -666,8 +670,12 @@ static void affine_scan_n(const double* maps, int64_t cnt, const double* x_in, d
     const double* mp = (l == 0) ? maps : lv[l - 1];
     const int64_t mcnt = (l == 0) ? cnt : c[l - 1];
     double* outst = (l == 0) ? states : sv[l - 1];
-    down_maps_kernel<N><<<blocks_for(ceil_div(mcnt, G)), 128, 0, st>>>(mp, mcnt, G, sv[l], x_in, outst);
-    count_launch();
+    if (ceil_div(mcnt, G) < team_level_below<N>()) {
+      team_maps_down<N>(mp, mcnt, G, sv[l], x_in, outst, st);
+    } else {
+      down_maps_kernel<N><<<blocks_for(ceil_div(mcnt, G)), 128, 0, st>>>(mp, mcnt, G, sv[l], x_in, outst);
+      count_launch();
+    }
   }
 }
 

@@ -419,8 +419,9 @@ __device__ __forceinline__ void copy_rec(int lane, Rec<N> dst, Rec<N> src) {
 
 // ---------------------------------------------------------------------------
 // LU with partial pivoting on W (N x N), applied to R (N x Q); both in the
-// caller's buffers.  Scratch: fscratch 2 * TEAM doubles (a CTA keeps its row
-// scales at TEAM.., its pivot reciprocals at TEAM + 64..), iscratch TEAM ints.
+// caller's buffers.  Scratch: fscratch 2 * TEAM doubles (the pivot
+// reciprocals at TEAM.. for a warp; a CTA keeps its row scales at TEAM.. and
+// its pivot reciprocals at TEAM + 64..), iscratch TEAM ints.
 // The pivot search compares magnitude keys (mag_key) on the integer pipes.
 // W = I + P in every use (P = C J or C S): a pivot no larger than 2^-40 times
 // its row's original scale max(1, max_j |W_ij|) sets the SINGULAR status bit
@@ -525,8 +526,10 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
       sync<TEAM>();
       continue;
     }
-    // multipliers into column k (below the diagonal)
+    // multipliers into column k (below the diagonal); 1 / pivot kept for the
+    // back substitution
     const double inv = 1.0 / W[k * N + k];
+    if (lane == 0) fscratch[TEAM + k] = inv;
     for (int i = k + 1 + lane; i < N; i += TEAM) W[i * N + k] *= inv;
     sync<TEAM>();
     // rank-1 update of the trailing rows
@@ -565,7 +568,7 @@ __device__ void lu_solve(int lane, double* W, double* R, double* fscratch, int* 
   for (int k = N - 1; k >= 0; --k) {
     double inv;
     if constexpr (TEAM > 32) inv = fscratch[TEAM + 64 + k];
-    else inv = 1.0 / W[k * N + k];
+    else inv = fscratch[TEAM + k];
     for (int j = lane; j < Q; j += TEAM) R[k * Q + j] *= inv;
     sync<TEAM>();
     for (int e = lane; e < k * Q; e += TEAM) {
