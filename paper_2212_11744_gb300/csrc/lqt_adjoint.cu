@@ -656,13 +656,19 @@ __device__ void rhs_vjp(int lane, int n, const double* y, const double* F, const
   }
   for (int e = lane; e < nn; e += 32) Qb[e] -= Kb.J[e];
   sync();
-  mm_acc<false, true, true>(lane, n, Kb.J, F, YB.J);
-  mm_acc<false, false, true>(lane, n, F, Kb.J, YB.J);
-  mm_acc<false, true, false>(lane, n, Kb.J, t.t1, YB.J);
-  mtm(lane, n, Y.J, Kb.J, t.t3);  // Gbar2
-  for (int e = lane; e < nn; e += 32) Fb[e] -= t.t3[e];
+  // Kb.J F^T + F Kb.J = X + X^T with X = Kb.J F^T (Kb.J symmetric)
+  mmt(lane, n, Kb.J, F, t.t2);
+  for (int e = lane; e < nn; e += 32) {
+    const int i = e / n, c = e % n;
+    YB.J[e] -= t.t2[i * n + c] + t.t2[c * n + i];
+  }
   sync();
-  mm_acc<false, true, true>(lane, n, Y.J, Kb.J, Fb);
+  mm_acc<false, true, false>(lane, n, Kb.J, t.t1, YB.J);
+  // Gbar2 = J^T Kb.J, which is also J Kb.J^T term by term: the stage input's
+  // J is built symmetric and Kb.J was symmetrised above
+  mtm(lane, n, Y.J, Kb.J, t.t3);
+  for (int e = lane; e < nn; e += 32) Fb[e] -= 2.0 * t.t3[e];
+  sync();
   mm_acc<false, true, false>(lane, n, t.t3, Y.J, Bb);
   mm_acc<true, false, false>(lane, n, B, t.t3, YB.J);
   const double zb = *Kb.z;

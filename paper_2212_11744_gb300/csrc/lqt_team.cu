@@ -10,6 +10,7 @@
 #include "lqt_internal.h"
 #include "lqt_team.cuh"
 #include "lqt_warp16.cuh"
+#include "lqt_warp8.cuh"
 
 namespace lqt {
 
@@ -1006,23 +1007,87 @@ static cudaError_t team_run_g(const lqt_problem& p, const Coefs& cf, const ElemP
   return cudaGetLastError();
 }
 
-// Upper levels of the thread-per-element scans (lqt_scan.cu), n <= 8: one
-// warp per combination, records in the full-matrix layout.
+// Upper levels of the thread-per-element scans (lqt_scan.cu), n = 4 and 8:
+// one warp per pair with the register Gauss-Jordan combinations of
+// lqt_warp8.cuh, records in the full-matrix layout (full_elem_doubles,
+// full_val_doubles), staged in shared memory by coalesced loads.
+template <int N, typename GT>
+__global__ void __launch_bounds__(32) reduce_w8_kernel(const double* __restrict__ src, int64_t cnt,
+                                                       double* __restrict__ agg) {
+  using L = w8::Lay<N>;
+  __shared__ double e1[L::REC], e2[L::REC], out[L::REC], scr[L::SCRATCH];
+  const int lane = threadIdx.x;
+  const int64_t groups = tdiv(cnt, 2);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = 2 * g;
+    double* dst = agg + g * L::REC;
+    if (first + 1 >= cnt) {
+      for (int e = lane; e < L::REC; e += 32) dst[e] = src[first * L::REC + e];
+      continue;
+    }
+    for (int e = lane; e < L::REC; e += 32) {
+      e1[e] = src[first * L::REC + e];
+      e2[e] = src[(first + 1) * L::REC + e];
+    }
+    __syncwarp();
+    w8::combine<N, GT>(lane, e1, e2, out, scr);
+    for (int e = lane; e < L::REC; e += 32) dst[e] = out[e];
+    __syncwarp();
+  }
+}
+
+template <int N, typename GT>
+__global__ void __launch_bounds__(32) down_w8_kernel(const double* __restrict__ src, int64_t cnt,
+                                                     const double* __restrict__ above, int64_t cnt_above,
+                                                     double* __restrict__ vals) {
+  using L = w8::Lay<N>;
+  __shared__ double e[L::REC], c0[L::VAL], c1[L::VAL], scr[L::SCRATCH];
+  const int lane = threadIdx.x;
+  const int64_t groups = tdiv(cnt, 2);
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t first = 2 * g;
+    const int64_t last = (first + 2 < cnt ? first + 2 : cnt) - 1;
+    double* carry = c0;
+    double* nv = c1;
+    for (int q = lane; q < L::VAL; q += 32)
+      carry[q] = (above != nullptr && g + 1 < cnt_above) ? above[(g + 1) * L::VAL + q] : 0.0;
+    for (int64_t k = last; k >= first; --k) {
+      for (int q = lane; q < L::REC; q += 32) e[q] = src[k * L::REC + q];
+      __syncwarp();
+      w8::combine_value<N, GT>(lane, e, carry, nv, scr);
+      for (int q = lane; q < L::VAL; q += 32) vals[k * L::VAL + q] = nv[q];
+      __syncwarp();
+      double* t = carry;
+      carry = nv;
+      nv = t;
+    }
+  }
+}
+
 template <int N, typename GT>
 void team_upper_reduce(const double* src, int64_t cnt, double* agg, cudaStream_t st) {
   static_assert(Rec<N>::SIZE == full_elem_doubles<N>(), "record layouts differ");
-  TeamScanArgs a{};
-  a.src = src; a.cnt = cnt; a.G = 2; a.agg = agg;
-  team_launch<N>(reduce_team_kernel<N, GT>, tdiv(cnt, 2), reduce_slot_doubles<N>(), a, st);
+  if constexpr (N == 4 || N == 8) {
+    team_launch<N>(reduce_w8_kernel<N, GT>, tdiv(cnt, 2), 0, src, st, TeamCfg<N>::SLOTS, cnt, agg);
+  } else {
+    TeamScanArgs a{};
+    a.src = src; a.cnt = cnt; a.G = 2; a.agg = agg;
+    team_launch<N>(reduce_team_kernel<N, GT>, tdiv(cnt, 2), reduce_slot_doubles<N>(), a, st);
+  }
 }
 
 template <int N, typename GT>
 void team_upper_down(const double* src, int64_t cnt, const double* above, int64_t cnt_above, double* vals,
                      cudaStream_t st) {
   static_assert(team::val_doubles<N>() == full_val_doubles<N>(), "value layouts differ");
-  TeamScanArgs a{};
-  a.src = src; a.cnt = cnt; a.G = 2; a.above = above; a.cnt_above = cnt_above; a.vals = vals;
-  team_launch<N>(down_team_kernel<N, false, GT>, tdiv(cnt, 2), down_slot_doubles<N>(), a, st);
+  if constexpr (N == 4 || N == 8) {
+    team_launch<N>(down_w8_kernel<N, GT>, tdiv(cnt, 2), 0, src, st, TeamCfg<N>::SLOTS, cnt, above, cnt_above,
+                   vals);
+  } else {
+    TeamScanArgs a{};
+    a.src = src; a.cnt = cnt; a.G = 2; a.above = above; a.cnt_above = cnt_above; a.vals = vals;
+    team_launch<N>(down_team_kernel<N, false, GT>, tdiv(cnt, 2), down_slot_doubles<N>(), a, st);
+  }
 }
 
 template <int N>
