@@ -15,7 +15,8 @@
 //     from the cubic Hermite interpolant y(t + h/2) = (y_i + y_{i+1})/2 +
 //     h (y_i' - y_{i+1}')/8;
 //   controls u = U^-1 L^T (v - S x) (eq. LQT_optimal_control) with the U, L
-//     sample at each sub-step.
+//     sample at each sub-step: the prepared gain Ku when L and U do not vary
+//     within a sub-interval, else a Cholesky solve of that sub-step's U.
 // At the boundaries (i = 0 and the final point) the outputs are the given
 // boundary solution.
 #include <cuda_runtime.h>
@@ -36,6 +37,7 @@ struct DenseArgs {
   Coef L, U;  // raw samples: n x m and m x m
   const double *S, *v, *zeta, *x;  // boundary solution, [T+1]
   double *Sd, *vd, *zd, *xd, *ud;  // [T K + 1]
+  int ku_exact;  // L and U constant within every sub-interval: cf.Ku holds U^-1 L^T for every sub-step
 };
 
 // u = U^-1 L^T e for one sample (U symmetric positive definite, m <= MM, the
@@ -117,6 +119,18 @@ __device__ __forceinline__ void control_at(const DenseArgs& a, int64_t j, int32_
 #pragma unroll
     for (int l = 0; l < N; ++l) s = fma(-y.S[sidx<N>(i, l)], x[l], s);
     e[i] = s;
+  }
+  if (a.ku_exact) {
+    // the prepared gain of the sub-interval (of the final boundary at p = 2K)
+    const int64_t k = (p == 2 * a.K) ? j + 1 : j;
+    const double* Kk = a.cf.Ku + (a.cf.Ku_per_boundary ? k * a.m * N : 0);
+    for (int q = 0; q < a.m; ++q) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) s = fma(Kk[q * N + l], e[l], s);
+      u[q] = s;
+    }
+    return;
   }
   const double* L = a.L.ptr + sample_index(a.L.mode, j, p, a.K) * N * a.m;
   const double* U = a.U.ptr + sample_index(a.U.mode, j, p, a.K) * a.m * a.m;
@@ -281,6 +295,9 @@ cudaError_t launch_densify(const lqt_problem& p, const Layout& lay, const Coefs&
   a.U = Coef{(const double*)p.U.ptr, p.U.mode};
   a.S = S; a.v = v; a.zeta = zeta; a.x = x;
   a.Sd = Sd; a.vd = vd; a.zd = zd; a.xd = xd; a.ud = ud;
+  // Ku (prepared at the boundaries from sample (j, 0), or (T-1, 2K) at T) is
+  // the gain of every sub-step when no coefficient of it varies per stage
+  a.ku_exact = (p.L.mode != LQT_PER_STAGE && p.U.mode != LQT_PER_STAGE && cf.Ku != nullptr) ? 1 : 0;
   switch (p.n) {
     case 1: return launch_dense_n<1>(a, lay.M, st);
     case 2: return launch_dense_n<2>(a, lay.M, st);
