@@ -179,6 +179,13 @@ __host__ __device__ constexpr int split_lanes(int outputs, int team) {
 // so that every lane issues FP64 work: on this GPU a warp's FP64 instruction
 // costs its sub-partition the same 64 cycles whatever the active lanes.  The
 // symmetric C, J are formed on their upper triangles.
+//
+// A CTA (n = 64, buffers in global memory): one output per thread at a time
+// needs two operand loads per FMA, and the loads, not the FP64 pipe, then set
+// the pace (the LSU queue full, 71% FP64 busy).  So there AL, P and dA are
+// register-blocked team products (gemm: 4 x 4 blocks, half a load per FMA),
+// and dJ's J F + (J F)^T is one blocked product J F into shared memory, read
+// twice.
 template <int N, int M, int TEAM>
 __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, const double* __restrict__ c,
                     const double* __restrict__ Lt, const double* __restrict__ Q, const double* __restrict__ qr,
@@ -186,6 +193,20 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
   const double* A = y.A();
   const double* J = y.J();
   const double* eta = y.eta();
+  double* JF = nullptr;
+  if constexpr (TEAM > 32) {
+    __shared__ double jf_smem[N * N];
+    JF = jf_smem;
+    gemm<N, M, N, TEAM, double>(
+        lane, [&](int i, int l) { return A[i * N + l]; }, [&](int l, int a) { return Lt[l * M + a]; },
+        [&](int i, int a, double s) { AL[i * M + a] = s; });
+    gemm<N, M, N, TEAM, double>(
+        lane, [&](int i, int l) { return J[i * N + l]; }, [&](int l, int a) { return Lt[l * M + a]; },
+        [&](int i, int a, double s) { P[i * M + a] = s; });
+    gemm<N, N, N, TEAM, double>(
+        lane, [&](int i, int l) { return J[i * N + l]; }, [&](int l, int j) { return F[l * N + j]; },
+        [&](int i, int j, double s) { JF[i * N + j] = s; });
+  } else {
   for (int e = lane; e < N * M; e += TEAM) {
     const int i = e / M, a = e % M;
     double s1 = 0.0, s2 = 0.0;
@@ -195,6 +216,7 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
     }
     AL[e] = s1;
     P[e] = s2;
+  }
   }
   {  // w = Lt^T eta
     constexpr int S = split_lanes(M, TEAM);
@@ -208,12 +230,22 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
   sync<TEAM>();
   constexpr int NS = N * (N + 1) / 2;
   // dA = AL P^T - A F
-  for (int t = lane; t < N * N; t += TEAM) {
-    const int i = t / N, j = t % N;
-    double s = 0.0;
-    for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
-    for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
-    k.A()[t] = s;
+  if constexpr (TEAM > 32) {
+    double* kA = k.A();
+    gemm<N, N, M, TEAM, double>(
+        lane, [&](int i, int a) { return AL[i * M + a]; }, [&](int a, int j) { return P[j * M + a]; },
+        [&](int i, int j, double s) { kA[i * N + j] = s; });
+    gemm<N, N, N, TEAM, double>(
+        lane, [&](int i, int l) { return A[i * N + l]; }, [&](int l, int j) { return F[l * N + j]; },
+        [&](int i, int j, double s) { kA[i * N + j] -= s; });
+  } else {
+    for (int t = lane; t < N * N; t += TEAM) {
+      const int i = t / N, j = t % N;
+      double s = 0.0;
+      for (int a = 0; a < M; ++a) s = fma(AL[i * M + a], P[j * M + a], s);
+      for (int l = 0; l < N; ++l) s = fma(-A[i * N + l], F[l * N + j], s);
+      k.A()[t] = s;
+    }
   }
   {  // db = -AL w - A c ; deta = -q - F^T eta + J c + P w
     constexpr int S = split_lanes(N, TEAM);
@@ -241,6 +273,22 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
   }
   // dC = -AL AL^T ; dJ = -Q - JF - (JF)^T + P P^T  (upper triangles, mirrored):
   // whole passes one entry per thread, the remainder spread over lane groups
+  if constexpr (TEAM > 32) {
+    for (int t = lane; t < NS; t += TEAM) {
+      int i, j;
+      upper_ij(N, t, i, j);
+      double sc = 0.0, sj = -Q[i * N + j] - JF[i * N + j] - JF[j * N + i];
+      for (int a = 0; a < M; ++a) {
+        sc = fma(-AL[i * M + a], AL[j * M + a], sc);
+        sj = fma(P[i * M + a], P[j * M + a], sj);
+      }
+      const double cn = fma(sq, sc, qacc.C()[i * N + j]);
+      qacc.C()[i * N + j] = cn;
+      qacc.C()[j * N + i] = cn;
+      k.J()[i * N + j] = sj;
+      k.J()[j * N + i] = sj;
+    }
+  } else {
   constexpr int NSF = NS - NS % TEAM;
   for (int t = lane; t < NSF; t += TEAM) {
     int i, j;
@@ -287,6 +335,7 @@ __device__ void rhs(int lane, Rec<N> y, Rec<N> k, const double* __restrict__ F, 
       k.J()[i * N + j] = sj;
       k.J()[j * N + i] = sj;
     }
+  }
   }
   if (lane < 32) {  // dzeta = -rho/2 + |w|^2/2 + eta^T c, over the first warp
     double z = 0.0;
