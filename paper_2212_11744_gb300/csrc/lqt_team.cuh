@@ -44,7 +44,8 @@ __device__ __forceinline__ void upper_ij(int N, int t, int& i, int& j) {
 
 // Register-blocked product over a team: out(i, j, s) receives
 // s = sum_{l < INNER} a(i, l) b(l, j) for i < ROWS, j < COLS.  Each thread owns
-// an RB x CB block of outputs (RB * CB accumulators, RB + CB operand loads per
+// an RB x CB set of outputs, RB consecutive rows by CB columns a block-count
+// apart (RB * CB accumulators, RB + CB operand loads per
 // step of l), with the block shape chosen so that the blocks just cover the
 // team; the mapping depends only on (ROWS, COLS, TEAM), so two products of one
 // shape give every thread the same outputs (a thread may then accumulate
@@ -54,8 +55,8 @@ __device__ __forceinline__ void upper_ij(int N, int t, int& i, int& j) {
 // one column and RB consecutive rows, so that consecutive lanes read
 // consecutive words of b and share rows of a (an operand read from several
 // rows of one column would hit one shared-memory bank: the row stride is a
-// multiple of 32 words); a larger team (n = 64, buffers in global memory) takes
-// square 4 x 4 blocks, which need the fewest loads per FMA.
+// multiple of 32 words); a larger team (n = 64) takes 4 x 4 sets, which need
+// the fewest loads per FMA.
 template <int ROWS, int COLS, int TEAM>
 struct GemmShape {
   static constexpr int cb() {
@@ -78,8 +79,11 @@ template <int ROWS, int COLS, int INNER, int TEAM, typename G, class FA, class F
 __device__ __forceinline__ void gemm(int lane, FA a, FB b, FO out) {
   constexpr int RB = GemmShape<ROWS, COLS, TEAM>::RB, CB = GemmShape<ROWS, COLS, TEAM>::CB;
   constexpr int NBC = COLS / CB, NB = (ROWS / RB) * NBC;
+  // a thread's CB columns are jb, jb + NBC, ...: consecutive threads then read
+  // consecutive words of a row of b (one shared-memory wavefront for 16
+  // doubles) rather than words 32 bytes apart
   for (int blk = lane; blk < NB; blk += TEAM) {
-    const int i0 = (blk / NBC) * RB, j0 = (blk % NBC) * CB;
+    const int i0 = (blk / NBC) * RB, jb = blk % NBC;
     G acc[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -91,7 +95,7 @@ __device__ __forceinline__ void gemm(int lane, FA a, FB b, FO out) {
 #pragma unroll
       for (int r = 0; r < RB; ++r) av[r] = (G)a(i0 + r, l);
 #pragma unroll
-      for (int c = 0; c < CB; ++c) bv[c] = (G)b(l, j0 + c);
+      for (int c = 0; c < CB; ++c) bv[c] = (G)b(l, jb + c * NBC);
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
@@ -100,7 +104,7 @@ __device__ __forceinline__ void gemm(int lane, FA a, FB b, FO out) {
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int c = 0; c < CB; ++c) out(i0 + r, j0 + c, acc[r][c]);
+      for (int c = 0; c < CB; ++c) out(i0 + r, jb + c * NBC, acc[r][c]);
   }
 }
 
