@@ -181,3 +181,20 @@ def test_backward_workspace_holds_one_segment_of_stage_inputs(lib):
     T1, T2 = 1 << 16, 1 << 20
     assert ws(T2) > ws(T1) > 0
     assert (ws(T2) - ws(T1)) / (T2 - T1) < 0.5 * stage_record
+
+
+def test_method2_workspaces_cover_every_state_dimension(lib):
+    """Method 2 runs at every state dimension of lqt_solve: its workspace kinds
+    are non-zero for n = 16 and 64 (team kernels), the solve's exceeds the
+    trajectory's, and the n = 64 forward-element build's scratch (LQT_WS_BUILD)
+    holds 152 slots of four element records plus products."""
+    import paper_2212_11744_gb300 as m
+    for p in (W.batched_member(7, T=300, n=16), W.large_state_n64(T=129)):
+        hp = m.HostProblem(p, pinned=False)
+        traj = m.lqt_workspace_size(hp, m.LQT_WS_METHOD2)
+        solve = m.lqt_workspace_size(hp, m.LQT_WS_SOLVE_METHOD2)
+        assert traj > 0 and solve > traj, p.n
+    hp = m.HostProblem(W.large_state_n64(T=129), pinned=False)
+    n = 64
+    four_records = 4 * (3 * n * n + 2 * n + 1) * 8
+    assert m.lqt_workspace_size(hp, m.LQT_WS_BUILD) >= 152 * four_records
