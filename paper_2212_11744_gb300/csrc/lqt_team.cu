@@ -1,9 +1,13 @@
 // Solve path for state dimensions 16 and 64: the same three stages as the
 // one-thread-per-element kernels (lqt_build.cu, lqt_scan.cu) with a team of
 // threads per element (lqt_team.cuh).  n = 16: one warp per element, every
-// buffer in shared memory.  n = 64: one CTA of 256 threads per element, the
-// element-sized buffers in a per-CTA slot of the workspace (they stay in L2),
-// grid = one CTA per SM looping over the work.
+// buffer in shared memory (the combinations: lqt_warp16.cuh).  n = 64: one CTA
+// of 256 threads per element, the element-sized buffers in a per-CTA slot of
+// the workspace (they stay in L2) and the combinations' scratch in shared
+// memory, grid = one CTA per SM looping over the work.  Also here: Method 2
+// (forward-ODE elements, prefix scan, states) for n = 16 and 64, the
+// warp-per-element build of n = 4 and 8 at short horizons, and the warp-per-pair
+// upper scan levels of n = 4 and 8 (lqt_warp8.cuh).
 #include <cuda_runtime.h>
 
 #include "lqt_device.cuh"
